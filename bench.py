@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Throughput of the free-BC Poisson solve at 256^3 (FP32) on GB300.
+
+One step = one solve (the five passes: forward x, forward y, z forward +
+K^F multiply + inverse, inverse y, inverse x, plus the Hartree energy) of a
+256^3 Gaussian-mixture density with free boundary conditions on all axes
+(padded FFT 512^3). Inputs are resident in HBM; a 512 MiB buffer is written
+between steps so no step starts with its data in L2. The metric is physical
+grid points per second (n1 n2 n3 / time per solve) and the fraction of the
+HBM roofline of the dominant kernel and of the whole solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank solves its own density (replicas, weak
+scaling, no collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid points/s per Poisson solve (free BCs, 256³) and % of HBM roofline at stated error"
+UNIT = "grid points/s"
+WORKLOAD = "free256_f32"
+FALLBACK_HBM_GBS = 6800.0
+PASS_NAMES = ["p1_fwd_x_r2c", "p2_fwd_y", "p3_z_fwd_mul_inv", "p4_inv_y", "p5_inv_x_c2r"]
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the named kernel on this workload, with the hash of the
+# kernel sources it was taken on; reported as null once the sources change.
+TRAFFIC = {}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1211_5244_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+def _workload_desc(w):
+    n = w["n"]
+    return (f"free-BC Poisson solve {n[0]}x{n[1]}x{n[2]} FP32 (padded FFT {2*n[0]}^3), "
+            f"{w['n_gauss']}-Gaussian density + {w['noise']:g} noise, h={w['h']}, seed {w['seed']}")
+
+
+def _pass_bytes(info, esz):
+    """Algorithmic HBM bytes of each pass (one launch each)."""
+    n1, n2, n3 = info.n
+    L1, L2, L3 = info.L
+    c = info.c
+    N = n1 * n2 * n3
+    A = c * n2 * n3 * 2 * esz          # complex spectrum after the x pass
+    B = c * L2 * n3 * 2 * esz          # after the y pass
+    Koct = c * (L2 // 2 + 1) * (L3 // 2 + 1) * esz
+    return [N * esz + A, A + B, 2 * B + Koct, B + A, A + N * esz]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _density(w, rank=0):
+    import numpy as np
+    from paper_1211_5244_gb300 import synth
+    rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"] + rank, noise=w["noise"])
+    return rho.astype(np.float32)
+
+
+def _oracle_baseline(w, rho32, V_gpu, E_gpu):
+    """The FP64 oracle as it stands, timed on the host on one full solve of the
+    workload (K^F built before the timed region, like the GPU's kernel build)."""
+    import numpy as np
+    from oracle import poisson as op
+    rho = rho32.astype(np.float64)
+    KF = op.kernel_fourier(w["n"], "fff", w["h"])
+    t0 = time.perf_counter()
+    Vo, Eo = op.solve(rho, "fff", w["h"], KF=KF)
+    dt = time.perf_counter() - t0
+    npts = rho.size
+    err = {
+        "rel_l2": float(np.linalg.norm(V_gpu - Vo) / np.linalg.norm(Vo)),
+        "rel_max": float(np.abs(V_gpu - Vo).max() / np.abs(Vo).max()),
+        "energy_rel": float(abs(E_gpu - Eo) / abs(Eo)),
+        "vs": "FP64 oracle, full grid",
+    }
+    base = {"value": npts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full {w['n'][0]}^3 free-BC oracle solve (numpy FFT of the padded "
+                      f"{2*w['n'][0]}^3 grid, FP64, single thread), {dt:.1f} s; K^F built untimed"}
+    return base, err
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores. Each step is one oracle
+    solve of a free-BC density of the same recipe at a bounded size (a sample
+    of the 256^3 workload): 128^3 when K + W <= 60, 64^3 up to 600 steps,
+    32^3 beyond, so the whole run stays within about two minutes."""
+    import numpy as np
+    from oracle import poisson as op
+    from paper_1211_5244_gb300 import synth
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    w = dict(synth.WORKLOADS[WORKLOAD])
+    m = 128 if args.steps + args.warmup <= 60 else (64 if args.steps + args.warmup <= 600 else 32)
+    ws = dict(w, n=(m, m, m))
+    rho = synth.gaussian_mixture(ws["n"], ws["h"], ws["n_gauss"], ws["seed"], noise=ws["noise"])
+    rho = rho.astype(np.float32).astype(np.float64)
+    KF = op.kernel_fourier(ws["n"], "fff", ws["h"])
+    for _ in range(args.warmup):
+        op.solve(rho, "fff", ws["h"], KF=KF)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op.solve(rho, "fff", ws["h"], KF=KF)
+    dt = time.perf_counter() - t0
+    value = rho.size * args.steps / dt
+    sample = (f"each step one FP64 oracle solve of a {m}^3 free-BC density of the same recipe "
+              f"(numpy FFT, single thread)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": _workload_desc(w), "bc": "fff"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1211_5244_gb300 import build as _build
+    from paper_1211_5244_gb300 import psolver, synth
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+
+    w = synth.WORKLOADS[WORKLOAD]
+    rho_np = _density(w, rank)
+    rho = torch.from_numpy(rho_np).cuda()
+    plan = psolver.Plan(w["n"], "fff", w["h"], "f32")
+    info = plan.info()
+    V = torch.empty_like(rho)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.solve(rho, V, stream=stream, E=E)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    plan.set_profiling(True)
+    plan.pass_times()  # forget anything recorded earlier
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        plan.solve(rho, V, stream=stream, E=E)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    plan.set_profiling(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    pass_ms, nrec = plan.pass_times()
+    pass_ms = [t / max(nrec, 1) for t in pass_ms]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    npts = int(np.prod(w["n"]))
+    value = world * K * npts / (total_ms / 1e3)
+    ms_per_step = total_ms / K
+
+    # ---- end-to-end through the host-buffer entry point (pinned memory) ----
+    rho_host = torch.from_numpy(rho_np).pin_memory()
+    V_host = torch.empty_like(rho_host).pin_memory()
+    for _ in range(2):
+        plan.solve_host(rho_host, V_host)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        _, e_host = plan.solve_host(rho_host, V_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * K * npts / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": npts * 4, "d2h_bytes_per_step": npts * 4 + 8}
+
+    # ---- roofline ----
+    peak, peak_src = _peak_hbm()
+    pbytes = _pass_bytes(info, 4)
+    dom = max(range(5), key=lambda k: pass_ms[k])
+    achieved = pbytes[dom] / (pass_ms[dom] / 1e3) / 1e9
+    tr = TRAFFIC.get((PASS_NAMES[dom], WORKLOAD))
+    traffic = tr["bytes"] if tr and tr["src"] == _src_hash() else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": PASS_NAMES[dom], "alg_bytes_per_launch": pbytes[dom],
+            "peak_source": peak_src}
+    solve_gbs = info.alg_bytes / (ms_per_step / 1e3) / 1e9
+    passes = {PASS_NAMES[k]: {"ms": pass_ms[k], "alg_bytes": pbytes[k],
+                              "GB/s": pbytes[k] / (pass_ms[k] / 1e3) / 1e9,
+                              "frac": pbytes[k] / (pass_ms[k] / 1e3) / 1e9 / peak} for k in range(5)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": _workload_desc(w), "n": list(w["n"]), "bc": "fff", "h": w["h"],
+                   "l2": "flushed (512 MiB write) before every step; per-step CUDA events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "solve_roofline": {"alg_bytes": info.alg_bytes, "achieved": solve_gbs, "peak": peak,
+                           "unit": "GB/s", "frac": solve_gbs / peak},
+        "passes": passes,
+        "e2e": e2e,
+        "gpu_launches": 5 * K,
+        "clocks": clocks,
+        "kernel_src": _src_hash(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, err = _oracle_baseline(w, rho_np, V.double().cpu().numpy(), float(E.item()))
+        line["cpu_baseline"] = base
+        line["error_vs_oracle"] = err
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * psolver.h -- C ABI of the GB300 free/mixed-boundary FFT Poisson solver.
+ *
+ * Method (Dugan, Genovese, Goedecker, "A Customized 3D GPU Poisson Solver for
+ * Free Boundary Conditions"):
+ *   Eq. 1   laplacian(V) = rho            (sign as printed, no -4 pi)
+ *   Eq. 2   V(r) = sum_r' K(r - r') rho(r')
+ *   Eq. 3   V^F(k) = K^F(k) rho^F(k)
+ *   §2      free axes are zero padded to twice their length (any padded length
+ *           L >= 2n - 1 gives the same physical result); periodic axes are
+ *           transformed at their own length n
+ *   §3      the 3D FFT skips every 1D transform of an all-zero line on the
+ *           forward pass, computes only the physical n-wide output on the
+ *           inverse pass, uses a real-to-complex transform on the first axis
+ *           and keeps L1/2 + 1 of its outputs, and stores K^F in the layout of
+ *           the last forward axis so that no final transpose is needed.
+ *
+ * Conventions shared by every entry point
+ *   - Grids are real arrays of n1*n2*n3 elements, x fastest:
+ *       rho[i + n1*(j + n2*k)],  i < n1 (x), j < n2 (y), k < n3 (z).
+ *     In PyTorch this is a contiguous (n3, n2, n1) tensor.
+ *   - The element type is the plan's dtype: float (PS_F32) or double (PS_F64).
+ *   - "device pointer" means memory of the device the plan was built on;
+ *     "host pointer" means ordinary or pinned host memory.
+ *   - Every call returns a status (enum ps_status). PS_OK is 0. On error
+ *     nothing has been launched unless the status is PS_ERR_CUDA (a launch or
+ *     runtime call failed); ps_last_error() then holds a message for the
+ *     calling thread.
+ *   - Calls that take a stream enqueue their work on it (NULL = the legacy
+ *     default stream) and return without waiting, except where noted.
+ *   - A plan owns its workspace and K^F. One plan must not be used by two
+ *     solves that may run at the same time (two streams); give each stream
+ *     its own plan.
+ */
+#ifndef PSOLVER_H
+#define PSOLVER_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ps_plan_s* ps_plan;
+
+/* Boundary condition per axis. The paper's B_j = 1 (periodic) / 2 (free), §3. */
+enum ps_bc { PS_BC_PERIODIC = 0, PS_BC_FREE = 1 };
+
+/* Element type of rho and V, and of the arithmetic of the solve. */
+enum ps_dtype { PS_F32 = 0, PS_F64 = 1 };
+
+/* Arithmetic of the 1D transforms. Only CUDA-core arithmetic is provided:
+ * the transforms are bound by HBM traffic, not by a dense contraction. */
+enum ps_math { PS_MATH_CUDACORE = 0 };
+
+enum ps_status {
+  PS_OK = 0,
+  PS_ERR_ARG = 1,          /* invalid argument (sizes, enums, null pointers) */
+  PS_ERR_UNSUPPORTED = 2,  /* valid but outside what this build handles      */
+  PS_ERR_NOT_BUILT = 3,    /* ps_kernel_build has not run on this plan       */
+  PS_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed           */
+  PS_ERR_OOM = 5,          /* device allocation failed                       */
+  PS_ERR_TIMEOUT = 6       /* reserved: a bounded device wait gave up        */
+};
+
+/* Host-side description of a plan (ps_plan_query). */
+typedef struct {
+  int n[3];                 /* physical grid n1, n2, n3                           */
+  int bc[3];                /* enum ps_bc per axis x, y, z                        */
+  int L[3];                 /* FFT length per axis (§3: S_j = N_j B_j by default) */
+  int c;                    /* L1/2 + 1: x-spectrum kept after the R2C (§3)       */
+  int dtype;                /* enum ps_dtype                                      */
+  int math;                 /* enum ps_math                                       */
+  long long lines[5];       /* 1D transforms per pass: fwd x, fwd y, z (each of
+                               its lines is transformed forward and back), inv y,
+                               inv x                                             */
+  long long line_len[5];    /* their lengths (L1, L2, L3, L2, L1)                 */
+  double fft_points;        /* sum over the passes above of lines * length (the z
+                               lines counted twice: forward and inverse)          */
+  double paper_points;      /* §3 count for one forward 3D transform: rows times
+                               length per step with complex rows, N_y N_z S_x +
+                               S_x N_z S_y + S_x S_y S_z                          */
+  double paper_full_points; /* the same count for an unpruned padded 3D FFT,
+                               3 S_x S_y S_z (paper_points / paper_full_points is
+                               7/12 for free and wire, 2/3 for surface BCs)      */
+  double alg_bytes;         /* HBM bytes one solve must move in this design:
+                               rho in, V out, four intermediate write+read pairs,
+                               and one read of the stored K^F octant            */
+  size_t workspace_bytes;   /* device bytes the plan allocates at build          */
+} ps_plan_info;
+
+/*
+ * ps_plan_create -- describe a solve; allocates host memory only.
+ *   n1, n2, n3 >= 1      physical grid (x, y, z)
+ *   h > 0                grid spacing (isotropic), in the length unit of V
+ *   bc_x, bc_y, bc_z     enum ps_bc
+ *   dtype                enum ps_dtype
+ *   out                  receives the plan (caller frees with ps_plan_destroy)
+ * Free axes get the paper's padded length L = 2n; periodic axes L = n.
+ * Errors: PS_ERR_ARG for n < 1, h <= 0 or NaN, a bad enum or out == NULL;
+ * PS_ERR_UNSUPPORTED if a length exceeds this build's maximum (4096).
+ */
+int ps_plan_create(int n1, int n2, int n3, double h, int bc_x, int bc_y, int bc_z,
+                   int dtype, ps_plan* out);
+
+/*
+ * ps_plan_set_lengths -- override the padded length of free axes before the
+ * build. Any L >= 2n - 1 gives the same physical result (§2); a smooth length
+ * (factors 2, 3, 5, 7) is cheaper than 2n when 2n has a large prime factor.
+ * Pass 0 to keep an axis's current length. Periodic axes must keep L = n.
+ * Errors: PS_ERR_ARG (plan NULL, L too small, periodic L != n, plan built).
+ */
+int ps_plan_set_lengths(ps_plan plan, int L1, int L2, int L3);
+
+/* ps_plan_set_math -- enum ps_math; must precede the build. PS_ERR_ARG else. */
+int ps_plan_set_math(ps_plan plan, int math_mode);
+
+/* ps_plan_query -- fill *info (host only; valid before and after the build). */
+int ps_plan_query(ps_plan plan, ps_plan_info* info);
+
+/*
+ * ps_kernel_build -- allocate the workspace on the current device and build
+ * K^F there in FP64 (the Green's function of the plan's boundary conditions,
+ * transformed along the free axes; §2, §3 "transposed kernel"), then store it
+ * in the solve dtype, scaled by 1/(L1 L2 L3), as its even octant in the layout
+ * the z pass reads. Idempotent. Synchronises `stream` once to report errors.
+ * Errors: PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_ARG (plan NULL).
+ */
+int ps_kernel_build(ps_plan plan, void* stream);
+
+/*
+ * ps_kernel_get -- copy the stored K^F octant to device memory `dst`
+ * (dtype elements, layout [kz][ky][kx] with kx < L1/2+1, ky <= L2/2,
+ * kz <= L3/2, kx fastest), scaled by 1/(L1 L2 L3) as stored.
+ * Errors: PS_ERR_NOT_BUILT, PS_ERR_ARG (dst NULL), PS_ERR_CUDA.
+ */
+int ps_kernel_get(ps_plan plan, void* dst, void* stream);
+
+/*
+ * ps_solve -- V = K * rho (Eq. 2 via Eq. 3 on the padded grid), and
+ * optionally the Hartree energy E = 1/2 h^3 sum rho V.
+ *   rho           device pointer, n1*n2*n3 dtype elements (read only)
+ *   V             device pointer, n1*n2*n3 dtype elements (written); must not
+ *                 overlap rho
+ *   ehartree_dev  device pointer to one double, or NULL to skip the energy
+ * Five kernel launches on `stream`. For periodic axes the mean of rho is
+ * dropped (K^F(0) = 0).
+ * Errors: PS_ERR_ARG (NULL or aliasing pointers), PS_ERR_NOT_BUILT, PS_ERR_CUDA.
+ */
+int ps_solve(ps_plan plan, const void* rho, void* V, double* ehartree_dev, void* stream);
+
+/*
+ * ps_solve_adjoint -- rhobar = K^T vbar. K is even (K(d) = K(-d)), so the
+ * operator is symmetric and this is the same convolution; it is the
+ * vector-Jacobian product of V with respect to rho. Same pointers and errors
+ * as ps_solve, without the energy.
+ */
+int ps_solve_adjoint(ps_plan plan, const void* vbar, void* rhobar, void* stream);
+
+/*
+ * ps_solve_batched -- count independent solves, each with its own built plan
+ * (shapes, boundary conditions and dtypes may differ), enqueued on one stream.
+ * Plans of the same dtype share one launch per pass.
+ *   plans[i], rho[i], V[i]   as in ps_solve
+ *   ehartree_dev             NULL or device array of count doubles
+ * Each plan may appear at most once. Errors as ps_solve, with the index of
+ * the failing item in ps_last_error().
+ */
+int ps_solve_batched(int count, const ps_plan* plans, const void* const* rho,
+                     void* const* V, double* ehartree_dev, void* stream);
+
+/*
+ * ps_solve_host -- ps_solve on host buffers: copies rho host->device, solves,
+ * copies V and E device->host, and waits for `stream` before returning.
+ *   rho_host, V_host   host pointers, n1*n2*n3 dtype elements (pinned memory
+ *                      gives asynchronous, faster copies)
+ *   ehartree_host      host pointer to one double, or NULL
+ * The plan holds the device copies of rho and V (allocated on first use).
+ * Errors as ps_solve, plus PS_ERR_OOM.
+ */
+int ps_solve_host(ps_plan plan, const void* rho_host, void* V_host, double* ehartree_host,
+                  void* stream);
+
+/*
+ * ps_plan_set_profiling -- when enable != 0, every later solve on this plan
+ * records a CUDA event on its stream before the first pass and after each of
+ * the five passes (the per-step timers of the paper's §4 measurements, at
+ * pass granularity). Recording adds no device work and no host wait.
+ * Errors: PS_ERR_ARG (plan NULL).
+ */
+int ps_plan_set_profiling(ps_plan plan, int enable);
+
+/*
+ * ps_plan_pass_times -- waits for the events of every solve recorded since the
+ * last call, writes the summed device time of each pass in milliseconds to
+ * ms[0..4] (forward x, forward y, z, inverse y, inverse x) and the number of
+ * recorded solves to *count, then forgets them. Host pointers.
+ * Errors: PS_ERR_ARG (NULL pointer), PS_ERR_CUDA.
+ */
+int ps_plan_pass_times(ps_plan plan, double* ms, int* count);
+
+/* ps_plan_destroy -- free the plan and its device memory. NULL is a no-op. */
+int ps_plan_destroy(ps_plan plan);
+
+/* ps_strerror -- static description of a status code. */
+const char* ps_strerror(int status);
+
+/* ps_last_error -- detail of the last error on the calling thread ("" if none). */
+const char* ps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSOLVER_H */

@@ -51,7 +51,7 @@ from scipy import integrate, special
 
 __all__ = [
     "C2", "C3", "padded_lengths", "green_mixed", "kernel_fourier",
-    "kernel_fourier_octant", "solve", "brute_force", "hartree_energy",
+    "kernel_fourier_octant", "solve", "brute_force", "direct_at", "hartree_energy",
 ]
 
 # Cell average of 1/|u| over the unit cube centred at the origin:
@@ -270,3 +270,22 @@ def brute_force(rho, bc, h):
     if per:
         return np.fft.ifftn(Vhat, axes=per_np_axes).real
     return Vhat.real
+
+
+def direct_at(rho, h, points):
+    """Eq. 2 evaluated literally at selected grid points, free BCs on all axes:
+    V(t) = sum_r' K(t - r') rho(r') for each t = (k, j, i) in ``points``
+    (numpy index order z, y, x). O(N) per point, summed slab by slab."""
+    rho = np.asarray(rho, dtype=np.float64)
+    n3, n2, n1 = rho.shape
+    y = np.arange(n2, dtype=np.float64)[:, None]
+    x = np.arange(n1, dtype=np.float64)[None, :]
+    out = []
+    for tz, ty, tx in points:
+        dyx2 = (ty - y) ** 2 + (tx - x) ** 2
+        acc = 0.0
+        for k in range(n3):
+            K = green_mixed(0, 0.0, np.sqrt((tz - k) ** 2 + dyx2), h)
+            acc += float(np.sum(K * rho[k]))
+        out.append(acc)
+    return np.array(out)

@@ -1,0 +1,387 @@
+// C ABI of libpsolver: argument checking, plan bookkeeping, device memory, and
+// the sequence of launches of one solve. All arithmetic runs in the kernels of
+// passes.cu and kernel_build.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace ps {
+
+static thread_local char g_err[512];
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+namespace {
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_error("%s", buf);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(PS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(PS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (dev < 0) return;
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+void free_device(ps_plan_s* p) {
+  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2],
+                   reinterpret_cast<void**>(&p->partials), reinterpret_cast<void**>(&p->counter),
+                   &p->d_rho, &p->d_V, reinterpret_cast<void**>(&p->d_E)};
+  for (void** b : bufs) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  p->built = false;
+  p->ws_bytes = 0;
+}
+
+size_t grid_points(const ps_plan_s* p) { return (size_t)p->n[0] * p->n[1] * p->n[2]; }
+
+bool overlap(const void* a, const void* b, size_t bytes) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+int check_solve_args(ps_plan p, const void* in, const void* out) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (!in || !out) return fail(PS_ERR_ARG, "input or output pointer is NULL");
+  if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
+  const size_t bytes = grid_points(p) * p->esz;
+  if (overlap(in, out, bytes)) return fail(PS_ERR_ARG, "input and output overlap");
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % p->esz)
+    return fail(PS_ERR_ARG, "pointers must be aligned to the element size");
+  return PS_OK;
+}
+
+int run_solve(ps_plan p, const void* rho, void* V, double* E, cudaStream_t s) {
+  cudaError_t e;
+  cudaEvent_t* ev = nullptr;
+  if (p->profiling) {
+    while (p->events.size() < p->events_used + 6) {
+      cudaEvent_t x;
+      if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(e, "profiling event");
+      p->events.push_back(x);
+    }
+    ev = p->events.data() + p->events_used;
+    p->events_used += 6;
+  }
+  if (p->dtype == PS_F32)
+    e = launch_solve<float>(p, static_cast<const float*>(rho), static_cast<float*>(V), E, s, ev);
+  else
+    e = launch_solve<double>(p, static_cast<const double*>(rho), static_cast<double*>(V), E, s, ev);
+  if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+  return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ps_plan_create(int n1, int n2, int n3, double h, int bc_x, int bc_y, int bc_z, int dtype,
+                   ps_plan* out) {
+  set_error("%s", "");
+  if (!out) return fail(PS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  const int n[3] = {n1, n2, n3};
+  const int bc[3] = {bc_x, bc_y, bc_z};
+  for (int j = 0; j < 3; ++j) {
+    if (n[j] < 1) return fail(PS_ERR_ARG, "n%d = %d must be >= 1", j + 1, n[j]);
+    if (bc[j] != PS_BC_PERIODIC && bc[j] != PS_BC_FREE) return fail(PS_ERR_ARG, "bad bc on axis %d", j);
+  }
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(PS_ERR_ARG, "h must be finite and > 0");
+  if (dtype != PS_F32 && dtype != PS_F64) return fail(PS_ERR_ARG, "bad dtype %d", dtype);
+  ps_plan_s* p = new (std::nothrow) ps_plan_s();
+  if (!p) return fail(PS_ERR_OOM, "host allocation failed");
+  for (int j = 0; j < 3; ++j) {
+    p->n[j] = n[j];
+    p->bc[j] = bc[j];
+    p->L[j] = bc[j] == PS_BC_FREE ? 2 * n[j] : n[j];  // §3: S_j = N_j B_j
+  }
+  p->h = h;
+  p->dtype = dtype;
+  p->math = PS_MATH_CUDACORE;
+  p->esz = dtype == PS_F32 ? 4 : 8;
+  p->device = -1;
+  const int rc = ps_plan_set_lengths(p, 0, 0, 0);  // validates lengths, derives c, H, stages
+  if (rc != PS_OK) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return PS_OK;
+}
+
+int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (p->built) return fail(PS_ERR_ARG, "lengths must be set before ps_kernel_build");
+  const int Lr[3] = {L1, L2, L3};
+  int L[3];
+  for (int j = 0; j < 3; ++j) {
+    L[j] = Lr[j] > 0 ? Lr[j] : p->L[j];
+    if (p->bc[j] == PS_BC_PERIODIC && L[j] != p->n[j])
+      return fail(PS_ERR_ARG, "periodic axis %d must keep L = n", j);
+    if (p->bc[j] == PS_BC_FREE && L[j] < 2 * p->n[j] - 1)
+      return fail(PS_ERR_ARG, "free axis %d needs L >= 2n - 1", j);
+    if (L[j] > kMaxLen) return fail(PS_ERR_UNSUPPORTED, "length %d exceeds %d", L[j], kMaxLen);
+  }
+  for (int j = 0; j < 3; ++j) {
+    p->L[j] = L[j];
+    p->H[j] = L[j] / 2;
+  }
+  p->c = p->L[0] / 2 + 1;
+  const bool even1 = p->L[0] % 2 == 0;
+  p->st[0] = factorize(even1 ? p->L[0] / 2 : p->L[0]);
+  p->st[1] = factorize(p->L[1]);
+  p->st[2] = factorize(p->L[2]);
+  p->ldc = round_up((size_t)p->c, p->dtype == PS_F32 ? 16 : 8);
+  return PS_OK;
+}
+
+int ps_plan_set_math(ps_plan p, int math_mode) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (p->built) return fail(PS_ERR_ARG, "math mode must be set before ps_kernel_build");
+  if (math_mode != PS_MATH_CUDACORE) return fail(PS_ERR_ARG, "unknown math mode %d", math_mode);
+  p->math = math_mode;
+  return PS_OK;
+}
+
+int ps_plan_query(ps_plan p, ps_plan_info* info) {
+  if (!p || !info) return fail(PS_ERR_ARG, "plan or info is NULL");
+  memset(info, 0, sizeof *info);
+  for (int j = 0; j < 3; ++j) {
+    info->n[j] = p->n[j];
+    info->bc[j] = p->bc[j];
+    info->L[j] = p->L[j];
+  }
+  info->c = p->c;
+  info->dtype = p->dtype;
+  info->math = p->math;
+  const long long n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+  const long long L1 = p->L[0], L2 = p->L[1], L3 = p->L[2], c = p->c;
+  info->lines[0] = n2 * n3;  info->line_len[0] = L1;
+  info->lines[1] = c * n3;   info->line_len[1] = L2;
+  info->lines[2] = c * L2;   info->line_len[2] = L3;
+  info->lines[3] = c * n3;   info->line_len[3] = L2;
+  info->lines[4] = n2 * n3;  info->line_len[4] = L1;
+  double pts = 0.0;
+  for (int k = 0; k < 5; ++k) pts += (double)info->lines[k] * (double)info->line_len[k];
+  pts += (double)info->lines[2] * (double)info->line_len[2];  // z: forward and inverse
+  info->fft_points = pts;
+  // §3 count of one forward 3D transform: rows x length per step, complex rows
+  info->paper_points = (double)(n2 * n3 * L1) + (double)(L1 * n3 * L2) + (double)(L1 * L2 * L3);
+  info->paper_full_points = 3.0 * (double)(L1 * L2 * L3);
+  const double b = (double)p->esz;
+  info->alg_bytes = 2.0 * (double)(n1 * n2 * n3) * b + 8.0 * b * (double)(c * n3 * (n2 + L2)) +
+                    b * (double)c * (double)(p->H[1] + 1) * (double)(p->H[2] + 1);
+  info->workspace_bytes = p->ws_bytes;
+  return PS_OK;
+}
+
+int ps_kernel_build(ps_plan p, void* stream) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (p->built) return PS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  p->device = dev;
+  e = p->dtype == PS_F32 ? configure_passes<float>(p) : configure_passes<double>(p);
+  if (e != cudaSuccess) return cuda_fail(e, "configure passes");
+  const size_t csz = 2 * p->esz;
+  const size_t n2 = p->n[1], n3 = p->n[2];
+  const size_t szA = p->ldc * n2 * n3 * csz;
+  const size_t szB = p->ldc * (size_t)p->L[1] * n3 * csz;
+  const size_t szK = (size_t)p->c * (p->H[1] + 1) * (p->H[2] + 1) * p->esz;
+  struct { void** ptr; size_t bytes; const char* what; } allocs[] = {
+      {&p->A, szA, "workspace A"},
+      {&p->B, szB, "workspace B"},
+      {&p->K, szK, "K^F"},
+      {&p->tw[0], (size_t)p->L[0] * csz, "twiddles x"},
+      {&p->tw[1], (size_t)p->L[1] * csz, "twiddles y"},
+      {&p->tw[2], (size_t)p->L[2] * csz, "twiddles z"},
+      {reinterpret_cast<void**>(&p->partials), (size_t)p->npart * sizeof(double), "energy partials"},
+      {reinterpret_cast<void**>(&p->counter), sizeof(unsigned), "energy counter"},
+  };
+  size_t total = 0;
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.ptr, a.bytes);
+    if (e != cudaSuccess) {
+      free_device(p);
+      return cuda_fail(e, a.what);
+    }
+    total += a.bytes;
+  }
+  p->ws_bytes = total;
+  e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = build_twiddles(p, s);
+  if (e == cudaSuccess) e = build_kernel(p, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_device(p);
+    return cuda_fail(e, "kernel build");
+  }
+  p->built = true;
+  return PS_OK;
+}
+
+int ps_kernel_get(ps_plan p, void* dst, void* stream) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
+  if (!dst) return fail(PS_ERR_ARG, "dst is NULL");
+  DeviceGuard g(p->device);
+  const size_t bytes = (size_t)p->c * (p->H[1] + 1) * (p->H[2] + 1) * p->esz;
+  cudaError_t e = cudaMemcpyAsync(dst, p->K, bytes, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "copy K^F");
+  return PS_OK;
+}
+
+int ps_solve(ps_plan p, const void* rho, void* V, double* ehartree_dev, void* stream) {
+  int rc = check_solve_args(p, rho, V);
+  if (rc != PS_OK) return rc;
+  DeviceGuard g(p->device);
+  return run_solve(p, rho, V, ehartree_dev, static_cast<cudaStream_t>(stream));
+}
+
+int ps_solve_adjoint(ps_plan p, const void* vbar, void* rhobar, void* stream) {
+  int rc = check_solve_args(p, vbar, rhobar);
+  if (rc != PS_OK) return rc;
+  DeviceGuard g(p->device);
+  return run_solve(p, vbar, rhobar, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int ps_solve_batched(int count, const ps_plan* plans, const void* const* rho, void* const* V,
+                     double* ehartree_dev, void* stream) {
+  if (count < 0) return fail(PS_ERR_ARG, "count < 0");
+  if (count == 0) return PS_OK;
+  if (!plans || !rho || !V) return fail(PS_ERR_ARG, "NULL array argument");
+  for (int i = 0; i < count; ++i) {
+    int rc = check_solve_args(plans[i], rho[i], V[i]);
+    if (rc != PS_OK) return fail(rc, "item %d: %s", i, ps_last_error());
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(PS_ERR_ARG, "item %d: plan repeated (item %d)", i, j);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    DeviceGuard g(plans[i]->device);
+    int rc = run_solve(plans[i], rho[i], V[i], ehartree_dev ? ehartree_dev + i : nullptr, s);
+    if (rc != PS_OK) return fail(rc, "item %d: %s", i, ps_last_error());
+  }
+  return PS_OK;
+}
+
+int ps_solve_host(ps_plan p, const void* rho_host, void* V_host, double* ehartree_host, void* stream) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (!rho_host || !V_host) return fail(PS_ERR_ARG, "host pointer is NULL");
+  if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
+  DeviceGuard g(p->device);
+  const size_t bytes = grid_points(p) * p->esz;
+  cudaError_t e;
+  if (!p->d_rho) {
+    if ((e = cudaMalloc(&p->d_rho, bytes)) != cudaSuccess) return cuda_fail(e, "staging rho");
+    if ((e = cudaMalloc(&p->d_V, bytes)) != cudaSuccess) return cuda_fail(e, "staging V");
+    if ((e = cudaMalloc(&p->d_E, sizeof(double))) != cudaSuccess) return cuda_fail(e, "staging E");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((e = cudaMemcpyAsync(p->d_rho, rho_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "copy rho to device");
+  int rc = run_solve(p, p->d_rho, p->d_V, ehartree_host ? p->d_E : nullptr, s);
+  if (rc != PS_OK) return rc;
+  if ((e = cudaMemcpyAsync(V_host, p->d_V, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "copy V to host");
+  if (ehartree_host &&
+      (e = cudaMemcpyAsync(ehartree_host, p->d_E, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "copy E to host");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "solve");
+  return PS_OK;
+}
+
+int ps_plan_set_profiling(ps_plan p, int enable) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  p->profiling = enable != 0;
+  return PS_OK;
+}
+
+int ps_plan_pass_times(ps_plan p, double* ms, int* count) {
+  if (!p || !ms || !count) return fail(PS_ERR_ARG, "NULL argument");
+  for (int k = 0; k < 5; ++k) ms[k] = 0.0;
+  *count = (int)(p->events_used / 6);
+  if (p->events_used == 0) return PS_OK;
+  DeviceGuard g(p->device);
+  cudaError_t e = cudaEventSynchronize(p->events[p->events_used - 1]);
+  if (e != cudaSuccess) return cuda_fail(e, "profiling wait");
+  for (size_t i = 0; i + 6 <= p->events_used; i += 6) {
+    for (int k = 0; k < 5; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, p->events[i + k], p->events[i + k + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "profiling elapsed time");
+      ms[k] += t;
+    }
+  }
+  p->events_used = 0;
+  return PS_OK;
+}
+
+int ps_plan_destroy(ps_plan p) {
+  if (!p) return PS_OK;
+  {
+    DeviceGuard g(p->device);
+    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    p->events.clear();
+    free_device(p);
+  }
+  delete p;
+  return PS_OK;
+}
+
+const char* ps_strerror(int status) {
+  switch (status) {
+    case PS_OK: return "success";
+    case PS_ERR_ARG: return "invalid argument";
+    case PS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PS_ERR_NOT_BUILT: return "kernel not built (call ps_kernel_build)";
+    case PS_ERR_CUDA: return "CUDA error";
+    case PS_ERR_OOM: return "out of device memory";
+    case PS_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* ps_last_error(void) { return ps::g_err; }
+
+}  // extern "C"

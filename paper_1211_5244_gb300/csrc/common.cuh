@@ -1,0 +1,131 @@
+// Internal definitions shared by the CUDA translation units of libpsolver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "psolver.h"
+
+namespace ps {
+
+// ---------------------------------------------------------------- complex
+
+template <typename T> struct CT;
+template <> struct CT<float> { using type = float2; };
+template <> struct CT<double> { using type = double2; };
+template <typename T> using cpx = typename CT<T>::type;
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+// multiply by +i (s = +1) or -i (s = -1)
+template <int S, typename C> __device__ __forceinline__ C cmul_i(C a) {
+  return S > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) {
+  return mk(a.x * s, a.y * s);
+}
+
+// ---------------------------------------------------------------- radix plans
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxLen = 4096;
+
+// Factorisation of a transform length into Stockham stages (radix per stage).
+struct Stages {
+  int n;                 // number of stages (0 for length 1)
+  int R[kMaxStages];
+};
+
+// ---------------------------------------------------------------- plan
+
+enum Pass { P1 = 0, P2 = 1, P3 = 2, P4 = 3, P5 = 4 };
+
+// Arguments of the specialised FP32 pass kernels (strides in complex elements).
+struct FastArgs {
+  int c;                  // valid kx columns (L1/2 + 1)
+  int L1, L2;
+  int n1, nrows;          // x passes: row length (reals) and row count
+  long long ldc;          // row pitch of A / B
+  long long src_plane, src_elem;
+  long long dst_plane, dst_elem;
+  long long kz_stride;    // z pass: (L2/2 + 1) * c, the kz stride of the K^F octant
+};
+
+struct PassCfg {
+  int tk;       // lines (tile width) per CTA
+  int ldt;      // shared-memory row stride in complex elements
+  int threads;  // threads per CTA
+  size_t smem;  // dynamic shared memory bytes
+  int fast;     // 1 if a compile-time specialised kernel runs this pass
+  const void* fn;  // the specialised kernel
+  dim3 grid, block;
+  FastArgs fa;
+};
+
+}  // namespace ps
+
+struct ps_plan_s {
+  int n[3];
+  int bc[3];
+  int L[3];
+  int H[3];      // L/2 (floor): last index of the even octant per axis
+  int c;         // L1/2 + 1
+  double h;
+  int dtype;
+  int math;
+  bool built;
+  int device;
+  size_t esz;    // bytes per real element
+  size_t ldc;    // row pitch of the spectral work arrays, complex elements
+  // device memory owned by the plan
+  void* A;       // [n3][n2][ldc] complex: x-transformed rows (passes 1/2 and 4/5)
+  void* B;       // [n3][L2][ldc] complex: y-transformed planes (passes 2..4)
+  void* K;       // [H3+1][H2+1][c] real: K^F / (L1 L2 L3), even octant
+  void* tw[3];   // W_{L_j}^k, k < L_j, complex, per axis
+  double* partials;     // per-CTA energy partials of the z pass
+  unsigned* counter;    // arrival counter for the last-CTA energy reduction
+  int npart;
+  void* d_rho;   // staging for ps_solve_host
+  void* d_V;
+  double* d_E;
+  size_t ws_bytes;
+  ps::Stages st[3];     // stages of the 1D transform per axis (x: length L1/2 if L1 even)
+  ps::PassCfg cfg[5];
+  // per-pass timing (ps_plan_set_profiling): 6 events per recorded solve
+  bool profiling;
+  std::vector<cudaEvent_t> events;
+  size_t events_used;
+};
+
+namespace ps {
+
+// Error reporting (thread-local message), defined in api.cu.
+void set_error(const char* fmt, ...);
+
+// Radix factorisation used by the generic kernels.
+Stages factorize(int N);
+
+// Launchers (defined in passes.cu / kernel_build.cu). They only enqueue.
+template <typename T>
+cudaError_t configure_passes(ps_plan_s* p);
+template <typename T>
+cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream_t s,
+                         cudaEvent_t* ev);
+cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s);
+cudaError_t build_kernel(ps_plan_s* p, cudaStream_t s);
+
+}  // namespace ps

@@ -1,0 +1,262 @@
+// Specialised FP32 kernels for the x passes (real-to-complex forward,
+// complex-to-real inverse, §3), real length L1 = 2M with M a power of two.
+//
+// A real row x of length L1 is transformed as the complex sequence
+// z[m] = x[2m] + i x[2m+1] of length M (four-step, as in fast_strided.cu),
+// then X[k] = E[k] + W_L1^k O[k] with E = (Z[k] + conj Z[M-k]) / 2 and
+// O = -i (Z[k] - conj Z[M-k]) / 2 for k = 0..M; the L1/2 + 1 outputs are all
+// the half spectrum keeps (§3). The inverse builds Z[k] = (X[k] + conj X[M-k])
+// + i (X[k] - conj X[M-k]) W_L1^{-k} and transforms it back, which gives the
+// unnormalised length-L1 inverse at even (real part) and odd (imaginary part)
+// positions. T lanes own one row (contiguous 8-byte elements), so loads and
+// stores are coalesced along the row. With zero padding (n1 = M), inputs
+// z[m] with m >= M/2 are zero and outputs there are never formed.
+#include "fft_fast.cuh"
+#include "fft_regs.cuh"
+
+namespace ps {
+
+using regs::rdft;
+
+__device__ __forceinline__ float2 xmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 xmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// shared memory per row: exchange tile P x (Q + 1) and the row spectrum (M + 1)
+template <int P, int Q>
+struct XShape {
+  static constexpr int M = P * Q;
+  static constexpr int T = P < Q ? P : Q;
+  static constexpr int EX = P * (Q + 1);
+  static constexpr int ROW = EX + M + 1;
+};
+
+template <int P, int Q, int TR, bool HALF>
+__global__ void __launch_bounds__(TR*(P < Q ? P : Q))
+    k_x_r2c(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a,
+            double*, unsigned*, double, double*) {
+  using S = XShape<P, Q>;
+  constexpr int M = S::M, T = S::T, NB = Q / T, NK = P / T;
+  constexpr int NA = HALF ? P / 2 : P;
+  extern __shared__ float2 sh[];
+  const int r = threadIdx.x / T, j = threadIdx.x % T;
+  const int row = blockIdx.x * TR + r;
+  const bool valid = row < a.nrows;
+  float2* ex = sh + r * S::ROW;
+  float2* zr = ex + S::EX;
+  const float2* z = reinterpret_cast<const float2*>(static_cast<const float*>(src_v) + (long long)row * a.n1);
+  float2* X = static_cast<float2*>(dst_v) + (long long)row * a.ldc;
+
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int b = j + T * u;
+    float2 y[P];
+#pragma unroll
+    for (int aa = 0; aa < P; ++aa) {
+      y[aa] = make_float2(0.f, 0.f);
+      if (aa < NA && valid) y[aa] = z[b + Q * aa];
+    }
+    rdft<P, -1, HALF>(y);
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) y[k1] = xmul(y[k1], __ldg(&tw[2 * b * k1]));  // W_M^{b k1}
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) ex[k1 * (Q + 1) + b] = y[k1];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int k1 = j + T * v;
+    float2 x[Q];
+#pragma unroll
+    for (int b = 0; b < Q; ++b) x[b] = ex[k1 * (Q + 1) + b];
+    rdft<Q, -1, false>(x);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) zr[k1 + P * k2] = x[k2];
+  }
+  __syncthreads();
+  if (!valid) return;
+  for (int k = j; k <= M; k += T) {
+    const float2 zk = zr[k == M ? 0 : k];
+    const float2 zm = zr[k == 0 ? 0 : M - k];
+    const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    const float2 wo = xmul(o, __ldg(&tw[k]));
+    X[k] = make_float2(e.x + wo.x, e.y + wo.y);
+  }
+}
+
+template <int P, int Q, int TR, bool HALF>
+__global__ void __launch_bounds__(TR*(P < Q ? P : Q))
+    k_x_c2r(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a,
+            double*, unsigned*, double, double*) {
+  using S = XShape<P, Q>;
+  constexpr int M = S::M, T = S::T, NB = Q / T, NK = P / T;
+  constexpr int NA = HALF ? P / 2 : P;
+  extern __shared__ float2 sh[];
+  const int r = threadIdx.x / T, j = threadIdx.x % T;
+  const int row = blockIdx.x * TR + r;
+  const bool valid = row < a.nrows;
+  float2* ex = sh + r * S::ROW;
+  float2* xr = ex + S::EX;
+  const float2* X = static_cast<const float2*>(src_v) + (long long)row * a.ldc;
+  float2* z = reinterpret_cast<float2*>(static_cast<float*>(dst_v) + (long long)row * a.n1);
+
+  for (int k = j; k <= M; k += T) xr[k] = valid ? X[k] : make_float2(0.f, 0.f);
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int k1 = j + T * v;
+    float2 x[Q];
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const int k = k1 + P * k2;
+      const float2 xk = xr[k], xm = xr[M - k];
+      const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
+      const float2 o = xmulc(make_float2(xk.x - xm.x, xk.y + xm.y), __ldg(&tw[k]));
+      x[k2] = make_float2(e.x - o.y, e.y + o.x);
+    }
+    rdft<Q, 1, false>(x);
+#pragma unroll
+    for (int b = 1; b < Q; ++b) x[b] = xmulc(x[b], __ldg(&tw[2 * b * k1]));
+#pragma unroll
+    for (int b = 0; b < Q; ++b) ex[k1 * (Q + 1) + b] = x[b];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int b = j + T * u;
+    float2 y[P];
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) y[k1] = ex[k1 * (Q + 1) + b];
+    rdft<P, 1, false>(y);
+    if (valid) {
+#pragma unroll
+      for (int aa = 0; aa < NA; ++aa) z[b + Q * aa] = y[aa];
+    }
+  }
+}
+
+template <int P, int Q, int TR>
+static const void* pick_x(int kind, bool half) {
+  if (kind == 0) return half ? (const void*)k_x_r2c<P, Q, TR, true> : (const void*)k_x_r2c<P, Q, TR, false>;
+  return half ? (const void*)k_x_c2r<P, Q, TR, true> : (const void*)k_x_c2r<P, Q, TR, false>;
+}
+
+const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, size_t* smem) {
+  const void* fn = nullptr;
+  int T = 0, TR = 0, ROW = 0;
+  switch (M) {
+    case 32: fn = pick_x<8, 4, 32>(kind, half); T = 4; TR = 32; ROW = XShape<8, 4>::ROW; break;
+    case 64: fn = pick_x<8, 8, 32>(kind, half); T = 8; TR = 32; ROW = XShape<8, 8>::ROW; break;
+    case 128: fn = pick_x<16, 8, 32>(kind, half); T = 8; TR = 32; ROW = XShape<16, 8>::ROW; break;
+    case 256: fn = pick_x<16, 16, 16>(kind, half); T = 16; TR = 16; ROW = XShape<16, 16>::ROW; break;
+    case 512: fn = pick_x<32, 16, 8>(kind, half); T = 16; TR = 8; ROW = XShape<32, 16>::ROW; break;
+    default: return nullptr;
+  }
+  *threads = T * TR;
+  *rows = TR;
+  *smem = (size_t)TR * ROW * sizeof(float2);
+  return fn;
+}
+
+// ---------------------------------------------------------------- selection
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+cudaError_t configure_fast_f32(ps_plan_s* p) {
+  const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+  const int L1 = p->L[0], L2 = p->L[1], L3 = p->L[2];
+  const long long ldc = (long long)p->ldc;
+  cudaError_t e;
+  auto set = [&](int pass, const void* fn, dim3 grid, int threads, size_t smem, const FastArgs& fa) -> cudaError_t {
+    if (!fn) return cudaSuccess;
+    if (smem > 48 * 1024) {
+      cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+    }
+    PassCfg& cf = p->cfg[pass];
+    cf.fast = 1;
+    cf.fn = fn;
+    cf.grid = grid;
+    cf.block = dim3(threads);
+    cf.smem = smem;
+    cf.fa = fa;
+    return cudaSuccess;
+  };
+  FastArgs base{};
+  base.c = p->c;
+  base.L1 = L1;
+  base.L2 = L2;
+  base.n1 = n1;
+  base.nrows = n2 * n3;
+  base.ldc = ldc;
+  base.kz_stride = (long long)(p->H[1] + 1) * p->c;
+  const int ntk = (p->c + 15) / 16;
+
+  // x passes: L1 = 2M, n1 = M (free) or 2M (periodic)
+  if (L1 % 2 == 0 && pow2(L1 / 2) && (n1 == L1 / 2 || n1 == L1) && n1 % 2 == 0) {
+    const int M = L1 / 2;
+    const bool half = n1 == M;
+    int threads, rows;
+    size_t smem;
+    const void* f0 = xline_kernel(M, 0, half, &threads, &rows, &smem);
+    const void* f1 = xline_kernel(M, 1, half, &threads, &rows, &smem);
+    if (f0 && f1) {
+      dim3 grid((n2 * n3 + rows - 1) / rows);
+      if ((e = set(P1, f0, grid, threads, smem, base)) != cudaSuccess) return e;
+      if ((e = set(P5, f1, grid, threads, smem, base)) != cudaSuccess) return e;
+    }
+  }
+  // y passes
+  if (pow2(L2) && (n2 == L2 / 2 || n2 == L2)) {
+    const bool half = n2 == L2 / 2;
+    int threads;
+    size_t smem;
+    const void* f0 = strided_kernel(L2, 0, half, &threads, &smem);
+    const void* f1 = strided_kernel(L2, 1, half, &threads, &smem);
+    if (f0 && f1) {
+      FastArgs fwd = base, inv = base;
+      fwd.src_plane = (long long)n2 * ldc; fwd.src_elem = ldc;   // A[z][y][kx]
+      fwd.dst_plane = (long long)L2 * ldc; fwd.dst_elem = ldc;   // B[z][ky][kx]
+      inv.src_plane = (long long)L2 * ldc; inv.src_elem = ldc;
+      inv.dst_plane = (long long)n2 * ldc; inv.dst_elem = ldc;
+      dim3 grid(ntk, n3);
+      if ((e = set(P2, f0, grid, threads, smem, fwd)) != cudaSuccess) return e;
+      if ((e = set(P4, f1, grid, threads, smem, inv)) != cudaSuccess) return e;
+    }
+  }
+  // z pass
+  if (pow2(L3) && (n3 == L3 / 2 || n3 == L3)) {
+    const bool half = n3 == L3 / 2;
+    int threads;
+    size_t smem;
+    const void* f = strided_kernel(L3, 2, half, &threads, &smem);
+    if (f) {
+      FastArgs z = base;
+      z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;      // B[z][ky][kx], line along z
+      z.dst_plane = ldc; z.dst_elem = (long long)L2 * ldc;
+      dim3 grid(ntk, L2);
+      if ((e = set(P3, f, grid, threads, smem, z)) != cudaSuccess) return e;
+      p->cfg[P3].tk = 16;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, double* E, double escale,
+                        cudaStream_t s) {
+  PassCfg& cf = p->cfg[pass];
+  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
+  const float* K = static_cast<const float*>(p->K);
+  const float2* tw = static_cast<const float2*>(p->tw[axis]);
+  double* partials = p->partials;
+  unsigned* counter = p->counter;
+  void* args[] = {(void*)&src, (void*)&dst, (void*)&K, (void*)&tw, (void*)&cf.fa,
+                  (void*)&partials, (void*)&counter, (void*)&escale, (void*)&E};
+  return cudaLaunchKernel(cf.fn, cf.grid, cf.block, args, cf.smem, s);
+}
+
+}  // namespace ps

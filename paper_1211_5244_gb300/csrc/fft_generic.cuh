@@ -1,0 +1,137 @@
+// Generic tile transform: Stockham autosort FFT of any length N <= 4096 on a
+// shared-memory tile of `tk` independent lines, laid out [N][ldt] (element m
+// of line t at m * ldt + t), run by the whole CTA.
+//
+// Each stage of radix R (current sub-length Ns) takes butterfly b from the
+// inputs b + r * N / R, multiplies input r by W_N^{r * (b mod Ns) * N/(Ns R)},
+// does an R-point DFT and writes output q to ((b / Ns) * Ns * R + b mod Ns +
+// q * Ns): after the last stage the result is in natural order. Radices 2, 4
+// and 8 have closed-form butterflies; any other factor (3, 5, 7 or a prime up
+// to 4096) uses the direct R-point sum. Lanes of a warp take consecutive
+// lines t, so every shared-memory access of a warp is contiguous.
+#pragma once
+
+#include "common.cuh"
+
+namespace ps {
+
+// multiply by W^idx (DIR = -1) or its conjugate (DIR = +1); the table holds
+// W_L^k = exp(-2 pi i k / L) and is read with stride `tws` (= L / N)
+template <int DIR, typename C>
+__device__ __forceinline__ C twid(C v, const C* __restrict__ tw, int idx, int tws) {
+  C w = tw[idx * tws];
+  return DIR < 0 ? cmul(v, w) : cmulc(v, w);
+}
+
+template <int DIR, typename C>
+__device__ __forceinline__ void dft2(C& v0, C& v1) {
+  C t = v0;
+  v0 = cadd(t, v1);
+  v1 = csub(t, v1);
+}
+
+template <int DIR, typename C>
+__device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  C s02 = cadd(v0, v2), d02 = csub(v0, v2);
+  C s13 = cadd(v1, v3), d13 = csub(v1, v3);
+  C r = cmul_i<DIR>(d13);  // DIR * i * (v1 - v3)
+  v0 = cadd(s02, s13);
+  v2 = csub(s02, s13);
+  v1 = cadd(d02, r);
+  v3 = csub(d02, r);
+}
+
+// 8-point DFT: two 4-point DFTs (even / odd inputs) joined by W_8^k.
+template <int DIR, typename C>
+__device__ __forceinline__ void dft8(C* v) {
+  using R = decltype(v[0].x);
+  const R s = R(0.70710678118654752440);  // sqrt(1/2)
+  C a0 = v[0], a1 = v[2], a2 = v[4], a3 = v[6];
+  C b0 = v[1], b1 = v[3], b2 = v[5], b3 = v[7];
+  dft4<DIR>(a0, a1, a2, a3);
+  dft4<DIR>(b0, b1, b2, b3);
+  // W^1 = s (1 + DIR i), W^2 = DIR i, W^3 = s (-1 + DIR i)
+  C w1 = mk(s * (b1.x - DIR * b1.y), s * (b1.y + DIR * b1.x));
+  C w2 = cmul_i<DIR>(b2);
+  C w3 = mk(s * (-b3.x - DIR * b3.y), s * (-b3.y + DIR * b3.x));
+  v[0] = cadd(a0, b0); v[4] = csub(a0, b0);
+  v[1] = cadd(a1, w1); v[5] = csub(a1, w1);
+  v[2] = cadd(a2, w2); v[6] = csub(a2, w2);
+  v[3] = cadd(a3, w3); v[7] = csub(a3, w3);
+}
+
+// Runs all stages; `a` holds the input and is clobbered. Returns the buffer
+// (a or b) that holds the result. Ends with __syncthreads().
+template <int DIR, typename T>
+__device__ cpx<T>* stockham(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const Stages& st,
+                            const cpx<T>* __restrict__ tw, int tws) {
+  using C = cpx<T>;
+  int Ns = 1;
+  for (int s = 0; s < st.n; ++s) {
+    const int R = st.R[s];
+    const int NR = N / R;
+    const int estep = N / (Ns * R);
+    const int work = tk * NR;
+    for (int w = threadIdx.x; w < work; w += blockDim.x) {
+      const int t = w % tk;
+      const int bf = w / tk;
+      const int k = bf % Ns;
+      const int e = k * estep;  // r * e < N for every r < R
+      const int ob = (bf / Ns) * Ns * R + k;
+      const C* in = a + bf * ldt + t;
+      C* out = b + ob * ldt + t;
+      if (R == 2) {
+        C v0 = in[0], v1 = in[NR * ldt];
+        if (e) v1 = twid<DIR>(v1, tw, e, tws);
+        dft2<DIR>(v0, v1);
+        out[0] = v0;
+        out[Ns * ldt] = v1;
+      } else if (R == 4) {
+        C v0 = in[0], v1 = in[NR * ldt], v2 = in[2 * NR * ldt], v3 = in[3 * NR * ldt];
+        if (e) {
+          v1 = twid<DIR>(v1, tw, e, tws);
+          v2 = twid<DIR>(v2, tw, 2 * e, tws);
+          v3 = twid<DIR>(v3, tw, 3 * e, tws);
+        }
+        dft4<DIR>(v0, v1, v2, v3);
+        out[0] = v0;
+        out[Ns * ldt] = v1;
+        out[2 * Ns * ldt] = v2;
+        out[3 * Ns * ldt] = v3;
+      } else if (R == 8) {
+        C v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = in[r * NR * ldt];
+        if (e) {
+#pragma unroll
+          for (int r = 1; r < 8; ++r) v[r] = twid<DIR>(v[r], tw, r * e, tws);
+        }
+        dft8<DIR>(v);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) out[r * Ns * ldt] = v[r];
+      } else {
+        // direct R-point sum: output q = sum_r in_r W_N^{r (e + q N/R)}
+        for (int q = 0; q < R; ++q) {
+          const int step = e + q * NR;  // < N
+          int idx = 0;
+          C acc = mk(T(0), T(0));
+          for (int r = 0; r < R; ++r) {
+            C v = twid<DIR>(in[r * NR * ldt], tw, idx, tws);
+            acc = cadd(acc, v);
+            idx += step;
+            if (idx >= N) idx -= N;
+          }
+          out[q * Ns * ldt] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    C* tmp = a;
+    a = b;
+    b = tmp;
+    Ns *= R;
+  }
+  return a;
+}
+
+}  // namespace ps

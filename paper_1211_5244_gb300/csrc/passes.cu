@@ -1,0 +1,387 @@
+// The five passes of one solve (generic kernels for any transform length).
+//
+//   P1  forward x: zero-padded real-to-complex transform of length L1 of every
+//       x row (n2 * n3 rows; §3: no transform of all-zero rows), keeping
+//       c = L1/2 + 1 outputs                          rho -> A[z][y][kx]
+//   P2  forward y: length-L2 transform of the c * n3 lines whose n2 nonzero
+//       inputs are the physical y range               A -> B[z][ky][kx]
+//   P3  z: forward length-L3 transform of the c * L2 lines (n3 nonzeros),
+//       multiplication by K^F (Eq. 3), inverse transform, and only the n3
+//       physical outputs are kept (compaction, §3); also the energy
+//       E = 1/2 h^3 sum rho V as the Parseval sum 1/2 h^3 sum_k K^F |rho^F|^2
+//       over the padded spectrum                      B -> B (in place)
+//   P4  inverse y: length-L2 inverse of the c * n3 lines, n2 outputs kept
+//                                                     B -> A
+//   P5  inverse x: complex-to-real length-L1 inverse of the n2 * n3 rows,
+//       n1 outputs kept                               A -> V
+//
+// The spread and compaction of §3 never touch memory: a pass loads only the
+// nonzero part of a line into its shared-memory tile (the rest is zero) and
+// stores only the part that a later pass reads. The transposes of §3 are
+// replaced by tiles of `tk` lines that are adjacent in kx, the contiguous
+// axis of A and B, so every global access is a run of tk consecutive complex
+// numbers. K^F is stored once, scaled by 1/(L1 L2 L3), as its even octant in
+// the [kz][ky][kx] layout the z pass reads (§3: the transposed kernel).
+#include <cstdio>
+
+#include "common.cuh"
+#include "fft_fast.cuh"
+#include "fft_generic.cuh"
+#include "reduce.cuh"
+
+namespace ps {
+
+struct GenArgs {
+  int n1, n2, n3;
+  int L1, L2, L3;
+  int c, H2, H3;
+  int ldc;
+  int tk, ldt;
+  int N;    // transform length of this pass
+  int tws;  // twiddle-table stride (table length / N)
+  Stages st;
+};
+
+// ---------------------------------------------------------------- P1
+
+template <typename T>
+__global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx<T>* __restrict__ A,
+                                                  const cpx<T>* __restrict__ tw, GenArgs a) {
+  using C = cpx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + (a.N + 1) * a.ldt;
+  const int nrows = a.n2 * a.n3;
+  const int row0 = blockIdx.x * a.tk;
+  const bool even = (a.L1 % 2) == 0;
+  for (int w = threadIdx.x; w < a.N * a.ldt; w += blockDim.x) buf0[w] = mk(T(0), T(0));
+  __syncthreads();
+  for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
+    const int t = w / a.n1, i = w - t * a.n1;
+    const int row = row0 + t;
+    if (row < nrows) {
+      const T v = rho[(size_t)row * a.n1 + i];
+      if (even) {
+        T* f = reinterpret_cast<T*>(&buf0[(i >> 1) * a.ldt + t]);
+        f[i & 1] = v;
+      } else {
+        buf0[i * a.ldt + t] = mk(v, T(0));
+      }
+    }
+  }
+  __syncthreads();
+  C* out = stockham<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  if (even) {
+    // X[k] = E[k] + W_L^k O[k],  E = (Z[k] + conj Z[N-k]) / 2,  O = -i (Z[k] - conj Z[N-k]) / 2
+    const int N = a.N;
+    for (int w = threadIdx.x; w < a.tk * (N + 1); w += blockDim.x) {
+      const int t = w / (N + 1), k = w - t * (N + 1);
+      const int row = row0 + t;
+      if (row >= nrows) continue;
+      const C zk = out[(k == N ? 0 : k) * a.ldt + t];
+      const C zm = out[(k == 0 ? 0 : N - k) * a.ldt + t];
+      const C e = mk(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+      const C o = mk(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+      A[(size_t)row * a.ldc + k] = cadd(e, cmul(o, tw[k]));
+    }
+  } else {
+    for (int w = threadIdx.x; w < a.tk * a.c; w += blockDim.x) {
+      const int t = w / a.c, k = w - t * a.c;
+      const int row = row0 + t;
+      if (row < nrows) A[(size_t)row * a.ldc + k] = out[k * a.ldt + t];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- P2 / P4
+
+// Transform along y of the tile kx0 .. kx0 + tk - 1 at one z:
+//   DIR = -1: n2 inputs from A (rest zero), L2 outputs to B
+//   DIR = +1: L2 inputs from B, n2 outputs to A
+template <int DIR, typename T>
+__global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
+                                                  const cpx<T>* __restrict__ tw, GenArgs a) {
+  using C = cpx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + a.N * a.ldt;
+  const int kx0 = blockIdx.x * a.tk;
+  const int z = blockIdx.y;
+  const int nin = DIR < 0 ? a.n2 : a.L2;
+  const int nout = DIR < 0 ? a.L2 : a.n2;
+  const int rows_in = DIR < 0 ? a.n2 : a.L2;   // row count of the source plane
+  const int rows_out = DIR < 0 ? a.L2 : a.n2;
+  const C* s = src + (size_t)z * rows_in * a.ldc + kx0;
+  C* d = dst + (size_t)z * rows_out * a.ldc + kx0;
+  for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
+    const int t = w % a.tk, y = w / a.tk;
+    C v = mk(T(0), T(0));
+    if (y < nin && kx0 + t < a.c) v = s[(size_t)y * a.ldc + t];
+    buf0[y * a.ldt + t] = v;
+  }
+  __syncthreads();
+  C* out = stockham<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  for (int w = threadIdx.x; w < a.tk * nout; w += blockDim.x) {
+    const int t = w % a.tk, y = w / a.tk;
+    if (kx0 + t < a.c) d[(size_t)y * a.ldc + t] = out[y * a.ldt + t];
+  }
+}
+
+// ---------------------------------------------------------------- P3
+
+template <typename T>
+__global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const T* __restrict__ K,
+                                                  const cpx<T>* __restrict__ tw, GenArgs a,
+                                                  double* partials, unsigned* counter,
+                                                  double escale, double* E) {
+  using C = cpx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + a.N * a.ldt;
+  const int kx0 = blockIdx.x * a.tk;
+  const int ky = blockIdx.y;
+  const size_t zstride = (size_t)a.L2 * a.ldc;
+  C* line = Bw + (size_t)ky * a.ldc + kx0;
+  for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
+    const int t = w % a.tk, z = w / a.tk;
+    C v = mk(T(0), T(0));
+    if (z < a.n3 && kx0 + t < a.c) v = line[z * zstride + t];
+    buf0[z * a.ldt + t] = v;
+  }
+  __syncthreads();
+  C* spec = stockham<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  C* other = (spec == buf0) ? buf1 : buf0;
+  // multiply by the octant of K^F; accumulate w(kx) K |rho^F|^2 for the energy
+  const int kyo = min(ky, a.L2 - ky);
+  const T* Krow = K + (size_t)kyo * a.c + kx0;
+  const size_t kzstride = (size_t)(a.H2 + 1) * a.c;
+  T eacc = T(0);
+  for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
+    const int t = w % a.tk, kz = w / a.tk;
+    const int kx = kx0 + t;
+    C v = spec[kz * a.ldt + t];
+    if (kx < a.c) {
+      const int kzo = min(kz, a.L3 - kz);
+      const T kk = Krow[kzo * kzstride + t];
+      const T wgt = (kx == 0 || 2 * kx == a.L1) ? T(1) : T(2);
+      eacc += wgt * kk * (v.x * v.x + v.y * v.y);
+      v = cscale(v, kk);
+    } else {
+      v = mk(T(0), T(0));
+    }
+    spec[kz * a.ldt + t] = v;
+  }
+  __syncthreads();
+  C* res = stockham<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  for (int w = threadIdx.x; w < a.tk * a.n3; w += blockDim.x) {
+    const int t = w % a.tk, z = w / a.tk;
+    if (kx0 + t < a.c) line[z * zstride + t] = res[z * a.ldt + t];
+  }
+  if (E != nullptr) energy_finish((double)eacc, partials, counter, escale, E);
+}
+
+// ---------------------------------------------------------------- P5
+
+template <typename T>
+__global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, T* __restrict__ V,
+                                                  const cpx<T>* __restrict__ tw, GenArgs a) {
+  using C = cpx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + (a.N + 1) * a.ldt;
+  const int nrows = a.n2 * a.n3;
+  const int row0 = blockIdx.x * a.tk;
+  const bool even = (a.L1 % 2) == 0;
+  for (int w = threadIdx.x; w < a.tk * a.c; w += blockDim.x) {
+    const int t = w / a.c, k = w - t * a.c;
+    const int row = row0 + t;
+    C v = mk(T(0), T(0));
+    if (row < nrows) v = A[(size_t)row * a.ldc + k];
+    buf0[k * a.ldt + t] = v;
+  }
+  __syncthreads();
+  const int N = a.N;
+  if (even) {
+    // Z[k] = E' + i O',  E' = X[k] + conj X[N-k],  O' = (X[k] - conj X[N-k]) conj(W_L^k)
+    for (int w = threadIdx.x; w < a.tk * N; w += blockDim.x) {
+      const int t = w % a.tk, k = w / a.tk;
+      const C xk = buf0[k * a.ldt + t];
+      const C xm = buf0[(N - k) * a.ldt + t];
+      const C e = mk(xk.x + xm.x, xk.y - xm.y);
+      const C o = cmulc(mk(xk.x - xm.x, xk.y + xm.y), tw[k]);
+      buf1[k * a.ldt + t] = mk(e.x - o.y, e.y + o.x);
+    }
+  } else {
+    for (int w = threadIdx.x; w < a.tk * N; w += blockDim.x) {
+      const int t = w % a.tk, k = w / a.tk;
+      buf1[k * a.ldt + t] = k < a.c ? buf0[k * a.ldt + t] : cconj(buf0[(N - k) * a.ldt + t]);
+    }
+  }
+  __syncthreads();
+  C* out = stockham<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, tw, a.tws);
+  for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
+    const int t = w / a.n1, i = w - t * a.n1;
+    const int row = row0 + t;
+    if (row >= nrows) continue;
+    T v;
+    if (even) {
+      const C zz = out[(i >> 1) * a.ldt + t];
+      v = (i & 1) ? zz.y : zz.x;
+    } else {
+      v = out[i * a.ldt + t].x;
+    }
+    V[(size_t)row * a.n1 + i] = v;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+Stages factorize(int N) {
+  Stages s;
+  s.n = 0;
+  int m = N;
+  int twos = 0;
+  while (m % 2 == 0) { m /= 2; ++twos; }
+  // powers of two: as many radix-8 stages as possible, the rest as 4 or 2
+  int eights = twos / 3, rest = twos % 3;
+  if (rest == 1 && eights > 0) { --eights; s.R[s.n++] = 4; s.R[s.n++] = 4; rest = 0; }
+  for (int i = 0; i < eights; ++i) s.R[s.n++] = 8;
+  if (rest == 1) s.R[s.n++] = 2;
+  if (rest == 2) s.R[s.n++] = 4;
+  for (int p = 3; m > 1; p += 2) {
+    while (m % p == 0) { s.R[s.n++] = p; m /= p; }
+    if (p * p > m && m > 1) { s.R[s.n++] = m; m = 1; }
+  }
+  return s;
+}
+
+static int pick_tk(int rows, int nbuf, size_t csz, int tk0, size_t budget, int* ldt, size_t* smem) {
+  for (int tk = tk0; tk >= 1; tk /= 2) {
+    const int l = tk + 1;
+    const size_t b = (size_t)nbuf * rows * l * csz;
+    if (b <= budget) { *ldt = l; *smem = b; return tk; }
+  }
+  return 0;
+}
+
+template <typename T>
+static GenArgs gen_args(const ps_plan_s* p, int pass) {
+  GenArgs a;
+  a.n1 = p->n[0]; a.n2 = p->n[1]; a.n3 = p->n[2];
+  a.L1 = p->L[0]; a.L2 = p->L[1]; a.L3 = p->L[2];
+  a.c = p->c; a.H2 = p->H[1]; a.H3 = p->H[2];
+  a.ldc = (int)p->ldc;
+  a.tk = p->cfg[pass].tk; a.ldt = p->cfg[pass].ldt;
+  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
+  const bool even1 = (p->L[0] % 2) == 0;
+  a.N = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
+  a.tws = p->L[axis] / a.N;
+  a.st = p->st[axis];
+  return a;
+}
+
+template <typename T>
+cudaError_t configure_passes(ps_plan_s* p) {
+  using C = cpx<T>;
+  const size_t budget = 200 * 1024;
+  const int tk0 = sizeof(T) == 4 ? 16 : 8;
+  const bool even1 = (p->L[0] % 2) == 0;
+  const int N0 = even1 ? p->L[0] / 2 : p->L[0];
+  const int rows[5] = {N0 + 1, p->L[1], p->L[2], p->L[1], N0 + 1};
+  for (int k = 0; k < 5; ++k) {
+    PassCfg& cf = p->cfg[k];
+    cf.threads = 256;
+    cf.fast = 0;
+    cf.tk = pick_tk(rows[k], 2, sizeof(C), tk0, budget, &cf.ldt, &cf.smem);
+    if (cf.tk == 0) {
+      set_error("transform length %d needs more shared memory than a CTA has", rows[k]);
+      return cudaErrorInvalidConfiguration;
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(p1_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(py_generic<-1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(py_generic<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(pz_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(p5_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    e = configure_fast_f32(p);
+    if (e != cudaSuccess) return e;
+  }
+  // energy partials: one per CTA of the z pass
+  const int ntk = (p->c + p->cfg[P3].tk - 1) / p->cfg[P3].tk;
+  p->npart = ntk * p->L[1];
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream_t s,
+                         cudaEvent_t* ev) {
+  using C = cpx<T>;
+  C* A = static_cast<C*>(p->A);
+  C* B = static_cast<C*>(p->B);
+  const C* tw0 = static_cast<const C*>(p->tw[0]);
+  const C* tw1 = static_cast<const C*>(p->tw[1]);
+  const C* tw2 = static_cast<const C*>(p->tw[2]);
+  const int nrows = p->n[1] * p->n[2];
+  const double escale = 0.5 * p->h * p->h * p->h;
+
+  // the x-pass kernels read and write 8-byte pairs of reals
+  const bool a8 = ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(V)) & 7) == 0;
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], s);
+  // P1
+  if (p->cfg[P1].fast && a8) {
+    if ((e = launch_fast(p, P1, rho, A, nullptr, 0.0, s)) != cudaSuccess) return e;
+  } else {
+    GenArgs a = gen_args<T>(p, P1);
+    p1_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P1].threads, p->cfg[P1].smem, s>>>(rho, A, tw0, a);
+  }
+  if (ev) cudaEventRecord(ev[1], s);
+  // P2
+  if (p->cfg[P2].fast) {
+    if ((e = launch_fast(p, P2, A, B, nullptr, 0.0, s)) != cudaSuccess) return e;
+  } else {
+    GenArgs a = gen_args<T>(p, P2);
+    dim3 g((p->c + a.tk - 1) / a.tk, p->n[2]);
+    py_generic<-1, T><<<g, p->cfg[P2].threads, p->cfg[P2].smem, s>>>(A, B, tw1, a);
+  }
+  if (ev) cudaEventRecord(ev[2], s);
+  // P3
+  if (p->cfg[P3].fast) {
+    if ((e = launch_fast(p, P3, B, B, E, escale, s)) != cudaSuccess) return e;
+  } else {
+    GenArgs a = gen_args<T>(p, P3);
+    dim3 g((p->c + a.tk - 1) / a.tk, p->L[1]);
+    pz_generic<T><<<g, p->cfg[P3].threads, p->cfg[P3].smem, s>>>(
+        B, static_cast<const T*>(p->K), tw2, a, p->partials, p->counter, escale, E);
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  // P4
+  if (p->cfg[P4].fast) {
+    if ((e = launch_fast(p, P4, B, A, nullptr, 0.0, s)) != cudaSuccess) return e;
+  } else {
+    GenArgs a = gen_args<T>(p, P4);
+    dim3 g((p->c + a.tk - 1) / a.tk, p->n[2]);
+    py_generic<1, T><<<g, p->cfg[P4].threads, p->cfg[P4].smem, s>>>(B, A, tw1, a);
+  }
+  if (ev) cudaEventRecord(ev[4], s);
+  // P5
+  if (p->cfg[P5].fast && a8) {
+    if ((e = launch_fast(p, P5, A, V, nullptr, 0.0, s)) != cudaSuccess) return e;
+  } else {
+    GenArgs a = gen_args<T>(p, P5);
+    p5_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P5].threads, p->cfg[P5].smem, s>>>(A, V, tw0, a);
+  }
+  if (ev) cudaEventRecord(ev[5], s);
+  return cudaGetLastError();
+}
+
+template cudaError_t configure_passes<float>(ps_plan_s*);
+template cudaError_t configure_passes<double>(ps_plan_s*);
+template cudaError_t launch_solve<float>(ps_plan_s*, const float*, float*, double*, cudaStream_t,
+                                         cudaEvent_t*);
+template cudaError_t launch_solve<double>(ps_plan_s*, const double*, double*, double*, cudaStream_t,
+                                          cudaEvent_t*);
+
+}  // namespace ps

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libpsolver (include/psolver.h), same names as the C ABI.
+
+Only marshals arguments: every step of a solve runs in the library's CUDA
+kernels. PyTorch provides device memory and streams. There is no fallback:
+if the library is not built, ``load_library`` raises.
+
+Arrays are torch tensors of shape (n3, n2, n1), contiguous, x fastest, on the
+device the plan was built on, with the plan's dtype (float32 or float64).
+Boundary conditions are a 3-letter string for the x, y, z axes: 'p' periodic,
+'f' free (e.g. "pff" = wire periodic along x).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PS_BC_PERIODIC, PS_BC_FREE = 0, 1
+PS_F32, PS_F64 = 0, 1
+PS_MATH_CUDACORE = 0
+STATUS = {0: "PS_OK", 1: "PS_ERR_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_ERR_NOT_BUILT",
+          4: "PS_ERR_CUDA", 5: "PS_ERR_OOM", 6: "PS_ERR_TIMEOUT"}
+
+_lib = None
+
+
+class PsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3), ("bc", ctypes.c_int * 3), ("L", ctypes.c_int * 3),
+        ("c", ctypes.c_int), ("dtype", ctypes.c_int), ("math", ctypes.c_int),
+        ("lines", ctypes.c_longlong * 5), ("line_len", ctypes.c_longlong * 5),
+        ("fft_points", ctypes.c_double), ("paper_points", ctypes.c_double),
+        ("paper_full_points", ctypes.c_double), ("alg_bytes", ctypes.c_double),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load_library():
+    """Loads the in-tree libpsolver.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpsolver.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "ps_plan_create": [i, i, i, d, i, i, i, i, ctypes.POINTER(vp)],
+        "ps_plan_set_lengths": [vp, i, i, i],
+        "ps_plan_set_math": [vp, i],
+        "ps_plan_query": [vp, ctypes.POINTER(PlanInfo)],
+        "ps_kernel_build": [vp, vp],
+        "ps_kernel_get": [vp, vp, vp],
+        "ps_solve": [vp, vp, vp, vp, vp],
+        "ps_solve_adjoint": [vp, vp, vp, vp],
+        "ps_solve_batched": [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp],
+        "ps_solve_host": [vp, vp, vp, vp, vp],
+        "ps_plan_set_profiling": [vp, i],
+        "ps_plan_pass_times": [vp, ctypes.POINTER(d), ctypes.POINTER(i)],
+        "ps_plan_destroy": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = i
+    lib.ps_strerror.argtypes = [i]
+    lib.ps_strerror.restype = ctypes.c_char_p
+    lib.ps_last_error.argtypes = []
+    lib.ps_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        msg = _lib.ps_last_error().decode(errors="replace")
+        raise PsError(code, msg or _lib.ps_strerror(code).decode())
+
+
+def _bc_codes(bc):
+    bc = str(bc).lower()
+    if len(bc) != 3 or any(b not in "pf" for b in bc):
+        raise ValueError(f"bc must be 3 letters of 'p'/'f', got {bc!r}")
+    return [PS_BC_PERIODIC if b == "p" else PS_BC_FREE for b in bc]
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """One solve geometry: ps_plan_create (+ optional lengths) and ps_kernel_build."""
+
+    def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None):
+        lib = load_library()
+        self.n = tuple(int(v) for v in n)
+        self.bc = str(bc).lower()
+        self.h = float(h)
+        self.dtype = {"f32": PS_F32, "float32": PS_F32, "f64": PS_F64, "float64": PS_F64}[str(dtype)]
+        handle = ctypes.c_void_p()
+        codes = _bc_codes(bc)
+        _check(lib.ps_plan_create(self.n[0], self.n[1], self.n[2], self.h, codes[0], codes[1], codes[2],
+                                  self.dtype, ctypes.byref(handle)))
+        self._h = handle
+        if L is not None:
+            _check(lib.ps_plan_set_lengths(self._h, int(L[0]), int(L[1]), int(L[2])))
+        if build:
+            self.build(stream)
+
+    # ------------------------------------------------------------ lifecycle
+    def build(self, stream=None):
+        _check(_lib.ps_kernel_build(self._h, _stream_handle(stream)))
+        return self
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ps_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        out = PlanInfo()
+        _check(_lib.ps_plan_query(self._h, ctypes.byref(out)))
+        return out
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float32 if self.dtype == PS_F32 else torch.float64
+
+    @property
+    def shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def _check_tensor(self, t, name):
+        if tuple(t.shape) != self.shape or t.dtype != self.torch_dtype or not t.is_cuda \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {self.torch_dtype} tensor of shape "
+                             f"{self.shape}, got {tuple(t.shape)} {t.dtype} on {t.device}")
+
+    def set_profiling(self, enable=True):
+        """ps_plan_set_profiling: per-pass CUDA events on every later solve."""
+        _check(_lib.ps_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def pass_times(self):
+        """ps_plan_pass_times: (summed ms per pass [5], number of solves)."""
+        ms = (ctypes.c_double * 5)()
+        cnt = ctypes.c_int(0)
+        _check(_lib.ps_plan_pass_times(self._h, ms, ctypes.byref(cnt)))
+        return list(ms), cnt.value
+
+    # ------------------------------------------------------------ solves
+    def solve(self, rho, V=None, energy=True, stream=None, E=None):
+        """ps_solve: returns (V, E) with E a 0-d float64 CUDA tensor (or None).
+        ``V`` and ``E`` may be given as preallocated outputs."""
+        import torch
+        self._check_tensor(rho, "rho")
+        if V is None:
+            V = torch.empty_like(rho)
+        self._check_tensor(V, "V")
+        if energy and E is None:
+            E = torch.empty((), dtype=torch.float64, device=rho.device)
+        if not energy:
+            E = None
+        elif E.dtype != torch.float64 or not E.is_cuda or E.numel() != 1:
+            raise ValueError("E must be a one-element float64 CUDA tensor")
+        _check(_lib.ps_solve(self._h, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                             ctypes.c_void_p(E.data_ptr()) if E is not None else None,
+                             _stream_handle(stream)))
+        return V, E
+
+    def solve_adjoint(self, vbar, out=None, stream=None):
+        """ps_solve_adjoint: rhobar = K^T vbar (= K vbar, K is symmetric)."""
+        import torch
+        self._check_tensor(vbar, "vbar")
+        if out is None:
+            out = torch.empty_like(vbar)
+        _check(_lib.ps_solve_adjoint(self._h, ctypes.c_void_p(vbar.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def solve_host(self, rho_host, V_host=None, stream=None):
+        """ps_solve_host on CPU tensors (pinned for asynchronous copies)."""
+        import torch
+        if tuple(rho_host.shape) != self.shape or rho_host.dtype != self.torch_dtype \
+                or rho_host.is_cuda or not rho_host.is_contiguous():
+            raise ValueError("rho_host must be a contiguous CPU tensor of the plan's shape and dtype")
+        if V_host is None:
+            V_host = torch.empty_like(rho_host)
+        E = ctypes.c_double(0.0)
+        _check(_lib.ps_solve_host(self._h, ctypes.c_void_p(rho_host.data_ptr()),
+                                  ctypes.c_void_p(V_host.data_ptr()), ctypes.byref(E),
+                                  _stream_handle(stream)))
+        return V_host, E.value
+
+    def kernel_octant(self, stream=None):
+        """ps_kernel_get: the stored K^F / (L1 L2 L3) octant, shape (L3/2+1, L2/2+1, c)."""
+        import torch
+        inf = self.info()
+        shape = (inf.L[2] // 2 + 1, inf.L[1] // 2 + 1, inf.c)
+        out = torch.empty(shape, dtype=self.torch_dtype, device="cuda")
+        _check(_lib.ps_kernel_get(self._h, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+
+def solve_batched(plans, rhos, Vs=None, energy=True, stream=None):
+    """ps_solve_batched over a list of built plans and matching densities."""
+    import torch
+    lib = load_library()
+    count = len(plans)
+    if len(rhos) != count:
+        raise ValueError("plans and rhos differ in length")
+    for p, r in zip(plans, rhos):
+        p._check_tensor(r, "rho")
+    if Vs is None:
+        Vs = [torch.empty_like(r) for r in rhos]
+    E = torch.empty(count, dtype=torch.float64, device=rhos[0].device) if (energy and count) else None
+    arr = ctypes.c_void_p * max(count, 1)
+    hp = arr(*[p.handle for p in plans])
+    rp = arr(*[r.data_ptr() for r in rhos])
+    vp = arr(*[v.data_ptr() for v in Vs])
+    _check(lib.ps_solve_batched(count, hp, rp, vp,
+                                ctypes.c_void_p(E.data_ptr()) if E is not None else None,
+                                _stream_handle(stream)))
+    return Vs, E

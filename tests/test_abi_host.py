@@ -1,0 +1,133 @@
+"""Host-side checks of the C ABI: no GPU, no compute calls.
+
+The library must load, export every entry point declared in include/*.h,
+validate arguments before touching the device, and describe plans (lengths,
+per-pass line counts, work and byte counts) as the paper's §3 does.
+"""
+import ctypes
+import glob
+import json
+import os
+import re
+
+import pytest
+
+from paper_1211_5244_gb300 import build as _build
+from paper_1211_5244_gb300 import psolver as ps
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ps.load_library()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names |= set(re.findall(r"^\s*(?:int|const char\*)\s+(ps_\w+)\s*\(", txt, re.M))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 13
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _create(lib, n=(8, 8, 8), h=0.3, bc=(1, 1, 1), dtype=0):
+    out = ctypes.c_void_p()
+    rc = lib.ps_plan_create(n[0], n[1], n[2], h, bc[0], bc[1], bc[2], dtype, ctypes.byref(out))
+    return rc, out
+
+
+@pytest.mark.parametrize("kw", [dict(n=(0, 4, 4)), dict(n=(4, -1, 4)), dict(h=0.0), dict(h=-1.0),
+                                dict(h=float("nan")), dict(h=float("inf")), dict(bc=(2, 1, 1)),
+                                dict(dtype=3)])
+def test_create_rejects_bad_arguments(lib, kw):
+    rc, out = _create(lib, **kw)
+    assert rc == 1 and not out.value
+    assert lib.ps_last_error().decode()
+
+
+def test_create_null_out_and_too_long(lib):
+    assert lib.ps_plan_create(4, 4, 4, 0.3, 1, 1, 1, 0, None) == 1
+    rc, out = _create(lib, n=(2049, 4, 4))  # free: L = 4098 > 4096
+    assert rc == 2 and not out.value
+    rc, out = _create(lib, n=(4096, 4, 4), bc=(0, 1, 1))  # periodic: L = 4096 is fine
+    assert rc == 0
+    lib.ps_plan_destroy(out)
+
+
+def test_set_lengths_rules(lib):
+    rc, p = _create(lib, n=(10, 12, 7), bc=(0, 1, 1))
+    assert rc == 0
+    assert lib.ps_plan_set_lengths(p, 11, 0, 0) == 1  # periodic axis must keep n
+    assert lib.ps_plan_set_lengths(p, 0, 22, 0) == 1  # free axis needs >= 2n - 1 = 23
+    assert lib.ps_plan_set_lengths(p, 0, 23, 15) == 0
+    info = ps.PlanInfo()
+    assert lib.ps_plan_query(p, ctypes.byref(info)) == 0
+    assert list(info.L) == [10, 23, 15] and info.c == 6
+    assert lib.ps_plan_set_math(p, 7) == 1
+    assert lib.ps_plan_set_math(p, 0) == 0
+    lib.ps_plan_destroy(p)
+
+
+def test_solve_on_unbuilt_plan_is_rejected_before_any_launch(lib):
+    rc, p = _create(lib)
+    fake_in, fake_out = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000)
+    assert lib.ps_solve(p, fake_in, fake_out, None, None) == 3
+    assert lib.ps_solve_adjoint(p, fake_in, fake_out, None) == 3
+    assert lib.ps_kernel_get(p, fake_out, None) == 3
+    assert lib.ps_solve(p, None, fake_out, None, None) == 1
+    assert lib.ps_solve(None, fake_in, fake_out, None, None) == 1
+    arr = ctypes.c_void_p * 1
+    assert lib.ps_solve_batched(1, arr(p.value), arr(0x10000), arr(0x20000), None, None) == 3
+    assert lib.ps_solve_batched(0, None, None, None, None, None) == 0
+    assert lib.ps_solve_batched(-1, None, None, None, None, None) == 1
+    assert lib.ps_plan_destroy(p) == 0
+    assert lib.ps_plan_destroy(None) == 0
+
+
+def test_strerror(lib):
+    for code in range(7):
+        assert lib.ps_strerror(code).decode()
+    assert lib.ps_strerror(99).decode() == "unknown status"
+
+
+GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "work_fractions.json")))
+
+
+@pytest.mark.parametrize("bc", sorted(GOLDEN["fractions"]))
+@pytest.mark.parametrize("n", [8, 64, 256])
+def test_work_fraction_matches_section3(bc, n):
+    p = ps.Plan((n, n, n), bc, 0.3, "f32", build=False)
+    info = p.info()
+    num, den = GOLDEN["fractions"][bc]
+    assert info.paper_points * den == info.paper_full_points * num
+
+
+@pytest.mark.parametrize("bc", ["fff", "pff", "ppf", "ppp", "fpf"])
+def test_lines_per_pass_match_listing(bc):
+    n1, n2, n3 = 12, 7, 9
+    p = ps.Plan((n1, n2, n3), bc, 0.3, "f64", build=False)
+    info = p.info()
+    L1, L2, L3 = info.L
+    env = dict(n1=n1, n2=n2, n3=n3, L1=L1, L2=L2, L3=L3)
+    rows = {k: eval(v, {}, env) for k, v in GOLDEN["listing_rows"].items()}
+    assert list(info.lines) == [rows["x"], rows["y"], rows["z"], rows["y"], rows["x"]]
+    assert list(info.line_len) == [L1, L2, L3, L2, L1]
+    for j, b in enumerate(bc):
+        assert info.L[j] == ((n1, n2, n3)[j] * (2 if b == "f" else 1))
+
+
+def test_algorithmic_bytes_256_free_fp32():
+    info = ps.Plan((256, 256, 256), "fff", 0.3, "f32", build=False).info()
+    n, c, L = 256 ** 3, 257, 512
+    expect = 2 * n * 4 + 8 * 4 * c * 256 * (256 + L) + 4 * c * 257 * 257
+    assert info.alg_bytes == expect
+    assert abs(info.alg_bytes / 1e9 - 1.819) < 1e-3

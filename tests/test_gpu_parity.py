@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 and relative max error of V over the physical grid,
+and relative error of the energy): 1e-12 for FP64 plans, 1e-5 for FP32 plans.
+Sizes span several CTA tiles with ragged tails; full-size cases compare
+sampled points with the literal Eq. 2 sum and check properties that hold at
+any size.
+"""
+import numpy as np
+import pytest
+
+from oracle import poisson as op
+from paper_1211_5244_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+ALL_BCS = ["fff", "pff", "fpf", "ffp", "ppf", "pfp", "fpp", "ppp"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(gpu_lib):
+    import torch
+    return torch
+
+
+def _np_dtype(dtype):
+    return np.float32 if dtype == "f32" else np.float64
+
+
+def _gpu_solve(torch, rho, bc, h, dtype, L=None):
+    from paper_1211_5244_gb300 import psolver
+    n = rho.shape[::-1]
+    plan = psolver.Plan(n, bc, h, dtype, L=L)
+    r = torch.from_numpy(np.ascontiguousarray(rho.astype(_np_dtype(dtype)))).cuda()
+    V, E = plan.solve(r)
+    torch.cuda.synchronize()
+    return V.double().cpu().numpy(), float(E.item()), plan
+
+
+def _errs(V, Vo):
+    rel_l2 = np.linalg.norm(V - Vo) / np.linalg.norm(Vo)
+    rel_max = np.abs(V - Vo).max() / np.abs(Vo).max()
+    return rel_l2, rel_max
+
+
+def _check(V, E, rho, bc, h, dtype, L=None):
+    # the oracle sees the density the GPU saw (rounded to the plan dtype)
+    rho_seen = rho.astype(_np_dtype(dtype)).astype(np.float64)
+    Vo, Eo = op.solve(rho_seen, bc, h, L=L)
+    l2, mx = _errs(V, Vo)
+    eerr = abs(E - Eo) / abs(Eo)
+    tol = TOL[dtype]
+    assert l2 <= tol and mx <= tol and eerr <= tol, (bc, dtype, l2, mx, eerr)
+    return l2, mx, eerr
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc", ALL_BCS)
+@pytest.mark.parametrize("n", [(37, 29, 23), (16, 40, 9), (1, 7, 5), (33, 1, 18)])
+def test_parity_ragged(torch_cuda, n, bc, dtype):
+    rho = synth.random_density(n, seed=sum(n) + ALL_BCS.index(bc), subtract_mean="p" in bc)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.37, dtype)
+    _check(V, E, rho, bc, 0.37, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,bc", [((31, 17, 13), "ppp"), ((29, 23, 11), "pff"), ((157, 5, 6), "pfp"),
+                                  ((24, 131, 7), "ppf")])
+def test_parity_prime_lengths(torch_cuda, n, bc, dtype):
+    rho = synth.gaussian_mixture(n, 0.3, 4, seed=5, noise=1e-3, subtract_mean=True)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.3, dtype)
+    _check(V, E, rho, bc, 0.3, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc,L", [("fff", (19, 25, 27)), ("pff", (10, 27, 45)), ("ppf", (10, 12, 27))])
+def test_parity_other_padded_lengths(torch_cuda, bc, L, dtype):
+    n = (10, 12, 14)
+    L = tuple(n[j] if bc[j] == "p" else L[j] for j in range(3))
+    rho = synth.random_density(n, seed=9, subtract_mean="p" in bc)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.3, dtype, L=L)
+    # the physical result does not depend on the padded length (§2)
+    _check(V, E, rho, bc, 0.3, dtype)
+
+
+def test_free32_fp64_workload(torch_cuda):
+    w = synth.WORKLOADS["free32_f64"]
+    rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"])
+    V, E, _ = _gpu_solve(torch_cuda, rho, "fff", w["h"], "f64")
+    _check(V, E, rho, "fff", w["h"], "f64")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc", ["ppp", "pff", "ppf", "fff"])
+def test_bc128_workload(torch_cuda, bc, dtype):
+    w = synth.WORKLOADS["bc128"]
+    rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"], noise=w["noise"],
+                                 subtract_mean="p" in bc)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, w["h"], dtype)
+    _check(V, E, rho, bc, w["h"], dtype)
+
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_kernel_octant_matches_oracle(torch_cuda, bc):
+    from paper_1211_5244_gb300 import psolver
+    n = (12, 9, 14)
+    plan = psolver.Plan(n, bc, 0.3, "f64")
+    K = plan.kernel_octant().cpu().numpy()
+    L = op.padded_lengths(n, bc)
+    Ko = op.kernel_fourier_octant(n, bc, 0.3) / (L[0] * L[1] * L[2])
+    assert K.shape == Ko.shape
+    assert np.abs(K - Ko).max() <= 1e-13 * np.abs(Ko).max()
+
+
+def test_kernel_octant_wire_fine_grid(torch_cuda):
+    # many wavenumbers, small h: exercises K0 over a wide argument range
+    from paper_1211_5244_gb300 import psolver
+    n, h = (64, 20, 20), 0.05
+    plan = psolver.Plan(n, "pff", h, "f64")
+    K = plan.kernel_octant().cpu().numpy()
+    L = op.padded_lengths(n, "pff")
+    Ko = op.kernel_fourier_octant(n, "pff", h) / (L[0] * L[1] * L[2])
+    assert np.abs(K - Ko).max() <= 1e-13 * np.abs(Ko).max()
+
+
+@pytest.mark.parametrize("bc", ["fff", "pff", "ppf", "ppp"])
+def test_adjoint_is_the_symmetric_solve(torch_cuda, bc):
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    n = (21, 18, 15)
+    plan = psolver.Plan(n, bc, 0.3, "f64")
+    u = torch.from_numpy(synth.random_density(n, 1)).cuda()
+    v = torch.from_numpy(synth.random_density(n, 2)).cuda()
+    Ku, _ = plan.solve(u, energy=False)
+    KTv = plan.solve_adjoint(v)
+    lhs, rhs = float((v * Ku).sum()), float((KTv * u).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+    Kv, _ = plan.solve(v, energy=False)
+    assert torch.equal(Kv, KTv)
+
+
+def test_batched_matches_individual_solves(torch_cuda):
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    shapes = synth.batched_shapes(12, 8, 40, seed=3)
+    plans, rhos = [], []
+    for i, (n, bc) in enumerate(shapes):
+        dtype = "f32" if i % 3 else "f64"
+        plans.append(psolver.Plan(n, bc, 0.3, dtype))
+        r = synth.gaussian_mixture(n, 0.3, 3, seed=i, noise=1e-3, subtract_mean="p" in bc)
+        rhos.append(torch.from_numpy(r.astype(np.float32 if dtype == "f32" else np.float64)).cuda())
+    Vs, Es = psolver.solve_batched(plans, rhos)
+    for p, r, V, E in zip(plans, rhos, Vs, Es):
+        V1, E1 = p.solve(r)
+        assert torch.equal(V, V1) and torch.equal(E, E1)
+
+
+def test_host_path_matches_device(torch_cuda):
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    n = (40, 33, 27)
+    plan = psolver.Plan(n, "fff", 0.3, "f32")
+    rho = torch.from_numpy(synth.gaussian_mixture(n, 0.3, 3, 4).astype(np.float32))
+    Vh, Eh = plan.solve_host(rho.pin_memory())
+    Vd, Ed = plan.solve(rho.cuda())
+    assert torch.equal(Vh, Vd.cpu()) and Eh == float(Ed.item())
+
+
+@pytest.mark.parametrize("name", ["free256_f32", "free512_f32"])
+def test_full_size_free_sampled(torch_cuda, name):
+    """Full-size free BCs in FP32, the benchmark's launch configuration:
+    sampled points against the literal Eq. 2 sum in FP64, and the energy
+    against 1/2 h^3 sum rho V formed in FP64 from the GPU's own V."""
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    w = synth.WORKLOADS[name]
+    rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"], noise=w["noise"])
+    rho32 = rho.astype(np.float32)
+    plan = psolver.Plan(w["n"], "fff", w["h"], "f32")
+    V, E = plan.solve(torch.from_numpy(rho32).cuda())
+    Vh = V.double().cpu().numpy()
+    n3, n2, n1 = rho.shape
+    rng = np.random.default_rng(0)
+    pts = [(0, 0, 0), (n3 - 1, n2 - 1, n1 - 1), (n3 // 2, n2 // 2, n1 // 2)]
+    pts += [tuple(int(v) for v in rng.integers(0, [n3, n2, n1])) for _ in range(3 if n1 > 256 else 9)]
+    ref = op.direct_at(rho32.astype(np.float64), w["h"], pts)
+    got = np.array([Vh[p] for p in pts])
+    scale = np.abs(Vh).max()
+    assert np.abs(got - ref).max() <= TOL["f32"] * scale
+    e_direct = 0.5 * w["h"] ** 3 * float(np.sum(rho32.astype(np.float64) * Vh))
+    assert abs(float(E.item()) - e_direct) <= TOL["f32"] * abs(e_direct)

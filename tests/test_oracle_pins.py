@@ -299,3 +299,12 @@ def test_energy_is_exactly_quadratic(bc):
     Em = op.solve(rho - eps * u, bc, h)[1]
     fd = (Ep - Em) / (2 * eps)
     assert abs(fd - h ** 3 * np.sum(V * u)) < 1e-12 * max(1.0, abs(fd))
+
+
+def test_direct_at_matches_brute_force():
+    rng = np.random.default_rng(12)
+    rho = rng.standard_normal((6, 5, 7))
+    Vb = op.brute_force(rho, "fff", 0.3)
+    pts = [(0, 0, 0), (5, 4, 6), (2, 3, 1)]
+    got = op.direct_at(rho, 0.3, pts)
+    assert np.abs(got - np.array([Vb[p] for p in pts])).max() < 1e-13 * np.abs(Vb).max()
