@@ -190,3 +190,31 @@ def test_full_size_free_sampled(torch_cuda, name):
     assert np.abs(got - ref).max() <= TOL["f32"] * scale
     e_direct = 0.5 * w["h"] ** 3 * float(np.sum(rho32.astype(np.float64) * Vh))
     assert abs(float(E.item()) - e_direct) <= TOL["f32"] * abs(e_direct)
+
+
+# Shapes that select every specialised FP32 kernel: strided lengths 64..1024
+# (half = zero-padded free axis, full = periodic axis) and x passes with
+# M = L1/2 from 32 to 512.
+FAST_CASES = [
+    ((32, 32, 32), "fff"),     # x M=32 half, y/z L=64 half
+    ((64, 64, 64), "ppp"),     # x M=32 full, y/z L=64 full
+    ((128, 64, 32), "pff"),    # x M=64 full, y L=128 half, z L=64 half
+    ((64, 128, 128), "fpp"),   # x M=64 half, y/z L=128 full
+    ((128, 128, 8), "ffp"),    # x M=128 half, y L=256 half, z generic
+    ((256, 8, 256), "ppp"),    # x M=128 full, z L=256 full
+    ((512, 4, 128), "pff"),    # x M=256 full, z L=256 half
+    ((8, 512, 16), "fpf"),     # y L=512 full
+    ((8, 256, 16), "pff"),     # y L=512 half
+    ((4, 4, 512), "ffp"),      # z L=512 full
+    ((4, 4, 512), "fff"),      # z L=1024 half
+    ((6, 1024, 4), "ppf"),     # y L=1024 full
+    ((1024, 4, 6), "pff"),     # x M=512 full
+    ((512, 6, 4), "fff"),      # x M=512 half
+]
+
+
+@pytest.mark.parametrize("n,bc", FAST_CASES)
+def test_parity_fast_kernels_fp32(torch_cuda, n, bc):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
+    _check(V, E, rho, bc, 0.25, "f32")
