@@ -202,6 +202,33 @@ int ps_plan_pass_times(ps_plan plan, double* ms, int* count);
 /* ps_plan_destroy -- free the plan and its device memory. NULL is a no-op. */
 int ps_plan_destroy(ps_plan plan);
 
+/*
+ * ps_hartree_energy_noalloc -- E = 1/2 h^3 sum_r rho(r) V(r) without allocating
+ * any device memory. The paper has no counterpart: this entry point exists for
+ * callers that must not call cudaMalloc or cudaFree on their compute path --
+ * a host application whose device memory is owned by its own arena or by a
+ * framework's allocator, or code that cannot risk an allocation failing, or
+ * the device-wide synchronisation cudaFree implies, in the middle of a run.
+ *   dtype          enum ps_dtype of rho and V
+ *   npoints        number of grid points, 1 .. 536870912 (= 65536 * 8192);
+ *                  larger grids return PS_ERR_UNSUPPORTED before any launch
+ *   h > 0          grid spacing
+ *   rho, V         device pointers, npoints elements each (read only)
+ *   ehartree_dev   device pointer to one double (written)
+ * The grid reduction's scratch (65536 partial sums and a counter, 512 KiB) is
+ * a static device array inside the library, held by every GPU that loads the
+ * library until the process exits. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current), so
+ * make that first call before any stream capture. Every call shares the one
+ * array: calls whose work may overlap on the GPU (two streams, or two host
+ * threads) race and give wrong energies; serialise them. The counter is
+ * cleared at the start of every call; the partial sums are overwritten.
+ * Errors: PS_ERR_ARG (dtype, npoints < 1, h, NULL or misaligned pointers),
+ * PS_ERR_UNSUPPORTED (npoints too large), PS_ERR_CUDA.
+ */
+int ps_hartree_energy_noalloc(int dtype, long long npoints, double h, const void* rho,
+                              const void* V, double* ehartree_dev, void* stream);
+
 /* ps_strerror -- static description of a status code. */
 const char* ps_strerror(int status);
 

@@ -75,6 +75,8 @@ def load_library():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = i
+    lib.ps_hartree_energy_noalloc.argtypes = [i, ctypes.c_longlong, d, vp, vp, vp, vp]
+    lib.ps_hartree_energy_noalloc.restype = i
     lib.ps_strerror.argtypes = [i]
     lib.ps_strerror.restype = ctypes.c_char_p
     lib.ps_last_error.argtypes = []
@@ -247,3 +249,23 @@ def solve_batched(plans, rhos, Vs=None, energy=True, stream=None):
                                 ctypes.c_void_p(E.data_ptr()) if E is not None else None,
                                 _stream_handle(stream)))
     return Vs, E
+
+
+def hartree_energy_noalloc(rho, V, h, E=None, stream=None):
+    """ps_hartree_energy_noalloc: E = 1/2 h^3 sum rho V from device tensors,
+    without any device allocation inside the library (``E``, a one-element
+    float64 CUDA tensor, may be passed in so the call allocates nothing)."""
+    import torch
+    lib = load_library()
+    if rho.shape != V.shape or rho.dtype != V.dtype or not (rho.is_cuda and V.is_cuda) \
+            or not (rho.is_contiguous() and V.is_contiguous()):
+        raise ValueError("rho and V must be contiguous CUDA tensors of one shape and dtype")
+    dtype = {torch.float32: PS_F32, torch.float64: PS_F64}.get(rho.dtype)
+    if dtype is None:
+        raise ValueError("rho must be float32 or float64")
+    if E is None:
+        E = torch.empty((), dtype=torch.float64, device=rho.device)
+    _check(lib.ps_hartree_energy_noalloc(dtype, rho.numel(), float(h), ctypes.c_void_p(rho.data_ptr()),
+                                         ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(E.data_ptr()),
+                                         _stream_handle(stream)))
+    return E
