@@ -199,6 +199,62 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """64 uneven problems (n ~ U{24..160} per axis, BC uniform over free, wire,
+    surface, periodic; FP32), autotuned plans, one ps_solve_batched per step.
+    The metric is total physical points per second of the batch."""
+    import numpy as np
+    import torch
+    from paper_1211_5244_gb300 import build as _build
+    from paper_1211_5244_gb300 import psolver, synth
+    _build.build()
+    w = synth.WORKLOADS["batched64"]
+    shapes = synth.batched_shapes(w["count"], w["nmin"], w["nmax"], w["seed"])
+    tune = not os.environ.get("PS_BENCH_NO_TUNE")
+    plans, rhos = [], []
+    for i, (n, bc) in enumerate(shapes):
+        plans.append(psolver.Plan(n, bc, w["h"], "f32", autotune=tune))
+        r = synth.gaussian_mixture(n, w["h"], w["n_gauss"], w["seed"] + 1000 + i, noise=w["noise"],
+                                   subtract_mean="p" in bc)
+        rhos.append(torch.from_numpy(r.astype(np.float32)).cuda())
+    Vs = [torch.empty_like(r) for r in rhos]
+    E = torch.empty(len(plans), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.zero_()
+        psolver.solve_batched(plans, rhos, Vs, stream=stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.2)
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        psolver.solve_batched(plans, rhos, Vs, stream=stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    npts = sum(int(np.prod(n)) for n, _ in shapes)
+    alg = sum(p.info().alg_bytes for p in plans)
+    peak, peak_src = _peak_hbm()
+    ms = total_ms / args.steps
+    line = {"metric": "grid points/s of a batch of 64 uneven mixed-BC Poisson solves", "value":
+            npts * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"64 problems, n ~ U{{24..160}} per axis, BC uniform over fff/pff/ppf/ppp, "
+                                   f"seed {w['seed']}, autotuned={tune}", "points": npts,
+                       "lengths": [list(p.info().L) for p in plans]},
+            "solve_roofline": {"alg_bytes": alg, "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
+            "gpu_launches": 5 * len(plans) * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,10 +262,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched64":
+        run_batched(args)
         return
 
     import numpy as np

@@ -112,6 +112,20 @@ int ps_plan_create(int n1, int n2, int n3, double h, int bc_x, int bc_y, int bc_
  */
 int ps_plan_set_lengths(ps_plan plan, int L1, int L2, int L3);
 
+/*
+ * ps_plan_autotune -- choose the padded lengths of the free axes by timing.
+ * Any L >= 2n - 1 gives the same physical result (§2); the candidates are the
+ * paper's 2n and the smallest lengths >= 2n - 1 made of the factors {2},
+ * {2, 3} and {2, 3, 5, 7} (a power of two selects the register-resident
+ * kernels). One trial plan per candidate is built on the current device and
+ * `reps` solves of it are timed on `stream` (reps < 1 means 5); the fastest
+ * lengths are set on `plan` (not built). Results are cached per geometry and
+ * device in memory and, when the environment variable PS_TUNE_CACHE names a
+ * file, in that file. Must precede ps_kernel_build; synchronises `stream`.
+ * Errors: PS_ERR_ARG (plan NULL or built), PS_ERR_OOM, PS_ERR_CUDA.
+ */
+int ps_plan_autotune(ps_plan plan, int reps, void* stream);
+
 /* ps_plan_set_math -- enum ps_math; must precede the build. PS_ERR_ARG else. */
 int ps_plan_set_math(ps_plan plan, int math_mode);
 
@@ -158,6 +172,21 @@ int ps_solve(ps_plan plan, const void* rho, void* V, double* ehartree_dev, void*
 int ps_solve_adjoint(ps_plan plan, const void* vbar, void* rhobar, void* stream);
 
 /*
+ * ps_solve_vjp -- vector-Jacobian product of the solve's two outputs,
+ *   rhobar = K^T vbar + h^3 gE V,
+ * the gradient with respect to rho of <vbar, V> + gE * E, since V = K rho,
+ * E = 1/2 h^3 <rho, K rho> and K is symmetric (dE/drho = h^3 V).
+ *   vbar    device pointer (n1*n2*n3 dtype) or NULL (term omitted)
+ *   V       device pointer to the forward result, or NULL (term omitted)
+ *   gE_dev  device pointer to one double, or NULL (term omitted); V and
+ *           gE_dev are both given or both NULL
+ *   rhobar  device pointer (written); must not overlap vbar or V
+ * Errors as ps_solve; PS_ERR_ARG if every term is omitted.
+ */
+int ps_solve_vjp(ps_plan plan, const void* vbar, const void* V, const double* gE_dev, void* rhobar,
+                 void* stream);
+
+/*
  * ps_solve_batched -- count independent solves, each with its own built plan
  * (shapes, boundary conditions and dtypes may differ), enqueued on one stream.
  * Plans of the same dtype share one launch per pass.
@@ -165,6 +194,14 @@ int ps_solve_adjoint(ps_plan plan, const void* vbar, void* rhobar, void* stream)
  *   ehartree_dev             NULL or device array of count doubles
  * Each plan may appear at most once. Errors as ps_solve, with the index of
  * the failing item in ps_last_error().
+ * The five launches of every problem are captured once into a CUDA graph in
+ * which different problems' chains run concurrently (up to 16 at a time);
+ * the instantiated graph is cached for the exact set of plans and pointers
+ * and replayed by later calls with the same arguments (destroying a plan drops
+ * the graphs that use it). The first call with a new argument set therefore
+ * costs a capture. When the caller's stream is itself being captured, or the
+ * plans live on different devices, the solves are launched in order instead.
+ * Per-pass profiling events are not recorded for batched solves.
  */
 int ps_solve_batched(int count, const ps_plan* plans, const void* const* rho,
                      void* const* V, double* ehartree_dev, void* stream);

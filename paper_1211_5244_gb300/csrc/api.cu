@@ -59,7 +59,7 @@ struct DeviceGuard {
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 void free_device(ps_plan_s* p) {
-  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2],
+  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2], &p->tw4z,
                    reinterpret_cast<void**>(&p->partials), reinterpret_cast<void**>(&p->counter),
                    &p->d_rho, &p->d_V, reinterpret_cast<void**>(&p->d_E)};
   for (void** b : bufs) {
@@ -237,9 +237,11 @@ int ps_kernel_build(ps_plan p, void* stream) {
       {&p->tw[2], (size_t)p->L[2] * csz, "twiddles z"},
       {reinterpret_cast<void**>(&p->partials), (size_t)p->npart * sizeof(double), "energy partials"},
       {reinterpret_cast<void**>(&p->counter), sizeof(unsigned), "energy counter"},
+      {&p->tw4z, p->zsoa_T ? (size_t)p->zsoa_T * p->zsoa_T * 16 : 0, "paired z twiddles"},
   };
   size_t total = 0;
   for (auto& a : allocs) {
+    if (a.bytes == 0) continue;
     e = cudaMalloc(a.ptr, a.bytes);
     if (e != cudaSuccess) {
       free_device(p);
@@ -285,6 +287,36 @@ int ps_solve_adjoint(ps_plan p, const void* vbar, void* rhobar, void* stream) {
   return run_solve(p, vbar, rhobar, nullptr, static_cast<cudaStream_t>(stream));
 }
 
+int ps_solve_vjp(ps_plan p, const void* vbar, const void* V, const double* gE_dev, void* rhobar,
+                 void* stream) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (!rhobar) return fail(PS_ERR_ARG, "rhobar is NULL");
+  if (!vbar && !V) return fail(PS_ERR_ARG, "every term of the VJP is omitted");
+  if ((V == nullptr) != (gE_dev == nullptr)) return fail(PS_ERR_ARG, "V and gE_dev must be given together");
+  if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
+  const size_t bytes = grid_points(p) * p->esz;
+  if ((vbar && overlap(vbar, rhobar, bytes)) || (V && overlap(V, rhobar, bytes)))
+    return fail(PS_ERR_ARG, "rhobar overlaps an input");
+  if ((reinterpret_cast<uintptr_t>(vbar) | reinterpret_cast<uintptr_t>(V) |
+       reinterpret_cast<uintptr_t>(rhobar)) % p->esz)
+    return fail(PS_ERR_ARG, "pointers must be aligned to the element size");
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (vbar) {
+    int rc = run_solve(p, vbar, rhobar, nullptr, s);
+    if (rc != PS_OK) return rc;
+  }
+  if (V) {
+    cudaError_t e = p->dtype == PS_F32
+        ? launch_vjp_axpy<float>(p, static_cast<float*>(rhobar), static_cast<const float*>(V), gE_dev,
+                                 vbar != nullptr, s)
+        : launch_vjp_axpy<double>(p, static_cast<double*>(rhobar), static_cast<const double*>(V), gE_dev,
+                                  vbar != nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "vjp energy term");
+  }
+  return PS_OK;
+}
+
 int ps_solve_batched(int count, const ps_plan* plans, const void* const* rho, void* const* V,
                      double* ehartree_dev, void* stream) {
   if (count < 0) return fail(PS_ERR_ARG, "count < 0");
@@ -297,6 +329,18 @@ int ps_solve_batched(int count, const ps_plan* plans, const void* const* rho, vo
       if (plans[j] == plans[i]) return fail(PS_ERR_ARG, "item %d: plan repeated (item %d)", i, j);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool one_device = true;
+  for (int i = 1; i < count; ++i) one_device &= plans[i]->device == plans[0]->device;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (count >= 2 && one_device && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusNone) {
+    DeviceGuard g(plans[0]->device);
+    cudaError_t e = batch_solve_graph(count, plans, rho, V, ehartree_dev, plans[0]->device, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched graph");
+    return PS_OK;
+  }
+  // one problem, several devices, or a stream that is itself being captured:
+  // plain launches in order on the caller's stream
   for (int i = 0; i < count; ++i) {
     DeviceGuard g(plans[i]->device);
     int rc = run_solve(plans[i], rho[i], V[i], ehartree_dev ? ehartree_dev + i : nullptr, s);
@@ -359,6 +403,7 @@ int ps_plan_pass_times(ps_plan p, double* ms, int* count) {
 
 int ps_plan_destroy(ps_plan p) {
   if (!p) return PS_OK;
+  batch_forget_plan(p);
   {
     DeviceGuard g(p->device);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);

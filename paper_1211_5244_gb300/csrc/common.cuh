@@ -96,6 +96,8 @@ struct ps_plan_s {
   void* B;       // [n3][L2][ldc] complex: y-transformed planes (passes 2..4)
   void* K;       // [H3+1][H2+1][c] real: K^F / (L1 L2 L3), even octant
   void* tw[3];   // W_{L_j}^k, k < L_j, complex, per axis
+  void* tw4z;    // paired z twiddles of the packed z kernel (T*T float4), or NULL
+  int zsoa_T;    // T of the packed z kernel (L3 = 2 T^2), 0 if not used
   double* partials;     // per-CTA energy partials of the z pass
   unsigned* counter;    // arrival counter for the last-CTA energy reduction
   int npart;
@@ -125,7 +127,14 @@ cudaError_t configure_passes(ps_plan_s* p);
 template <typename T>
 cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream_t s,
                          cudaEvent_t* ev);
+template <typename T>
+cudaError_t launch_vjp_axpy(ps_plan_s* p, T* out, const T* V, const double* gE, bool accumulate,
+                            cudaStream_t s);
 cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s);
+// batch.cu: the batch as one cached CUDA graph of concurrent per-problem chains
+cudaError_t batch_solve_graph(int count, ps_plan_s* const* plans, const void* const* rho, void* const* V,
+                              double* E, int device, cudaStream_t s);
+void batch_forget_plan(const ps_plan_s* p);
 cudaError_t build_kernel(ps_plan_s* p, cudaStream_t s);
 
 }  // namespace ps

@@ -29,8 +29,18 @@ __device__ __forceinline__ float2 cmulcf(float2 a, float2 b) {
 
 constexpr int kTK = 16;  // lines per CTA
 
+// z pass: rows ky and L2 - ky read the same row of the K^F octant; launch
+// them from adjacent CTA rows (y = 0 -> ky = 0, y = 1 -> ky = L2/2, then
+// pairs p, L2 - p) so the second read hits L2.
+__device__ __forceinline__ int paired_ky(int y, int L2) {
+  if (y == 0) return 0;
+  if (y == 1) return L2 / 2;
+  const int p = (y - 2) / 2 + 1;
+  return (y & 1) ? L2 - p : p;
+}
+
 template <int P, int Q, int KIND, bool HALF>
-__global__ void __launch_bounds__(kTK*(P < Q ? P : Q))
+__global__ void __launch_bounds__(kTK*(P < Q ? P : Q), kTK * (P < Q ? P : Q) <= 256 ? 2 : 1)
     k_strided(const void* src_v, void* dst_v, const float* __restrict__ K, const float2* __restrict__ tw,
               FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
   constexpr int L = P * Q;
@@ -45,8 +55,9 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q))
   const int j = threadIdx.x / kTK;
   const int kx = blockIdx.x * kTK + t;
   const bool valid = kx < a.c;
-  const float2* s = src + blockIdx.y * a.src_plane + kx;
-  float2* d = dst + blockIdx.y * a.dst_plane + kx;
+  const int yblk = KIND == 2 ? paired_ky(blockIdx.y, a.L2) : (int)blockIdx.y;
+  const float2* s = src + yblk * a.src_plane + kx;
+  float2* d = dst + yblk * a.dst_plane + kx;
   float2 X[NK][Q];  // X[v][k2] = spectrum at k1 + P k2, k1 = j + T v
 
   if constexpr (KIND == 0 || KIND == 2) {
@@ -101,7 +112,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q))
     float eacc = 0.f;
     if constexpr (KIND == 2) {
       // V^F = K^F rho^F on the even octant of K^F; energy sum w(kx) K |rho^F|^2
-      const int ky = blockIdx.y;
+      const int ky = yblk;
       const int kyo = min(ky, a.L2 - ky);
       const float* Kp = K + (long long)kyo * a.c + kx;
 #pragma unroll
@@ -149,7 +160,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q))
       }
     }
     if constexpr (KIND == 2) {
-      if (E != nullptr) energy_finish((double)eacc, partials, counter, escale, E);
+      if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
     }
   }
 }

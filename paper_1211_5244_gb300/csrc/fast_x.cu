@@ -11,6 +11,9 @@
 // positions. T lanes own one row (contiguous 8-byte elements), so loads and
 // stores are coalesced along the row. With zero padding (n1 = M), inputs
 // z[m] with m >= M/2 are zero and outputs there are never formed.
+#include <cstdlib>
+#include <cstring>
+
 #include "fft_fast.cuh"
 #include "fft_regs.cuh"
 
@@ -78,7 +81,10 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   }
   __syncthreads();
   if (!valid) return;
-  for (int k = j; k <= M; k += T) {
+#pragma unroll
+  for (int i = 0; i <= M / T; ++i) {
+    const int k = j + T * i;
+    if (k > M) break;
     const float2 zk = zr[k == M ? 0 : k];
     const float2 zm = zr[k == 0 ? 0 : M - k];
     const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
@@ -104,7 +110,16 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   const float2* X = static_cast<const float2*>(src_v) + (long long)row * a.ldc;
   float2* z = reinterpret_cast<float2*>(static_cast<float*>(dst_v) + (long long)row * a.n1);
 
-  for (int k = j; k <= M; k += T) xr[k] = valid ? X[k] : make_float2(0.f, 0.f);
+  {
+    // all loads of the row first (independent, in flight together), then the stores to shared memory
+    float2 xin[M / T];
+#pragma unroll
+    for (int i = 0; i < M / T; ++i) xin[i] = valid ? X[j + T * i] : make_float2(0.f, 0.f);
+    const float2 xny = (valid && j == 0) ? X[M] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < M / T; ++i) xr[j + T * i] = xin[i];
+    if (j == 0) xr[M] = xny;
+  }
   __syncthreads();
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
@@ -228,12 +243,16 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       if ((e = set(P4, f1, grid, threads, smem, inv)) != cudaSuccess) return e;
     }
   }
-  // z pass
+  // z pass: PS_ZPASS=soa selects the packed FP32x2 kernel where it exists
   if (pow2(L3) && (n3 == L3 / 2 || n3 == L3)) {
     const bool half = n3 == L3 / 2;
     int threads;
     size_t smem;
-    const void* f = strided_kernel(L3, 2, half, &threads, &smem);
+    const char* zp = getenv("PS_ZPASS");
+    const bool allow_soa = zp && strcmp(zp, "soa") == 0;
+    const void* f = allow_soa ? zsoa_kernel(L3, half, &threads, &smem) : nullptr;
+    p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;
+    if (!f) f = strided_kernel(L3, 2, half, &threads, &smem);
     if (f) {
       FastArgs z = base;
       z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;      // B[z][ky][kx], line along z
@@ -251,7 +270,7 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
   PassCfg& cf = p->cfg[pass];
   const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
   const float* K = static_cast<const float*>(p->K);
-  const float2* tw = static_cast<const float2*>(p->tw[axis]);
+  const void* tw = (pass == P3 && p->zsoa_T) ? p->tw4z : p->tw[axis];
   double* partials = p->partials;
   unsigned* counter = p->counter;
   void* args[] = {(void*)&src, (void*)&dst, (void*)&K, (void*)&tw, (void*)&cf.fa,

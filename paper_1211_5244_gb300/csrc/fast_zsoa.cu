@@ -1,0 +1,169 @@
+// z pass (forward transform, K^F multiply, inverse transform) for L3 = 2 T^2
+// (T = 8: 128, T = 16: 512) on packed FP32x2 pairs.
+//
+// Same four-step factorisation as fast_strided.cu with P = T, Q = 2T and T
+// threads per line, but every thread carries its two step-1 transforms
+// (b = j and b = j + T) as one structure-of-arrays pair, so their additions
+// run as FP32x2 instructions. The exchange stores each pair as one 16-byte
+// word. The Q-point step splits into a radix-2 stage across the pair
+// (lanes b and b + T) and two T-point transforms that again form a pair
+// (even and odd outputs). The same pairing returns in the inverse. The
+// twiddles W_L^{b k1} of both lanes come from one float4 table,
+// tw4[r * T + c] = (Re W^{rc}, Re W^{(r+T)c}, Im W^{rc}, Im W^{(r+T)c}),
+// used as (r, c) = (j, k1) by the forward and (b, j) by the inverse step.
+#include "fft_fast.cuh"
+#include "fft_soa.cuh"
+#include "reduce.cuh"
+
+namespace ps {
+
+using soa::c2;
+
+namespace {
+
+__device__ __forceinline__ c2 unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+
+// v * w (DIR = -1) or v * conj(w) (DIR = +1), lane by lane, w a table pair
+template <int DIR>
+__device__ __forceinline__ c2 cmul_pair(c2 v, float4 w) {
+  const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+  const float2 nwi = make_float2(-w.z, -w.w);
+  if (DIR < 0) return {soa::fma2(v.im, nwi, soa::mul2(v.re, wr)), soa::fma2(v.re, wi, soa::mul2(v.im, wr))};
+  return {soa::fma2(v.im, wi, soa::mul2(v.re, wr)), soa::fma2(v.re, nwi, soa::mul2(v.im, wr))};
+}
+
+// radix-2 DIF stage of a 2T-point forward DFT across the lanes of z[b]
+// (lanes x_b, x_{b+T}): z[b] <- (x_b + x_{b+T}, (x_b - x_{b+T}) W_{2T}^b)
+template <int T, int B>
+__device__ __forceinline__ void dif_lanes(c2 (&z)[T]) {
+  const float2 x0 = make_float2(z[B].re.x, z[B].im.x), x1 = make_float2(z[B].re.y, z[B].im.y);
+  const float2 s = make_float2(x0.x + x1.x, x0.y + x1.y);
+  const float2 d = regs::twc<2 * T, B, -1>(make_float2(x0.x - x1.x, x0.y - x1.y));
+  z[B] = {make_float2(s.x, d.x), make_float2(s.y, d.y)};
+}
+template <int T, int... B>
+__device__ __forceinline__ void dif_all(c2 (&z)[T], std::integer_sequence<int, B...>) {
+  (dif_lanes<T, B>(z), ...);
+}
+
+// radix-2 DIT stage of a 2T-point inverse DFT across the lanes of z[b]
+// (lanes E_b, O_b): z[b] <- (E_b + W_{2T}^{-b} O_b, E_b - W_{2T}^{-b} O_b)
+template <int T, int B>
+__device__ __forceinline__ void dit_lanes(c2 (&z)[T]) {
+  const float2 e = make_float2(z[B].re.x, z[B].im.x);
+  const float2 o = regs::twc<2 * T, B, 1>(make_float2(z[B].re.y, z[B].im.y));
+  z[B] = {make_float2(e.x + o.x, e.x - o.x), make_float2(e.y + o.y, e.y - o.y)};
+}
+template <int T, int... B>
+__device__ __forceinline__ void dit_all(c2 (&z)[T], std::integer_sequence<int, B...>) {
+  (dit_lanes<T, B>(z), ...);
+}
+
+__device__ __forceinline__ int paired_ky_soa(int y, int L2) {
+  if (y == 0) return 0;
+  if (y == 1) return L2 / 2;
+  const int p = (y - 2) / 2 + 1;
+  return (y & 1) ? L2 - p : p;
+}
+
+}  // namespace
+
+constexpr int kTKs = 16;  // lines per CTA
+
+template <int T, bool HALF>
+__global__ void __launch_bounds__(kTKs * T, 2)
+    k_zconv_soa(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
+                FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
+  constexpr int P = T, Q = 2 * T, L = P * Q;
+  constexpr int NA = HALF ? P / 2 : P;
+  extern __shared__ float4 sh4[];  // [T * P][kTKs]: slot (r, c) of line t at (r * P + c) * kTKs + t
+  const int t = threadIdx.x % kTKs;
+  const int j = threadIdx.x / kTKs;
+  const int kx = blockIdx.x * kTKs + t;
+  const bool valid = kx < a.c;
+  const int ky = paired_ky_soa(blockIdx.y, a.L2);
+  float2* line = static_cast<float2*>(line_v) + ky * a.src_plane + kx;
+  const long long es = a.src_elem;
+
+  // step 1: P-point transforms of x[b + Q a] for the lanes b = j and b = j + T
+  c2 y[P];
+#pragma unroll
+  for (int aa = 0; aa < P; ++aa) {
+    y[aa] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (aa < NA && valid) {
+      const float2 u0 = line[(long long)(j + Q * aa) * es];
+      const float2 u1 = line[(long long)(j + T + Q * aa) * es];
+      y[aa] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+    }
+  }
+  soa::dft2<P, -1, HALF>(y);
+#pragma unroll
+  for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], __ldg(&tw4[j * P + k1]));
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) sh4[(j * P + k1) * kTKs + t] = pack(y[k1]);
+  __syncthreads();
+
+  // step 3 for k1 = j: lanes (Y_b, Y_{b+T}) -> radix-2 across lanes -> two T-point
+  // transforms: z[m] = (X[j + P 2m], X[j + P (2m+1)])
+  c2 z[T];
+#pragma unroll
+  for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * kTKs + t]);
+  dif_all<T>(z, std::make_integer_sequence<int, T>{});
+  soa::dft2<T, -1, false>(z);
+
+  // V^F = K^F rho^F on the even octant; energy sum w(kx) K |rho^F|^2
+  const int kyo = min(ky, a.L2 - ky);
+  const float* Kp = K + (long long)kyo * a.c + kx;
+  float2 e2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < T; ++m) {
+    const int kz0 = j + P * 2 * m, kz1 = kz0 + P;
+    const int o0 = kz0 <= L / 2 ? kz0 : L - kz0, o1 = kz1 <= L / 2 ? kz1 : L - kz1;
+    const float2 kk = valid ? make_float2(__ldg(&Kp[(long long)o0 * a.kz_stride]), __ldg(&Kp[(long long)o1 * a.kz_stride]))
+                            : make_float2(0.f, 0.f);
+    const float2 p2 = soa::fma2(z[m].re, z[m].re, soa::mul2(z[m].im, z[m].im));
+    e2 = soa::fma2(kk, p2, e2);
+    z[m] = {soa::mul2(z[m].re, kk), soa::mul2(z[m].im, kk)};
+  }
+  float eacc = (e2.x + e2.y) * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
+
+  // inverse step A for k1 = j: two T-point inverses (even / odd k2), radix-2
+  // across lanes -> (Z_b, Z_{b+T}); step B: conjugate twiddles
+  soa::dft2<T, 1, false>(z);
+  dit_all<T>(z, std::make_integer_sequence<int, T>{});
+#pragma unroll
+  for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], __ldg(&tw4[b * P + j]));
+  __syncthreads();  // every thread has read the forward exchange
+#pragma unroll
+  for (int b = 0; b < T; ++b) sh4[(b * P + j) * kTKs + t] = pack(z[b]);
+  __syncthreads();
+
+  // step C for the lanes b = j and b = j + T: P-point inverses over k1
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * kTKs + t]);
+  soa::dft2<P, 1, false>(y);
+  if (valid) {
+#pragma unroll
+    for (int aa = 0; aa < NA; ++aa) {
+      line[(long long)(j + Q * aa) * es] = make_float2(y[aa].re.x, y[aa].im.x);
+      line[(long long)(j + T + Q * aa) * es] = make_float2(y[aa].re.y, y[aa].im.y);
+    }
+  }
+  if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
+}
+
+const void* zsoa_kernel(int L, bool half, int* threads, size_t* smem) {
+  const void* fn = nullptr;
+  int T = 0;
+  switch (L) {
+    case 128: fn = half ? (const void*)k_zconv_soa<8, true> : (const void*)k_zconv_soa<8, false>; T = 8; break;
+    case 512: fn = half ? (const void*)k_zconv_soa<16, true> : (const void*)k_zconv_soa<16, false>; T = 16; break;
+    default: return nullptr;
+  }
+  *threads = kTKs * T;
+  *smem = (size_t)T * T * kTKs * sizeof(float4);
+  return fn;
+}
+
+}  // namespace ps

@@ -1,0 +1,133 @@
+// Pairs of register DFTs in structure-of-arrays form, on the packed FP32x2
+// arithmetic of sm_100-class GPUs.
+//
+// A c2 holds two complex numbers: re = (re_0, re_1), im = (im_0, im_1). Two
+// transforms with the same shape (the same constants) are carried out at once:
+// every complex addition is two FP32x2 additions instead of four FP32
+// additions. Multiplications by the constant twiddles use scalar FMAs with
+// immediates (as many instructions as before); those by +-i are free (a swap of
+// re and im folded into the following additions).
+#pragma once
+
+#include <utility>
+
+#include "fft_regs.cuh"
+
+namespace ps {
+namespace soa {
+
+struct c2 {
+  float2 re, im;
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ c2 operator+(c2 a, c2 b) { return {add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ c2 operator-(c2 a, c2 b) { return {sub2(a.re, b.re), sub2(a.im, b.im)}; }
+
+// a + DIR i b and a - DIR i b, with the multiplication by i folded in
+template <int DIR>
+__device__ __forceinline__ c2 add_i(c2 a, c2 b) {  // a + (DIR i) b
+  return DIR < 0 ? c2{add2(a.re, b.im), sub2(a.im, b.re)} : c2{sub2(a.re, b.im), add2(a.im, b.re)};
+}
+template <int DIR>
+__device__ __forceinline__ c2 sub_i(c2 a, c2 b) {  // a - (DIR i) b
+  return DIR < 0 ? c2{sub2(a.re, b.im), add2(a.im, b.re)} : c2{add2(a.re, b.im), sub2(a.im, b.re)};
+}
+
+// v * W_N^K (DIR = -1) or v * conj(W_N^K) (DIR = +1), both lanes, constants folded.
+template <int N, int K, int DIR>
+__device__ __forceinline__ c2 twc2(c2 v) {
+  static_assert(64 % N == 0, "N must divide 64");
+  constexpr int m = (K * (64 / N)) & 63;
+  if constexpr (m == 0) {
+    return v;
+  } else if constexpr (m == 32) {
+    return {make_float2(-v.re.x, -v.re.y), make_float2(-v.im.x, -v.im.y)};
+  } else if constexpr (m == 16 || m == 48) {
+    // forward m = 16 and inverse m = 48 multiply by -i: (re, im) -> (im, -re)
+    constexpr bool minus_i = (m == 16) == (DIR < 0);
+    return minus_i ? c2{v.im, make_float2(-v.re.x, -v.re.y)} : c2{make_float2(-v.im.x, -v.im.y), v.re};
+  } else {
+    const float2 a = regs::twc<N, K, DIR>(make_float2(v.re.x, v.im.x));
+    const float2 b = regs::twc<N, K, DIR>(make_float2(v.re.y, v.im.y));
+    return {make_float2(a.x, b.x), make_float2(a.y, b.y)};
+  }
+}
+
+template <int N, int DIR, bool HZ>
+__device__ __forceinline__ void dft2(c2 (&x)[N]);
+
+template <int N, int K, int DIR>
+__device__ __forceinline__ void bfly4(c2 (&x)[N], const c2 (&s0)[N / 4], const c2 (&s1)[N / 4],
+                                      const c2 (&s2)[N / 4], const c2 (&s3)[N / 4]) {
+  constexpr int m2 = (2 * K * (64 / N)) & 63;
+  const c2 t0 = s0[K];
+  const c2 t1 = twc2<N, K, DIR>(s1[K]);
+  const c2 t3 = twc2<N, 3 * K, DIR>(s3[K]);
+  c2 a, b;
+  if constexpr (m2 == 16) {
+    // t2 = (DIR i) s2: fold the factor into the additions
+    a = add_i<DIR>(t0, s2[K]);
+    b = sub_i<DIR>(t0, s2[K]);
+  } else {
+    const c2 t2 = twc2<N, 2 * K, DIR>(s2[K]);
+    a = t0 + t2;
+    b = t0 - t2;
+  }
+  const c2 c = t1 + t3, d = t1 - t3;
+  x[K] = a + c;
+  x[K + N / 2] = a - c;
+  x[K + N / 4] = add_i<DIR>(b, d);
+  x[K + 3 * N / 4] = sub_i<DIR>(b, d);
+}
+
+template <int N, int DIR, int... K>
+__device__ __forceinline__ void combine4(c2 (&x)[N], const c2 (&s0)[N / 4], const c2 (&s1)[N / 4],
+                                         const c2 (&s2)[N / 4], const c2 (&s3)[N / 4],
+                                         std::integer_sequence<int, K...>) {
+  (bfly4<N, K, DIR>(x, s0, s1, s2, s3), ...);
+}
+
+// In-place N-point DFTs of both lanes (N a power of two <= 64), natural order.
+// HZ: the upper half of the input is zero.
+template <int N, int DIR, bool HZ>
+__device__ __forceinline__ void dft2(c2 (&x)[N]) {
+  if constexpr (N == 1) {
+  } else if constexpr (N == 2) {
+    if constexpr (HZ) {
+      x[1] = x[0];
+    } else {
+      const c2 a = x[0];
+      x[0] = a + x[1];
+      x[1] = a - x[1];
+    }
+  } else if constexpr (N == 4 && HZ) {
+    const c2 a = x[0], b = x[1];
+    x[0] = a + b;
+    x[2] = a - b;
+    x[1] = add_i<DIR>(a, b);
+    x[3] = sub_i<DIR>(a, b);
+  } else {
+    constexpr int M = N / 4;
+    c2 s0[M], s1[M], s2[M], s3[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      s0[i] = x[4 * i];
+      s1[i] = x[4 * i + 1];
+      s2[i] = x[4 * i + 2];
+      s3[i] = x[4 * i + 3];
+    }
+    dft2<M, DIR, HZ>(s0);
+    dft2<M, DIR, HZ>(s1);
+    dft2<M, DIR, HZ>(s2);
+    dft2<M, DIR, HZ>(s3);
+    combine4<N, DIR>(x, s0, s1, s2, s3, std::make_integer_sequence<int, M>{});
+  }
+}
+
+}  // namespace soa
+}  // namespace ps

@@ -217,6 +217,18 @@ __global__ void twiddle_kernel(cpx<T>* tw, int L) {
   }
 }
 
+// paired twiddles of the packed z kernel: tw4[r T + c] = (Re W^{rc}, Re W^{(r+T)c},
+// Im W^{rc}, Im W^{(r+T)c}), W = exp(-2 pi i / L), r, c < T
+__global__ void twiddle_pairs_kernel(float4* tw4, int L, int T) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < T * T; idx += gridDim.x * blockDim.x) {
+    const int r = idx / T, c = idx % T;
+    double s0, c0, s1, c1;
+    sincospi(2.0 * ((r * c) % L) / L, &s0, &c0);
+    sincospi(2.0 * (((r + T) * c) % L) / L, &s1, &c1);
+    tw4[idx] = make_float4((float)c0, (float)c1, (float)(-s0), (float)(-s1));
+  }
+}
+
 // ---------------------------------------------------------------- host
 
 static int grid_for(size_t n) {
@@ -233,6 +245,9 @@ cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s) {
     else
       twiddle_kernel<double><<<grid_for(L), 256, 0, s>>>(static_cast<double2*>(p->tw[j]), L);
   }
+  if (p->zsoa_T)
+    twiddle_pairs_kernel<<<grid_for(p->zsoa_T * p->zsoa_T), 256, 0, s>>>(static_cast<float4*>(p->tw4z), p->L[2],
+                                                                       p->zsoa_T);
   return cudaGetLastError();
 }
 

@@ -234,6 +234,34 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   }
 }
 
+// ---------------------------------------------------------------- VJP term
+
+// out = (accumulate ? out : 0) + h^3 * gE * V   (the dE/drho = h^3 V term of the VJP)
+template <typename T>
+__global__ void vjp_axpy_kernel(T* __restrict__ out, const T* __restrict__ V, const double* __restrict__ gE,
+                                double h3, long long n, int accumulate) {
+  const T a = (T)(h3 * __ldg(gE));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T v = a * V[i];
+    out[i] = accumulate ? out[i] + v : v;
+  }
+}
+
+template <typename T>
+cudaError_t launch_vjp_axpy(ps_plan_s* p, T* out, const T* V, const double* gE, bool accumulate,
+                            cudaStream_t s) {
+  const long long n = (long long)p->n[0] * p->n[1] * p->n[2];
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  vjp_axpy_kernel<T><<<(int)blocks, 256, 0, s>>>(out, V, gE, p->h * p->h * p->h, n, accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_vjp_axpy<float>(ps_plan_s*, float*, const float*, const double*, bool, cudaStream_t);
+template cudaError_t launch_vjp_axpy<double>(ps_plan_s*, double*, const double*, const double*, bool,
+                                             cudaStream_t);
+
 // ---------------------------------------------------------------- host side
 
 Stages factorize(int N) {

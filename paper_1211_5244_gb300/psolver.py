@@ -60,11 +60,13 @@ def load_library():
         "ps_plan_create": [i, i, i, d, i, i, i, i, ctypes.POINTER(vp)],
         "ps_plan_set_lengths": [vp, i, i, i],
         "ps_plan_set_math": [vp, i],
+        "ps_plan_autotune": [vp, i, vp],
         "ps_plan_query": [vp, ctypes.POINTER(PlanInfo)],
         "ps_kernel_build": [vp, vp],
         "ps_kernel_get": [vp, vp, vp],
         "ps_solve": [vp, vp, vp, vp, vp],
         "ps_solve_adjoint": [vp, vp, vp, vp],
+        "ps_solve_vjp": [vp, vp, vp, vp, vp, vp],
         "ps_solve_batched": [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp],
         "ps_solve_host": [vp, vp, vp, vp, vp],
         "ps_plan_set_profiling": [vp, i],
@@ -108,7 +110,7 @@ def _stream_handle(stream):
 class Plan:
     """One solve geometry: ps_plan_create (+ optional lengths) and ps_kernel_build."""
 
-    def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None):
+    def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None, autotune=False):
         lib = load_library()
         self.n = tuple(int(v) for v in n)
         self.bc = str(bc).lower()
@@ -121,6 +123,8 @@ class Plan:
         self._h = handle
         if L is not None:
             _check(lib.ps_plan_set_lengths(self._h, int(L[0]), int(L[1]), int(L[2])))
+        if autotune:
+            _check(lib.ps_plan_autotune(self._h, 5, _stream_handle(stream)))
         if build:
             self.build(stream)
 
@@ -203,6 +207,25 @@ class Plan:
             out = torch.empty_like(vbar)
         _check(_lib.ps_solve_adjoint(self._h, ctypes.c_void_p(vbar.data_ptr()),
                                      ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def solve_vjp(self, vbar=None, V=None, gE=None, out=None, stream=None):
+        """ps_solve_vjp: rhobar = K vbar + h^3 gE V (terms given as None are omitted)."""
+        import torch
+        ref = vbar if vbar is not None else V
+        if ref is None:
+            raise ValueError("vbar or (V, gE) must be given")
+        for t, nm in ((vbar, "vbar"), (V, "V")):
+            if t is not None:
+                self._check_tensor(t, nm)
+        if (V is None) != (gE is None):
+            raise ValueError("V and gE must be given together")
+        if gE is not None and (gE.dtype != torch.float64 or not gE.is_cuda or gE.numel() != 1):
+            raise ValueError("gE must be a one-element float64 CUDA tensor")
+        if out is None:
+            out = torch.empty_like(ref)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(_lib.ps_solve_vjp(self._h, ptr(vbar), ptr(V), ptr(gE), ptr(out), _stream_handle(stream)))
         return out
 
     def solve_host(self, rho_host, V_host=None, stream=None):

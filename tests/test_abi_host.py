@@ -131,3 +131,7 @@ def test_algorithmic_bytes_256_free_fp32():
     expect = 2 * n * 4 + 8 * 4 * c * 256 * (256 + L) + 4 * c * 257 * 257
     assert info.alg_bytes == expect
     assert abs(info.alg_bytes / 1e9 - 1.819) < 1e-3
+
+
+def test_autotune_rejects_null_plan(lib):
+    assert lib.ps_plan_autotune(None, 5, None) == 1

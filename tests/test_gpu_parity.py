@@ -218,3 +218,21 @@ def test_parity_fast_kernels_fp32(torch_cuda, n, bc):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=sum(n), noise=1e-3, subtract_mean="p" in bc)
     V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
     _check(V, E, rho, bc, 0.25, "f32")
+
+
+@pytest.mark.parametrize("n,bc,dtype", [((60, 37, 29), "fff", "f32"), ((50, 44, 70), "pff", "f32"),
+                                        ((33, 40, 27), "ppf", "f64")])
+def test_autotuned_plan_matches_oracle(torch_cuda, n, bc, dtype):
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    plan = psolver.Plan(n, bc, 0.3, dtype, autotune=True)
+    L = list(plan.info().L)
+    for j in range(3):
+        if bc[j] == "p":
+            assert L[j] == n[j]
+        else:
+            assert L[j] >= 2 * n[j] - 1
+    rho = synth.gaussian_mixture(n, 0.3, 4, seed=3, noise=1e-3, subtract_mean="p" in bc)
+    r = torch.from_numpy(rho.astype(_np_dtype(dtype))).cuda()
+    V, E = plan.solve(r)
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, dtype)
