@@ -170,6 +170,7 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
   p->st[1] = factorize(p->L[1]);
   p->st[2] = factorize(p->L[2]);
   p->ldc = round_up((size_t)p->c, p->dtype == PS_F32 ? 16 : 8);
+  p->ldk = round_up((size_t)p->c, 16);
   return PS_OK;
 }
 
@@ -227,7 +228,7 @@ int ps_kernel_build(ps_plan p, void* stream) {
   const size_t n2 = p->n[1], n3 = p->n[2];
   const size_t szA = p->ldc * n2 * n3 * csz;
   const size_t szB = p->ldc * (size_t)p->L[1] * n3 * csz;
-  const size_t szK = (size_t)p->c * (p->H[1] + 1) * (p->H[2] + 1) * p->esz;
+  const size_t szK = p->ldk * (p->H[1] + 1) * (p->H[2] + 1) * p->esz;
   struct { void** ptr; size_t bytes; const char* what; } allocs[] = {
       {&p->A, szA, "workspace A"},
       {&p->B, szB, "workspace B"},
@@ -267,8 +268,9 @@ int ps_kernel_get(ps_plan p, void* dst, void* stream) {
   if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
   if (!dst) return fail(PS_ERR_ARG, "dst is NULL");
   DeviceGuard g(p->device);
-  const size_t bytes = (size_t)p->c * (p->H[1] + 1) * (p->H[2] + 1) * p->esz;
-  cudaError_t e = cudaMemcpyAsync(dst, p->K, bytes, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)p->c * p->esz, p->K, p->ldk * p->esz, (size_t)p->c * p->esz,
+                                    (size_t)(p->H[1] + 1) * (p->H[2] + 1), cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "copy K^F");
   return PS_OK;
 }

@@ -60,6 +60,7 @@ struct FastArgs {
   int L1, L2;
   int n1, nrows;          // x passes: row length (reals) and row count
   long long ldc;          // row pitch of A / B
+  int ldk;                // kx pitch of the K^F octant
   long long src_plane, src_elem;
   long long dst_plane, dst_elem;
   long long kz_stride;    // z pass: (L2/2 + 1) * c, the kz stride of the K^F octant
@@ -91,10 +92,11 @@ struct ps_plan_s {
   int device;
   size_t esz;    // bytes per real element
   size_t ldc;    // row pitch of the spectral work arrays, complex elements
+  size_t ldk;    // kx pitch of the stored K^F octant (c rounded up to 16), real elements
   // device memory owned by the plan
   void* A;       // [n3][n2][ldc] complex: x-transformed rows (passes 1/2 and 4/5)
   void* B;       // [n3][L2][ldc] complex: y-transformed planes (passes 2..4)
-  void* K;       // [H3+1][H2+1][c] real: K^F / (L1 L2 L3), even octant
+  void* K;       // [H3+1][H2+1][ldk] real: K^F / (L1 L2 L3), even octant (kx < c used)
   void* tw[3];   // W_{L_j}^k, k < L_j, complex, per axis
   void* tw4z;    // paired z twiddles of the packed z kernel (T*T float4), or NULL
   int zsoa_T;    // T of the packed z kernel (L3 = 2 T^2), 0 if not used

@@ -40,7 +40,8 @@ __device__ __forceinline__ int paired_ky(int y, int L2) {
 }
 
 template <int P, int Q, int KIND, bool HALF>
-__global__ void __launch_bounds__(kTK*(P < Q ? P : Q), kTK * (P < Q ? P : Q) <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
+                                  kTK * (P < Q ? P : Q) <= 256 ? (KIND == 2 ? 2 : 3) : 1)
     k_strided(const void* src_v, void* dst_v, const float* __restrict__ K, const float2* __restrict__ tw,
               FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
   constexpr int L = P * Q;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), kTK * (P < Q ? P : Q) <= 
       // V^F = K^F rho^F on the even octant of K^F; energy sum w(kx) K |rho^F|^2
       const int ky = yblk;
       const int kyo = min(ky, a.L2 - ky);
-      const float* Kp = K + (long long)kyo * a.c + kx;
+      const float* Kp = K + (long long)kyo * a.ldk + kx;
 #pragma unroll
       for (int v = 0; v < NK; ++v) {
         const int k1 = j + T * v;

@@ -28,13 +28,14 @@ __device__ __forceinline__ float2 xmulc(float2 a, float2 b) {
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// shared memory per row: exchange tile P x (Q + 1) and the row spectrum (M + 1)
+// shared memory per row: the exchange tile P x (Q + 1) and the row spectrum
+// (M + 1) share one region (a barrier separates their uses)
 template <int P, int Q>
 struct XShape {
   static constexpr int M = P * Q;
   static constexpr int T = P < Q ? P : Q;
   static constexpr int EX = P * (Q + 1);
-  static constexpr int ROW = EX + M + 1;
+  static constexpr int ROW = EX > M + 1 ? EX : M + 1;
 };
 
 template <int P, int Q, int TR, bool HALF>
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   const int row = blockIdx.x * TR + r;
   const bool valid = row < a.nrows;
   float2* ex = sh + r * S::ROW;
-  float2* zr = ex + S::EX;
+  float2* zr = ex;  // reused for the row spectrum once the exchange has been read
   const float2* z = reinterpret_cast<const float2*>(static_cast<const float*>(src_v) + (long long)row * a.n1);
   float2* X = static_cast<float2*>(dst_v) + (long long)row * a.ldc;
 
@@ -69,15 +70,19 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     for (int k1 = 0; k1 < P; ++k1) ex[k1 * (Q + 1) + b] = y[k1];
   }
   __syncthreads();
+  float2 x[NK][Q];
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+#pragma unroll
+    for (int b = 0; b < Q; ++b) x[v][b] = ex[(j + T * v) * (Q + 1) + b];
+  }
+  __syncthreads();  // the exchange has been read: its space takes the row spectrum
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
     const int k1 = j + T * v;
-    float2 x[Q];
+    rdft<Q, -1, false>(x[v]);
 #pragma unroll
-    for (int b = 0; b < Q; ++b) x[b] = ex[k1 * (Q + 1) + b];
-    rdft<Q, -1, false>(x);
-#pragma unroll
-    for (int k2 = 0; k2 < Q; ++k2) zr[k1 + P * k2] = x[k2];
+    for (int k2 = 0; k2 < Q; ++k2) zr[k1 + P * k2] = x[v][k2];
   }
   __syncthreads();
   if (!valid) return;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   const int row = blockIdx.x * TR + r;
   const bool valid = row < a.nrows;
   float2* ex = sh + r * S::ROW;
-  float2* xr = ex + S::EX;
+  float2* xr = ex;  // the row spectrum first, the exchange tile after a barrier
   const float2* X = static_cast<const float2*>(src_v) + (long long)row * a.ldc;
   float2* z = reinterpret_cast<float2*>(static_cast<float*>(dst_v) + (long long)row * a.n1);
 
@@ -121,23 +126,28 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     if (j == 0) xr[M] = xny;
   }
   __syncthreads();
+  float2 x[NK][Q];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
     const int k1 = j + T * v;
-    float2 x[Q];
 #pragma unroll
     for (int k2 = 0; k2 < Q; ++k2) {
       const int k = k1 + P * k2;
       const float2 xk = xr[k], xm = xr[M - k];
       const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
       const float2 o = xmulc(make_float2(xk.x - xm.x, xk.y + xm.y), __ldg(&tw[k]));
-      x[k2] = make_float2(e.x - o.y, e.y + o.x);
+      x[v][k2] = make_float2(e.x - o.y, e.y + o.x);
     }
-    rdft<Q, 1, false>(x);
+  }
+  __syncthreads();  // the row spectrum has been read: its space takes the exchange
 #pragma unroll
-    for (int b = 1; b < Q; ++b) x[b] = xmulc(x[b], __ldg(&tw[2 * b * k1]));
+  for (int v = 0; v < NK; ++v) {
+    const int k1 = j + T * v;
+    rdft<Q, 1, false>(x[v]);
 #pragma unroll
-    for (int b = 0; b < Q; ++b) ex[k1 * (Q + 1) + b] = x[b];
+    for (int b = 1; b < Q; ++b) x[v][b] = xmulc(x[v][b], __ldg(&tw[2 * b * k1]));
+#pragma unroll
+    for (int b = 0; b < Q; ++b) ex[k1 * (Q + 1) + b] = x[v][b];
   }
   __syncthreads();
 #pragma unroll
@@ -208,7 +218,8 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   base.n1 = n1;
   base.nrows = n2 * n3;
   base.ldc = ldc;
-  base.kz_stride = (long long)(p->H[1] + 1) * p->c;
+  base.kz_stride = (long long)(p->H[1] + 1) * p->ldk;
+  base.ldk = (int)p->ldk;
   const int ntk = (p->c + 15) / 16;
 
   // x passes: L1 = 2M, n1 = M (free) or 2M (periodic)
@@ -243,23 +254,44 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       if ((e = set(P4, f1, grid, threads, smem, inv)) != cudaSuccess) return e;
     }
   }
-  // z pass: PS_ZPASS=soa selects the packed FP32x2 kernel where it exists
+  // z pass: the persistent prefetching packed kernel where it exists (L3 = 512),
+  // else the packed kernel (L3 = 128), else the unpacked one. PS_ZPASS=soa or
+  // PS_ZPASS=strided selects a simpler kernel (diagnostics and comparisons).
   if (pow2(L3) && (n3 == L3 / 2 || n3 == L3)) {
     const bool half = n3 == L3 / 2;
     int threads;
     size_t smem;
     const char* zp = getenv("PS_ZPASS");
-    const bool allow_soa = zp && strcmp(zp, "soa") == 0;
-    const void* f = allow_soa ? zsoa_kernel(L3, half, &threads, &smem) : nullptr;
+    const bool allow_soa = !(zp && strcmp(zp, "strided") == 0);
+    const char* ztk = getenv("PS_ZTK");
+    const int zsoa_tk = (ztk && atoi(ztk) == 8) ? 8 : 16;
+    const bool pipe = allow_soa && !(zp && strcmp(zp, "soa") == 0);
+    const void* f = pipe ? zpipe_kernel(L3, half, &threads, &smem) : nullptr;
+    const bool persistent = f != nullptr;
+    if (!f && allow_soa) f = zsoa_kernel(L3, half, zsoa_tk, &threads, &smem);
     p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;
+    const int ztile = f && !persistent ? zsoa_tk : 16;
     if (!f) f = strided_kernel(L3, 2, half, &threads, &smem);
     if (f) {
       FastArgs z = base;
       z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;      // B[z][ky][kx], line along z
       z.dst_plane = ldc; z.dst_elem = (long long)L2 * ldc;
-      dim3 grid(ntk, L2);
+      dim3 grid((p->c + ztile - 1) / ztile, L2);
+      if (persistent) {
+        // one wave of resident CTAs walks all tiles
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+          return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem)) != cudaSuccess) return e;
+        const long long tiles = (long long)grid.x * grid.y;
+        const long long g = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+        grid = dim3((unsigned)(g < tiles ? g : tiles), 1);
+      }
       if ((e = set(P3, f, grid, threads, smem, z)) != cudaSuccess) return e;
-      p->cfg[P3].tk = 16;
+      p->cfg[P3].tk = ztile;
     }
   }
   return cudaSuccess;

@@ -69,10 +69,8 @@ __device__ __forceinline__ int paired_ky_soa(int y, int L2) {
 
 }  // namespace
 
-constexpr int kTKs = 16;  // lines per CTA
-
-template <int T, bool HALF>
-__global__ void __launch_bounds__(kTKs * T, 2)
+template <int T, bool HALF, int kTKs>
+__global__ void __launch_bounds__(kTKs * T, 512 / (kTKs * T))
     k_zconv_soa(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
                 FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
   constexpr int P = T, Q = 2 * T, L = P * Q;
@@ -114,7 +112,7 @@ __global__ void __launch_bounds__(kTKs * T, 2)
 
   // V^F = K^F rho^F on the even octant; energy sum w(kx) K |rho^F|^2
   const int kyo = min(ky, a.L2 - ky);
-  const float* Kp = K + (long long)kyo * a.c + kx;
+  const float* Kp = K + (long long)kyo * a.ldk + kx;
   float2 e2 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int m = 0; m < T; ++m) {
@@ -153,16 +151,171 @@ __global__ void __launch_bounds__(kTKs * T, 2)
   if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
 }
 
-const void* zsoa_kernel(int L, bool half, int* threads, size_t* smem) {
+template <int T, int TK>
+static const void* pick_zsoa(bool half) {
+  return half ? (const void*)k_zconv_soa<T, true, TK> : (const void*)k_zconv_soa<T, false, TK>;
+}
+
+const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
+  const void* fn = nullptr;
+  int T = 0;
+  if (tk != 8 && tk != 16) return nullptr;
+  switch (L) {
+    case 128: fn = tk == 8 ? pick_zsoa<8, 8>(half) : pick_zsoa<8, 16>(half); T = 8; break;
+    case 512: fn = tk == 8 ? pick_zsoa<16, 8>(half) : pick_zsoa<16, 16>(half); T = 16; break;
+    default: return nullptr;
+  }
+  *threads = tk * T;
+  *smem = (size_t)T * T * tk * sizeof(float4);
+  return fn;
+}
+
+// ---------------------------------------------------------------- pipelined
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Persistent version of k_zconv_soa (16 lines per tile): each CTA walks tiles
+// (kx tile fastest, then the paired ky rows) and copies the next tile's n3
+// input rows and its K^F octant slice into shared memory with cp.async while
+// it computes the current tile, so the global-load latency of one tile
+// overlaps the arithmetic of the previous one.
+template <int T, bool HALF>
+__global__ void __launch_bounds__(16 * T, 2)
+    k_zconv_pipe(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
+                 FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
+  constexpr int TK = 16;
+  constexpr int P = T, Q = 2 * T, L = P * Q;
+  constexpr int NA = HALF ? P / 2 : P;
+  constexpr int ROWS = NA * Q;          // input rows per line (n3)
+  constexpr int KROWS = L / 2 + 1;      // rows of the K^F octant
+  extern __shared__ float4 smem4[];
+  float4* sh4 = smem4;                                              // exchange [T * P][TK]
+  float2* stage = reinterpret_cast<float2*>(smem4 + T * P * TK);    // inputs [ROWS][TK]
+  float* kstage = reinterpret_cast<float*>(stage + ROWS * TK);      // K^F [KROWS][TK]
+  const int t = threadIdx.x % TK;
+  const int j = threadIdx.x / TK;
+  const int ntk = (a.c + TK - 1) / TK;
+  const int ntiles = ntk * a.L2;
+  float2* const base = static_cast<float2*>(line_v);
+  const long long es = a.src_elem;
+
+  auto issue_input = [&](int tile) {
+    const int kx0 = (tile % ntk) * TK;
+    const int ky = paired_ky_soa(tile / ntk, a.L2);
+    const float2* src = base + ky * a.src_plane + kx0;
+    for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
+      const int row = q / (TK / 2), part = q % (TK / 2);
+      cp_async16(stage + row * TK + 2 * part, src + (long long)row * es + 2 * part);
+    }
+  };
+  auto issue_k = [&](int tile) {
+    const int kx0 = (tile % ntk) * TK;
+    const int ky = paired_ky_soa(tile / ntk, a.L2);
+    const int kyo = min(ky, a.L2 - ky);
+    const float* src = K + (long long)kyo * a.ldk + kx0;
+    for (int q = threadIdx.x; q < KROWS * (TK / 4); q += blockDim.x) {
+      const int row = q / (TK / 4), part = q % (TK / 4);
+      cp_async16(kstage + row * TK + 4 * part, src + (long long)row * a.kz_stride + 4 * part);
+    }
+  };
+
+  float eacc = 0.f;
+  int tile = blockIdx.x;
+  if (tile < ntiles) {
+    issue_input(tile);
+    issue_k(tile);
+  }
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    const int kx = (tile % ntk) * TK + t;
+    const bool valid = kx < a.c;
+    const int ky = paired_ky_soa(tile / ntk, a.L2);
+    float2* line = base + ky * a.src_plane + kx;
+    cp_async_wait_all();
+    __syncthreads();  // this tile's inputs and K^F slice have landed
+
+    c2 y[P];
+#pragma unroll
+    for (int aa = 0; aa < P; ++aa) {
+      y[aa] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      if (aa < NA && valid) {
+        const float2 u0 = stage[(j + Q * aa) * TK + t];
+        const float2 u1 = stage[(j + T + Q * aa) * TK + t];
+        y[aa] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+      }
+    }
+    __syncthreads();  // the input stage is free
+    if (next < ntiles) issue_input(next);
+    cp_async_commit();
+
+    soa::dft2<P, -1, HALF>(y);
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], __ldg(&tw4[j * P + k1]));
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) sh4[(j * P + k1) * TK + t] = pack(y[k1]);
+    __syncthreads();
+
+    c2 z[T];
+#pragma unroll
+    for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * TK + t]);
+    dif_all<T>(z, std::make_integer_sequence<int, T>{});
+    soa::dft2<T, -1, false>(z);
+
+    float2 e2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < T; ++m) {
+      const int kz0 = j + P * 2 * m, kz1 = kz0 + P;
+      const int o0 = kz0 <= L / 2 ? kz0 : L - kz0, o1 = kz1 <= L / 2 ? kz1 : L - kz1;
+      const float2 kk = valid ? make_float2(kstage[o0 * TK + t], kstage[o1 * TK + t]) : make_float2(0.f, 0.f);
+      const float2 p2 = soa::fma2(z[m].re, z[m].re, soa::mul2(z[m].im, z[m].im));
+      e2 = soa::fma2(kk, p2, e2);
+      z[m] = {soa::mul2(z[m].re, kk), soa::mul2(z[m].im, kk)};
+    }
+    eacc += (e2.x + e2.y) * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
+
+    soa::dft2<T, 1, false>(z);
+    dit_all<T>(z, std::make_integer_sequence<int, T>{});
+#pragma unroll
+    for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], __ldg(&tw4[b * P + j]));
+    __syncthreads();  // the forward exchange and the K^F stage have been read
+    if (next < ntiles) issue_k(next);
+    cp_async_commit();
+#pragma unroll
+    for (int b = 0; b < T; ++b) sh4[(b * P + j) * TK + t] = pack(z[b]);
+    __syncthreads();
+
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * TK + t]);
+    soa::dft2<P, 1, false>(y);
+    if (valid) {
+#pragma unroll
+      for (int aa = 0; aa < NA; ++aa) {
+        line[(long long)(j + Q * aa) * es] = make_float2(y[aa].re.x, y[aa].im.x);
+        line[(long long)(j + T + Q * aa) * es] = make_float2(y[aa].re.y, y[aa].im.y);
+      }
+    }
+  }
+  cp_async_wait_all();
+  if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
+}
+
+const void* zpipe_kernel(int L, bool half, int* threads, size_t* smem) {
   const void* fn = nullptr;
   int T = 0;
   switch (L) {
-    case 128: fn = half ? (const void*)k_zconv_soa<8, true> : (const void*)k_zconv_soa<8, false>; T = 8; break;
-    case 512: fn = half ? (const void*)k_zconv_soa<16, true> : (const void*)k_zconv_soa<16, false>; T = 16; break;
+    case 512: fn = half ? (const void*)k_zconv_pipe<16, true> : (const void*)k_zconv_pipe<16, false>; T = 16; break;
     default: return nullptr;
   }
-  *threads = kTKs * T;
-  *smem = (size_t)T * T * kTKs * sizeof(float4);
+  const int NA = half ? T / 2 : T;
+  *threads = 16 * T;
+  *smem = (size_t)T * T * 16 * sizeof(float4) + (size_t)NA * 2 * T * 16 * sizeof(float2) +
+          (size_t)(T * T + 1) * 16 * sizeof(float);
   return fn;
 }
 

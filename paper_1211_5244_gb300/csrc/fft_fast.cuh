@@ -20,8 +20,12 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 // Returns the kernel for an x pass (real length 2M): kind 0 R2C, 1 C2R.
 const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, size_t* smem);
 
-// The packed FP32x2 z-pass kernel for L3 = 2 T^2 (T = 8, 16), or nullptr.
-const void* zsoa_kernel(int L, bool half, int* threads, size_t* smem);
+// The packed FP32x2 z-pass kernel for L3 = 2 T^2 (T = 8, 16) with tk lines
+// per CTA (8 or 16), or nullptr.
+const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem);
+
+// The persistent, prefetching packed z-pass kernel (L3 = 512), or nullptr.
+const void* zpipe_kernel(int L, bool half, int* threads, size_t* smem);
 
 // Fills p->cfg[k].fast / fn / grid / block / smem / fa for the passes covered.
 cudaError_t configure_fast_f32(ps_plan_s* p);

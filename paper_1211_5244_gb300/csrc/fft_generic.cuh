@@ -5,8 +5,8 @@
 // Each stage of radix R (current sub-length Ns) takes butterfly b from the
 // inputs b + r * N / R, multiplies input r by W_N^{r * (b mod Ns) * N/(Ns R)},
 // does an R-point DFT and writes output q to ((b / Ns) * Ns * R + b mod Ns +
-// q * Ns): after the last stage the result is in natural order. Radices 2, 4
-// and 8 have closed-form butterflies; any other factor (3, 5, 7 or a prime up
+// q * Ns): after the last stage the result is in natural order. Radices 2, 3,
+// 4, 5 and 8 have closed-form butterflies; any other factor (7 or a prime up
 // to 4096) uses the direct R-point sum. Lanes of a warp take consecutive
 // lines t, so every shared-memory access of a warp is contiguous.
 #pragma once
@@ -39,6 +39,41 @@ __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
   v2 = csub(s02, s13);
   v1 = cadd(d02, r);
   v3 = csub(d02, r);
+}
+
+// 3-point DFT: y0 = a + s, y1,2 = (a - s/2) +- DIR i (sqrt3/2)(b - c), s = b + c.
+template <int DIR, typename C>
+__device__ __forceinline__ void dft3(C& v0, C& v1, C& v2) {
+  using R = decltype(v0.x);
+  const R h = R(0.86602540378443864676);  // sqrt(3)/2
+  const C s = cadd(v1, v2), d = csub(v1, v2);
+  const C t = mk(v0.x - R(0.5) * s.x, v0.y - R(0.5) * s.y);
+  const C u = cmul_i<DIR>(cscale(d, h));
+  v0 = cadd(v0, s);
+  v1 = cadd(t, u);
+  v2 = csub(t, u);
+}
+
+// 5-point DFT with cos(2 pi / 5), cos(4 pi / 5), sin(2 pi / 5), sin(4 pi / 5):
+// y1,4 = t1 +- DIR i u1, y2,3 = t2 +- DIR i u2 with
+// t1 = x0 + c1 a1 + c2 a2, t2 = x0 + c2 a1 + c1 a2, u1 = s1 b1 + s2 b2,
+// u2 = s2 b1 - s1 b2, a1,b1 = x1 +- x4, a2,b2 = x2 +- x3.
+template <int DIR, typename C>
+__device__ __forceinline__ void dft5(C* v) {
+  using R = decltype(v[0].x);
+  const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);
+  const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);
+  const C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+  const C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+  const C t1 = mk(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+  const C t2 = mk(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+  const C u1 = cmul_i<DIR>(mk(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+  const C u2 = cmul_i<DIR>(mk(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+  v[0] = cadd(v[0], cadd(a1, a2));
+  v[1] = cadd(t1, u1);
+  v[4] = csub(t1, u1);
+  v[2] = cadd(t2, u2);
+  v[3] = csub(t2, u2);
 }
 
 // 8-point DFT: two 4-point DFTs (even / odd inputs) joined by W_8^k.
@@ -98,6 +133,27 @@ __device__ cpx<T>* stockham(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const 
         out[Ns * ldt] = v1;
         out[2 * Ns * ldt] = v2;
         out[3 * Ns * ldt] = v3;
+      } else if (R == 3) {
+        C v0 = in[0], v1 = in[NR * ldt], v2 = in[2 * NR * ldt];
+        if (e) {
+          v1 = twid<DIR>(v1, tw, e, tws);
+          v2 = twid<DIR>(v2, tw, 2 * e, tws);
+        }
+        dft3<DIR>(v0, v1, v2);
+        out[0] = v0;
+        out[Ns * ldt] = v1;
+        out[2 * Ns * ldt] = v2;
+      } else if (R == 5) {
+        C v[5];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) v[r] = in[r * NR * ldt];
+        if (e) {
+#pragma unroll
+          for (int r = 1; r < 5; ++r) v[r] = twid<DIR>(v[r], tw, r * e, tws);
+        }
+        dft5<DIR>(v);
+#pragma unroll
+        for (int r = 0; r < 5; ++r) out[r * Ns * ldt] = v[r];
       } else if (R == 8) {
         C v[8];
 #pragma unroll

@@ -202,10 +202,12 @@ __global__ void cos_transform_kernel(const double* __restrict__ in, double* __re
   }
 }
 
+// dense octant (kx fastest, D0 = c columns) -> K with row pitch ldk
 template <typename T>
-__global__ void store_kernel(const double* __restrict__ M, T* __restrict__ K, size_t n, double scale) {
+__global__ void store_kernel(const double* __restrict__ M, T* __restrict__ K, size_t n, int D0, size_t ldk,
+                             double scale) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    K[i] = (T)(M[i] * scale);
+    K[(i / D0) * ldk + i % D0] = (T)(M[i] * scale);
 }
 
 template <typename T>
@@ -283,10 +285,14 @@ cudaError_t build_kernel(ps_plan_s* p, cudaStream_t s) {
   }
   {
     const double scale = 1.0 / ((double)p->L[0] * (double)p->L[1] * (double)p->L[2]);
+    // the pitch padding stays zero
+    e = cudaMemsetAsync(p->K, 0, p->ldk * (size_t)D1 * D2 * p->esz, s);
+    if (e != cudaSuccess) goto done;
     if (p->dtype == PS_F32)
-      store_kernel<float><<<grid_for(total), 256, 0, s>>>(M0, static_cast<float*>(p->K), total, scale);
+      store_kernel<float><<<grid_for(total), 256, 0, s>>>(M0, static_cast<float*>(p->K), total, D0, p->ldk, scale);
     else
-      store_kernel<double><<<grid_for(total), 256, 0, s>>>(M0, static_cast<double*>(p->K), total, scale);
+      store_kernel<double><<<grid_for(total), 256, 0, s>>>(M0, static_cast<double*>(p->K), total, D0, p->ldk,
+                                                            scale);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) goto done;
   e = cudaStreamSynchronize(s);

@@ -35,7 +35,7 @@ struct GenArgs {
   int n1, n2, n3;
   int L1, L2, L3;
   int c, H2, H3;
-  int ldc;
+  int ldc, ldk;
   int tk, ldt;
   int N;    // transform length of this pass
   int tws;  // twiddle-table stride (table length / N)
@@ -153,8 +153,8 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   C* other = (spec == buf0) ? buf1 : buf0;
   // multiply by the octant of K^F; accumulate w(kx) K |rho^F|^2 for the energy
   const int kyo = min(ky, a.L2 - ky);
-  const T* Krow = K + (size_t)kyo * a.c + kx0;
-  const size_t kzstride = (size_t)(a.H2 + 1) * a.c;
+  const T* Krow = K + (size_t)kyo * a.ldk + kx0;
+  const size_t kzstride = (size_t)(a.H2 + 1) * a.ldk;
   T eacc = T(0);
   for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
     const int t = w % a.tk, kz = w / a.tk;
@@ -299,6 +299,7 @@ static GenArgs gen_args(const ps_plan_s* p, int pass) {
   a.L1 = p->L[0]; a.L2 = p->L[1]; a.L3 = p->L[2];
   a.c = p->c; a.H2 = p->H[1]; a.H3 = p->H[2];
   a.ldc = (int)p->ldc;
+  a.ldk = (int)p->ldk;
   a.tk = p->cfg[pass].tk; a.ldt = p->cfg[pass].ldt;
   const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
   const bool even1 = (p->L[0] % 2) == 0;

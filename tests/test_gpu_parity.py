@@ -210,6 +210,9 @@ FAST_CASES = [
     ((6, 1024, 4), "ppf"),     # y L=1024 full
     ((1024, 4, 6), "pff"),     # x M=512 full
     ((512, 6, 4), "fff"),      # x M=512 half
+    ((16, 24, 64), "fff"),     # z L=128 half
+    ((12, 10, 128), "ffp"),    # z L=128 full
+    ((20, 12, 256), "pff"),    # z L=512 half
 ]
 
 
