@@ -236,6 +236,23 @@ int ps_plan_set_profiling(ps_plan plan, int enable);
  */
 int ps_plan_pass_times(ps_plan plan, double* ms, int* count);
 
+/*
+ * ps_solve_host_stream -- ps_solve_host for `count` densities with the
+ * transfers overlapped: while density i is solved, density i+1 is copied to
+ * the device and the potential of density i-1 is copied back (the pipelining
+ * of successive densities proposed in the paper's conclusions, §5).
+ *   count >= 0              number of densities
+ *   rho_host[i], V_host[i]  host pointers, n1*n2*n3 dtype elements each; use
+ *                           pinned memory, or the copies cannot overlap
+ *   ehartree_host           NULL or host array of count doubles
+ * The plan holds two device buffer sets and three streams of its own
+ * (allocated on first use). The batch starts after the work already queued on
+ * `stream`, and the call waits for the whole batch before returning.
+ * Errors as ps_solve_host.
+ */
+int ps_solve_host_stream(ps_plan plan, int count, const void* const* rho_host, void* const* V_host,
+                         double* ehartree_host, void* stream);
+
 /* ps_plan_destroy -- free the plan and its device memory. NULL is a no-op. */
 int ps_plan_destroy(ps_plan plan);
 

@@ -59,9 +59,9 @@ struct DeviceGuard {
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 void free_device(ps_plan_s* p) {
-  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2], &p->tw4z,
+  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2], &p->tw4z, &p->twx,
                    reinterpret_cast<void**>(&p->partials), reinterpret_cast<void**>(&p->counter),
-                   &p->d_rho, &p->d_V, reinterpret_cast<void**>(&p->d_E)};
+                   &p->d_rho, &p->d_V, reinterpret_cast<void**>(&p->d_E), &p->d_rho2, &p->d_V2};
   for (void** b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -239,6 +239,7 @@ int ps_kernel_build(ps_plan p, void* stream) {
       {reinterpret_cast<void**>(&p->partials), (size_t)p->npart * sizeof(double), "energy partials"},
       {reinterpret_cast<void**>(&p->counter), sizeof(unsigned), "energy counter"},
       {&p->tw4z, p->zsoa_T ? (size_t)p->zsoa_T * p->zsoa_T * 16 : 0, "paired z twiddles"},
+      {&p->twx, p->xP ? (size_t)p->xP * p->xP * 8 : 0, "x twiddle matrix"},
   };
   size_t total = 0;
   for (auto& a : allocs) {
@@ -361,7 +362,7 @@ int ps_solve_host(ps_plan p, const void* rho_host, void* V_host, double* ehartre
   if (!p->d_rho) {
     if ((e = cudaMalloc(&p->d_rho, bytes)) != cudaSuccess) return cuda_fail(e, "staging rho");
     if ((e = cudaMalloc(&p->d_V, bytes)) != cudaSuccess) return cuda_fail(e, "staging V");
-    if ((e = cudaMalloc(&p->d_E, sizeof(double))) != cudaSuccess) return cuda_fail(e, "staging E");
+    if ((e = cudaMalloc(&p->d_E, 2 * sizeof(double))) != cudaSuccess) return cuda_fail(e, "staging E");
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((e = cudaMemcpyAsync(p->d_rho, rho_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -403,11 +404,81 @@ int ps_plan_pass_times(ps_plan p, double* ms, int* count) {
   return PS_OK;
 }
 
+int ps_solve_host_stream(ps_plan p, int count, const void* const* rho_host, void* const* V_host,
+                         double* ehartree_host, void* stream) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (count < 0) return fail(PS_ERR_ARG, "count < 0");
+  if (count == 0) return PS_OK;
+  if (!rho_host || !V_host) return fail(PS_ERR_ARG, "NULL array argument");
+  for (int i = 0; i < count; ++i)
+    if (!rho_host[i] || !V_host[i]) return fail(PS_ERR_ARG, "item %d: host pointer is NULL", i);
+  if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
+  DeviceGuard g(p->device);
+  const size_t bytes = grid_points(p) * p->esz;
+  cudaError_t e;
+  if (!p->d_rho) {
+    if ((e = cudaMalloc(&p->d_rho, bytes)) != cudaSuccess) return cuda_fail(e, "staging rho");
+    if ((e = cudaMalloc(&p->d_V, bytes)) != cudaSuccess) return cuda_fail(e, "staging V");
+    if ((e = cudaMalloc(&p->d_E, 2 * sizeof(double))) != cudaSuccess) return cuda_fail(e, "staging E");
+  }
+  if (!p->d_rho2) {
+    if ((e = cudaMalloc(&p->d_rho2, bytes)) != cudaSuccess) return cuda_fail(e, "staging rho");
+    if ((e = cudaMalloc(&p->d_V2, bytes)) != cudaSuccess) return cuda_fail(e, "staging V");
+  }
+  if (!p->hs[0]) {
+    for (int k = 0; k < 3; ++k)
+      if ((e = cudaStreamCreateWithFlags(&p->hs[k], cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "transfer streams");
+    for (int k = 0; k < 7; ++k)
+      if ((e = cudaEventCreateWithFlags(&p->hev[k], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "transfer events");
+  }
+  cudaStream_t up = p->hs[0], comp = p->hs[1], down = p->hs[2];
+  cudaEvent_t* ev_in = p->hev;        // [2] upload of slot done
+  cudaEvent_t* ev_comp = p->hev + 2;  // [2] solve of slot done (its rho buffer is free)
+  cudaEvent_t* ev_out = p->hev + 4;   // [2] download of slot done (its V buffer is free)
+  cudaEvent_t start = p->hev[6];
+  void* drho[2] = {p->d_rho, p->d_rho2};
+  void* dV[2] = {p->d_V, p->d_V2};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+#define PS_TRY(call, what)                          \
+  do {                                              \
+    if ((e = (call)) != cudaSuccess) return cuda_fail(e, what); \
+  } while (0)
+  PS_TRY(cudaEventRecord(start, s), "ordering");
+  for (int k = 0; k < 3; ++k) PS_TRY(cudaStreamWaitEvent(p->hs[k], start, 0), "ordering");
+  for (int i = 0; i < count; ++i) {
+    const int b = i & 1;
+    if (i >= 2) PS_TRY(cudaStreamWaitEvent(up, ev_comp[b], 0), "ordering");
+    PS_TRY(cudaMemcpyAsync(drho[b], rho_host[i], bytes, cudaMemcpyHostToDevice, up), "copy rho to device");
+    PS_TRY(cudaEventRecord(ev_in[b], up), "ordering");
+    PS_TRY(cudaStreamWaitEvent(comp, ev_in[b], 0), "ordering");
+    if (i >= 2) PS_TRY(cudaStreamWaitEvent(comp, ev_out[b], 0), "ordering");
+    int rc = run_solve(p, drho[b], dV[b], ehartree_host ? p->d_E + b : nullptr, comp);
+    if (rc != PS_OK) return fail(rc, "item %d: %s", i, ps_last_error());
+    PS_TRY(cudaEventRecord(ev_comp[b], comp), "ordering");
+    PS_TRY(cudaStreamWaitEvent(down, ev_comp[b], 0), "ordering");
+    PS_TRY(cudaMemcpyAsync(V_host[i], dV[b], bytes, cudaMemcpyDeviceToHost, down), "copy V to host");
+    if (ehartree_host)
+      PS_TRY(cudaMemcpyAsync(ehartree_host + i, p->d_E + b, sizeof(double), cudaMemcpyDeviceToHost, down),
+             "copy E to host");
+    PS_TRY(cudaEventRecord(ev_out[b], down), "ordering");
+  }
+  PS_TRY(cudaStreamSynchronize(down), "transfer pipeline");
+  PS_TRY(cudaStreamSynchronize(comp), "transfer pipeline");
+#undef PS_TRY
+  return PS_OK;
+}
+
 int ps_plan_destroy(ps_plan p) {
   if (!p) return PS_OK;
   batch_forget_plan(p);
   {
     DeviceGuard g(p->device);
+    for (int k = 0; k < 3; ++k)
+      if (p->hs[k]) cudaStreamDestroy(p->hs[k]);
+    for (int k = 0; k < 7; ++k)
+      if (p->hev[k]) cudaEventDestroy(p->hev[k]);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     p->events.clear();
     free_device(p);

@@ -189,4 +189,159 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
   return fn;
 }
 
+// ---------------------------------------------------------------- pipelined y
+
+__device__ __forceinline__ void cpa16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Persistent y pass (KIND 0 forward, 1 inverse), 16 lines per tile, tiles =
+// (kx tile, z plane) with kx fastest. The shared-memory tile serves twice: as
+// the landing area of the tile's input rows (copied with cp.async) and as the
+// exchange of the four-step transform. Once a tile's exchange has been read,
+// the next tile's rows are copied in while the last transform step and the
+// stores of the current tile run.
+template <int P, int Q, int KIND, bool HALF>
+__global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
+    k_ypipe(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a, double*,
+            unsigned*, double, double*) {
+  constexpr int L = P * Q;
+  constexpr int T = P < Q ? P : Q;
+  constexpr int NB = Q / T;
+  constexpr int NK = P / T;
+  constexpr int NA = HALF ? P / 2 : P;
+  constexpr int ROWS = KIND == 0 ? NA * Q : L;  // input rows of a line
+  extern __shared__ float2 sh[];               // [L][kTK]
+  const float2* src = static_cast<const float2*>(src_v);
+  float2* dst = static_cast<float2*>(dst_v);
+  const int t = threadIdx.x % kTK;
+  const int j = threadIdx.x / kTK;
+  const int ntk = (a.c + kTK - 1) / kTK;
+  const int ntiles = ntk * (int)a.nrows;  // nrows = number of z planes here
+
+  auto prefetch = [&](int tile) {
+    const int kx0 = (tile % ntk) * kTK;
+    const float2* sp = src + (long long)(tile / ntk) * a.src_plane + kx0;
+    for (int q = threadIdx.x; q < ROWS * (kTK / 2); q += blockDim.x) {
+      const int row = q / (kTK / 2), part = q % (kTK / 2);
+      cpa16(sh + row * kTK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
+    }
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile);
+  cpa_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    const int kx = (tile % ntk) * kTK + t;
+    const bool valid = kx < a.c;
+    float2* d = dst + (long long)(tile / ntk) * a.dst_plane + kx;
+    cpa_wait_all();
+    __syncthreads();  // the tile's rows have landed
+    float2 X[NK][Q];
+    if constexpr (KIND == 0) {
+      float2 y[NB][P];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int b = j + T * u;
+#pragma unroll
+        for (int aa = 0; aa < P; ++aa) {
+          y[u][aa] = make_float2(0.f, 0.f);
+          if (aa < NA && valid) y[u][aa] = sh[(b + Q * aa) * kTK + t];
+        }
+      }
+      __syncthreads();  // inputs read: the tile becomes the exchange
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int b = j + T * u;
+        rdft<P, -1, HALF>(y[u]);
+#pragma unroll
+        for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], __ldg(&tw[b * k1]));
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * kTK + t] = y[u][k1];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int v = 0; v < NK; ++v) {
+        const int k1 = j + T * v;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * kTK + t];
+      }
+      __syncthreads();  // exchange read: the next tile's rows may land
+      if (next < ntiles) prefetch(next);
+      cpa_commit();
+#pragma unroll
+      for (int v = 0; v < NK; ++v) {
+        const int k1 = j + T * v;
+        rdft<Q, -1, false>(X[v]);
+        if (valid) {
+#pragma unroll
+          for (int k2 = 0; k2 < Q; ++k2) d[(long long)(k1 + P * k2) * a.dst_elem] = X[v][k2];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NK; ++v) {
+        const int k1 = j + T * v;
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2)
+          X[v][k2] = valid ? sh[(k1 + P * k2) * kTK + t] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();  // inputs read: the tile becomes the exchange
+#pragma unroll
+      for (int v = 0; v < NK; ++v) {
+        const int k1 = j + T * v;
+        rdft<Q, 1, false>(X[v]);
+#pragma unroll
+        for (int b = 1; b < Q; ++b) X[v][b] = cmulcf(X[v][b], __ldg(&tw[b * k1]));
+#pragma unroll
+        for (int b = 0; b < Q; ++b) sh[(b * P + k1) * kTK + t] = X[v][b];
+      }
+      __syncthreads();
+      float2 y[NB][P];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int b = j + T * u;
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * P + k1) * kTK + t];
+      }
+      __syncthreads();  // exchange read: the next tile's rows may land
+      if (next < ntiles) prefetch(next);
+      cpa_commit();
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int b = j + T * u;
+        rdft<P, 1, false>(y[u]);
+        if (valid) {
+#pragma unroll
+          for (int aa = 0; aa < NA; ++aa) d[(long long)(b + Q * aa) * a.dst_elem] = y[u][aa];
+        }
+      }
+    }
+  }
+  cpa_wait_all();
+}
+
+template <int P, int Q>
+static const void* pick_ypipe(int kind, bool half) {
+  if (kind == 0) return half ? (const void*)k_ypipe<P, Q, 0, true> : (const void*)k_ypipe<P, Q, 0, false>;
+  return half ? (const void*)k_ypipe<P, Q, 1, true> : (const void*)k_ypipe<P, Q, 1, false>;
+}
+
+const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem) {
+  const void* fn = nullptr;
+  int T = 0;
+  switch (L) {
+    case 256: fn = pick_ypipe<16, 16>(kind, half); T = 16; break;
+    case 512: fn = pick_ypipe<16, 32>(kind, half); T = 16; break;
+    default: return nullptr;
+  }
+  *threads = kTK * T;
+  *smem = (size_t)L * kTK * sizeof(float2);
+  return fn;
+}
+
 }  // namespace ps

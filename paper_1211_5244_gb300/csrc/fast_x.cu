@@ -40,8 +40,10 @@ struct XShape {
 
 template <int P, int Q, int TR, bool HALF>
 __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
-    k_x_r2c(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a,
+    k_x_r2c(const void* src_v, void* dst_v, const float* twm_v, const float2* __restrict__ tw, FastArgs a,
             double*, unsigned*, double, double*) {
+  // twm: the matrix W_M^{r c} (r, c < P), laid out so lanes read consecutive entries
+  const float2* __restrict__ twm = reinterpret_cast<const float2*>(twm_v);
   using S = XShape<P, Q>;
   constexpr int M = S::M, T = S::T, NB = Q / T, NK = P / T;
   constexpr int NA = HALF ? P / 2 : P;
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     }
     rdft<P, -1, HALF>(y);
 #pragma unroll
-    for (int k1 = 1; k1 < P; ++k1) y[k1] = xmul(y[k1], __ldg(&tw[2 * b * k1]));  // W_M^{b k1}
+    for (int k1 = 1; k1 < P; ++k1) y[k1] = xmul(y[k1], __ldg(&twm[k1 * P + b]));  // W_M^{b k1}
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) ex[k1 * (Q + 1) + b] = y[k1];
   }
@@ -101,8 +103,9 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
 
 template <int P, int Q, int TR, bool HALF>
 __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
-    k_x_c2r(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a,
+    k_x_c2r(const void* src_v, void* dst_v, const float* twm_v, const float2* __restrict__ tw, FastArgs a,
             double*, unsigned*, double, double*) {
+  const float2* __restrict__ twm = reinterpret_cast<const float2*>(twm_v);
   using S = XShape<P, Q>;
   constexpr int M = S::M, T = S::T, NB = Q / T, NK = P / T;
   constexpr int NA = HALF ? P / 2 : P;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     const int k1 = j + T * v;
     rdft<Q, 1, false>(x[v]);
 #pragma unroll
-    for (int b = 1; b < Q; ++b) x[v][b] = xmulc(x[v][b], __ldg(&tw[2 * b * k1]));
+    for (int b = 1; b < Q; ++b) x[v][b] = xmulc(x[v][b], __ldg(&twm[b * P + k1]));
 #pragma unroll
     for (int b = 0; b < Q; ++b) ex[k1 * (Q + 1) + b] = x[v][b];
   }
@@ -231,6 +234,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const void* f0 = xline_kernel(M, 0, half, &threads, &rows, &smem);
     const void* f1 = xline_kernel(M, 1, half, &threads, &rows, &smem);
     if (f0 && f1) {
+      p->xP = M == 32 ? 8 : (M == 64 ? 8 : (M == 128 ? 16 : (M == 256 ? 16 : 32)));
       dim3 grid((n2 * n3 + rows - 1) / rows);
       if ((e = set(P1, f0, grid, threads, smem, base)) != cudaSuccess) return e;
       if ((e = set(P5, f1, grid, threads, smem, base)) != cudaSuccess) return e;
@@ -241,8 +245,17 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const bool half = n2 == L2 / 2;
     int threads;
     size_t smem;
-    const void* f0 = strided_kernel(L2, 0, half, &threads, &smem);
-    const void* f1 = strided_kernel(L2, 1, half, &threads, &smem);
+    // the persistent prefetching kernels where they exist (PS_YPASS=plain keeps
+    // the non-persistent ones)
+    const char* yp = getenv("PS_YPASS");
+    const bool ypipe = !(yp && strcmp(yp, "plain") == 0);
+    const void* f0 = ypipe ? ypipe_kernel(L2, 0, half, &threads, &smem) : nullptr;
+    const void* f1 = ypipe ? ypipe_kernel(L2, 1, half, &threads, &smem) : nullptr;
+    const bool ypersist = f0 && f1;
+    if (!ypersist) {
+      f0 = strided_kernel(L2, 0, half, &threads, &smem);
+      f1 = strided_kernel(L2, 1, half, &threads, &smem);
+    }
     if (f0 && f1) {
       FastArgs fwd = base, inv = base;
       fwd.src_plane = (long long)n2 * ldc; fwd.src_elem = ldc;   // A[z][y][kx]
@@ -250,6 +263,20 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       inv.src_plane = (long long)L2 * ldc; inv.src_elem = ldc;
       inv.dst_plane = (long long)n2 * ldc; inv.dst_elem = ldc;
       dim3 grid(ntk, n3);
+      if (ypersist) {
+        fwd.nrows = inv.nrows = n3;  // z planes walked by the persistent CTAs
+        if (smem > 48 * 1024 &&
+            ((e = cudaFuncSetAttribute(f0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+             (e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess))
+          return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f0, threads, smem)) != cudaSuccess) return e;
+        const long long tiles = (long long)ntk * n3;
+        const long long g = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+        grid = dim3((unsigned)(g < tiles ? g : tiles), 1);
+      }
       if ((e = set(P2, f0, grid, threads, smem, fwd)) != cudaSuccess) return e;
       if ((e = set(P4, f1, grid, threads, smem, inv)) != cudaSuccess) return e;
     }
@@ -301,7 +328,8 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
                         cudaStream_t s) {
   PassCfg& cf = p->cfg[pass];
   const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
-  const float* K = static_cast<const float*>(p->K);
+  // x passes get the twiddle matrix in the K slot
+  const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
   const void* tw = (pass == P3 && p->zsoa_T) ? p->tw4z : p->tw[axis];
   double* partials = p->partials;
   unsigned* counter = p->counter;

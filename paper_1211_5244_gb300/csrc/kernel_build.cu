@@ -219,6 +219,16 @@ __global__ void twiddle_kernel(cpx<T>* tw, int L) {
   }
 }
 
+// twiddle matrix of the x passes: twx[r P + c] = W_M^{r c} = W_L1^{2 r c}, r, c < P
+__global__ void twiddle_matrix_kernel(float2* twx, int L1, int P) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < P * P; idx += gridDim.x * blockDim.x) {
+    const int r = idx / P, c = idx % P;
+    double s, co;
+    sincospi(2.0 * ((2 * r * c) % L1) / L1, &s, &co);
+    twx[idx] = make_float2((float)co, (float)(-s));
+  }
+}
+
 // paired twiddles of the packed z kernel: tw4[r T + c] = (Re W^{rc}, Re W^{(r+T)c},
 // Im W^{rc}, Im W^{(r+T)c}), W = exp(-2 pi i / L), r, c < T
 __global__ void twiddle_pairs_kernel(float4* tw4, int L, int T) {
@@ -247,6 +257,8 @@ cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s) {
     else
       twiddle_kernel<double><<<grid_for(L), 256, 0, s>>>(static_cast<double2*>(p->tw[j]), L);
   }
+  if (p->xP)
+    twiddle_matrix_kernel<<<grid_for(p->xP * p->xP), 256, 0, s>>>(static_cast<float2*>(p->twx), p->L[0], p->xP);
   if (p->zsoa_T)
     twiddle_pairs_kernel<<<grid_for(p->zsoa_T * p->zsoa_T), 256, 0, s>>>(static_cast<float4*>(p->tw4z), p->L[2],
                                                                        p->zsoa_T);

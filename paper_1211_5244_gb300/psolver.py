@@ -69,6 +69,7 @@ def load_library():
         "ps_solve_vjp": [vp, vp, vp, vp, vp, vp],
         "ps_solve_batched": [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp],
         "ps_solve_host": [vp, vp, vp, vp, vp],
+        "ps_solve_host_stream": [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp],
         "ps_plan_set_profiling": [vp, i],
         "ps_plan_pass_times": [vp, ctypes.POINTER(d), ctypes.POINTER(i)],
         "ps_plan_destroy": [vp],
@@ -241,6 +242,23 @@ class Plan:
                                   ctypes.c_void_p(V_host.data_ptr()), ctypes.byref(E),
                                   _stream_handle(stream)))
         return V_host, E.value
+
+    def solve_host_stream(self, rho_hosts, V_hosts=None, energy=True, stream=None):
+        """ps_solve_host_stream: many host densities with overlapped transfers.
+        Returns (V_hosts, energies) with energies a list of floats (or None)."""
+        import torch
+        count = len(rho_hosts)
+        for r in rho_hosts:
+            if tuple(r.shape) != self.shape or r.dtype != self.torch_dtype or r.is_cuda or not r.is_contiguous():
+                raise ValueError("rho_hosts must be contiguous CPU tensors of the plan's shape and dtype")
+        if V_hosts is None:
+            V_hosts = [torch.empty_like(r) for r in rho_hosts]
+        arr = ctypes.c_void_p * max(count, 1)
+        rp = arr(*[r.data_ptr() for r in rho_hosts])
+        vp = arr(*[v.data_ptr() for v in V_hosts])
+        E = (ctypes.c_double * max(count, 1))() if energy else None
+        _check(_lib.ps_solve_host_stream(self._h, count, rp, vp, E, _stream_handle(stream)))
+        return V_hosts, (list(E)[:count] if energy else None)
 
     def kernel_octant(self, stream=None):
         """ps_kernel_get: the stored K^F / (L1 L2 L3) octant, shape (L3/2+1, L2/2+1, c)."""

@@ -135,3 +135,20 @@ def test_algorithmic_bytes_256_free_fp32():
 
 def test_autotune_rejects_null_plan(lib):
     assert lib.ps_plan_autotune(None, 5, None) == 1
+
+
+def test_host_stream_and_vjp_argument_checks(lib):
+    rc, p = _create(lib)
+    arr = ctypes.c_void_p * 1
+    buf = ctypes.create_string_buffer(8 * 8 * 8 * 4)
+    assert lib.ps_solve_host_stream(None, 1, arr(ctypes.addressof(buf)), arr(ctypes.addressof(buf)), None, None) == 1
+    assert lib.ps_solve_host_stream(p, -1, None, None, None, None) == 1
+    assert lib.ps_solve_host_stream(p, 0, None, None, None, None) == 0
+    assert lib.ps_solve_host_stream(p, 1, None, None, None, None) == 1
+    assert lib.ps_solve_host_stream(p, 1, arr(ctypes.addressof(buf)), arr(None), None, None) == 1
+    assert lib.ps_solve_host_stream(p, 1, arr(ctypes.addressof(buf)), arr(ctypes.addressof(buf)), None, None) == 3
+    fake = ctypes.c_void_p(0x10000)
+    assert lib.ps_solve_vjp(p, None, None, None, fake, None) == 1          # every term omitted
+    assert lib.ps_solve_vjp(p, fake, ctypes.c_void_p(0x20000), None, ctypes.c_void_p(0x30000), None) == 1
+    assert lib.ps_solve_vjp(p, fake, None, None, ctypes.c_void_p(0x30000), None) == 3  # not built
+    lib.ps_plan_destroy(p)

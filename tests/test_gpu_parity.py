@@ -213,6 +213,7 @@ FAST_CASES = [
     ((16, 24, 64), "fff"),     # z L=128 half
     ((12, 10, 128), "ffp"),    # z L=128 full
     ((20, 12, 256), "pff"),    # z L=512 half
+    ((10, 256, 6), "ppf"),     # y L=256 full
 ]
 
 
@@ -239,3 +240,17 @@ def test_autotuned_plan_matches_oracle(torch_cuda, n, bc, dtype):
     r = torch.from_numpy(rho.astype(_np_dtype(dtype))).cuda()
     V, E = plan.solve(r)
     _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, dtype)
+
+
+def test_host_stream_matches_device_solves(torch_cuda):
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    n = (48, 40, 36)
+    plan = psolver.Plan(n, "pff", 0.3, "f32")
+    rhos = [torch.from_numpy(synth.gaussian_mixture(n, 0.3, 3, 20 + i, subtract_mean=True).astype(np.float32))
+            .pin_memory() for i in range(5)]
+    Vh, Eh = plan.solve_host_stream(rhos)
+    for r, v, e in zip(rhos, Vh, Eh):
+        Vd, Ed = plan.solve(r.cuda())
+        assert torch.equal(v, Vd.cpu()) and e == float(Ed.item())
+    assert plan.solve_host_stream([]) == ([], [])
