@@ -59,9 +59,10 @@ struct DeviceGuard {
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 void free_device(ps_plan_s* p) {
-  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2], &p->tw4z, &p->twx,
+  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2], &p->tw4z, &p->tw4y, &p->twx,
                    reinterpret_cast<void**>(&p->partials), reinterpret_cast<void**>(&p->counter),
-                   &p->d_rho, &p->d_V, reinterpret_cast<void**>(&p->d_E), &p->d_rho2, &p->d_V2};
+                   &p->d_rho, &p->d_V, reinterpret_cast<void**>(&p->d_E), &p->d_rho2, &p->d_V2,
+                   reinterpret_cast<void**>(&p->d_Eb)};
   for (void** b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -240,6 +241,7 @@ int ps_kernel_build(ps_plan p, void* stream) {
       {reinterpret_cast<void**>(&p->counter), sizeof(unsigned), "energy counter"},
       {&p->tw4z, p->zsoa_T ? (size_t)p->zsoa_T * p->zsoa_T * 16 : 0, "paired z twiddles"},
       {&p->twx, p->xP ? (size_t)p->xP * p->xP * 8 : 0, "x twiddle matrix"},
+      {&p->tw4y, p->ysoa ? (size_t)16 * 16 * 16 : 0, "paired y twiddles"},
   };
   size_t total = 0;
   for (auto& a : allocs) {
@@ -425,6 +427,15 @@ int ps_solve_host_stream(ps_plan p, int count, const void* const* rho_host, void
     if ((e = cudaMalloc(&p->d_rho2, bytes)) != cudaSuccess) return cuda_fail(e, "staging rho");
     if ((e = cudaMalloc(&p->d_V2, bytes)) != cudaSuccess) return cuda_fail(e, "staging V");
   }
+  if (ehartree_host && p->d_Eb_cap < count) {
+    // the energies stay on the device until the batch ends: a copy of 8 bytes
+    // to pageable host memory would block the host and serialise the pipeline
+    if (p->d_Eb) cudaFree(p->d_Eb);
+    p->d_Eb = nullptr;
+    p->d_Eb_cap = 0;
+    if ((e = cudaMalloc(&p->d_Eb, (size_t)count * sizeof(double))) != cudaSuccess) return cuda_fail(e, "energies");
+    p->d_Eb_cap = count;
+  }
   if (!p->hs[0]) {
     for (int k = 0; k < 3; ++k)
       if ((e = cudaStreamCreateWithFlags(&p->hs[k], cudaStreamNonBlocking)) != cudaSuccess)
@@ -454,15 +465,17 @@ int ps_solve_host_stream(ps_plan p, int count, const void* const* rho_host, void
     PS_TRY(cudaEventRecord(ev_in[b], up), "ordering");
     PS_TRY(cudaStreamWaitEvent(comp, ev_in[b], 0), "ordering");
     if (i >= 2) PS_TRY(cudaStreamWaitEvent(comp, ev_out[b], 0), "ordering");
-    int rc = run_solve(p, drho[b], dV[b], ehartree_host ? p->d_E + b : nullptr, comp);
+    int rc = run_solve(p, drho[b], dV[b], ehartree_host ? p->d_Eb + i : nullptr, comp);
     if (rc != PS_OK) return fail(rc, "item %d: %s", i, ps_last_error());
     PS_TRY(cudaEventRecord(ev_comp[b], comp), "ordering");
     PS_TRY(cudaStreamWaitEvent(down, ev_comp[b], 0), "ordering");
     PS_TRY(cudaMemcpyAsync(V_host[i], dV[b], bytes, cudaMemcpyDeviceToHost, down), "copy V to host");
-    if (ehartree_host)
-      PS_TRY(cudaMemcpyAsync(ehartree_host + i, p->d_E + b, sizeof(double), cudaMemcpyDeviceToHost, down),
-             "copy E to host");
     PS_TRY(cudaEventRecord(ev_out[b], down), "ordering");
+  }
+  if (ehartree_host) {
+    PS_TRY(cudaStreamWaitEvent(down, ev_comp[(count - 1) & 1], 0), "ordering");
+    PS_TRY(cudaMemcpyAsync(ehartree_host, p->d_Eb, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, down),
+           "copy energies to host");
   }
   PS_TRY(cudaStreamSynchronize(down), "transfer pipeline");
   PS_TRY(cudaStreamSynchronize(comp), "transfer pipeline");

@@ -99,8 +99,10 @@ struct ps_plan_s {
   void* K;       // [H3+1][H2+1][ldk] real: K^F / (L1 L2 L3), even octant (kx < c used)
   void* tw[3];   // W_{L_j}^k, k < L_j, complex, per axis
   void* tw4z;    // paired z twiddles of the packed z kernel (T*T float4), or NULL
+  void* tw4y;    // paired y twiddles of the packed y kernels (16*16 float4), or NULL
   void* twx;     // x passes: W_M^{r c}, r, c < xP (float2, M = L1/2), or NULL
   int xP;        // size of twx (the larger step of the x-pass factorisation)
+  int ysoa;      // 1 if the packed y kernels run (L2 = 512)
   int zsoa_T;    // T of the packed z kernel (L3 = 2 T^2), 0 if not used
   double* partials;     // per-CTA energy partials of the z pass
   unsigned* counter;    // arrival counter for the last-CTA energy reduction
@@ -110,6 +112,8 @@ struct ps_plan_s {
   double* d_E;   // two doubles: one per ps_solve_host_stream slot
   void* d_rho2;  // slot 1 of ps_solve_host_stream
   void* d_V2;
+  double* d_Eb;           // energies of a ps_solve_host_stream batch (grown as needed)
+  int d_Eb_cap;
   cudaStream_t hs[3];     // upload, compute, download streams of ps_solve_host_stream
   cudaEvent_t hev[7];     // per-slot upload / compute / download events, and a start event
   size_t ws_bytes;

@@ -249,8 +249,14 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     // the non-persistent ones)
     const char* yp = getenv("PS_YPASS");
     const bool ypipe = !(yp && strcmp(yp, "plain") == 0);
-    const void* f0 = ypipe ? ypipe_kernel(L2, 0, half, &threads, &smem) : nullptr;
-    const void* f1 = ypipe ? ypipe_kernel(L2, 1, half, &threads, &smem) : nullptr;
+    const bool ysoa = yp && strcmp(yp, "soa") == 0;
+    const void* f0 = ysoa ? ysoa_kernel(L2, 0, half, &threads, &smem) : nullptr;
+    const void* f1 = ysoa ? ysoa_kernel(L2, 1, half, &threads, &smem) : nullptr;
+    p->ysoa = (f0 && f1) ? 1 : 0;
+    if (!p->ysoa) {
+      f0 = ypipe ? ypipe_kernel(L2, 0, half, &threads, &smem) : nullptr;
+      f1 = ypipe ? ypipe_kernel(L2, 1, half, &threads, &smem) : nullptr;
+    }
     const bool ypersist = f0 && f1;
     if (!ypersist) {
       f0 = strided_kernel(L2, 0, half, &threads, &smem);
@@ -330,7 +336,8 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
   const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
   // x passes get the twiddle matrix in the K slot
   const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
-  const void* tw = (pass == P3 && p->zsoa_T) ? p->tw4z : p->tw[axis];
+  const void* tw = (pass == P3 && p->zsoa_T) ? p->tw4z
+                   : ((pass == P2 || pass == P4) && p->ysoa) ? p->tw4y : p->tw[axis];
   double* partials = p->partials;
   unsigned* counter = p->counter;
   void* args[] = {(void*)&src, (void*)&dst, (void*)&K, (void*)&tw, (void*)&cf.fa,

@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(16 * T, 2)
     float2 e2 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 0; m < T; ++m) {
+      // kz0 = j + 2 T m and kz1 = kz0 + T (j < T) are both below L/2 exactly
+      // when m < T/2; above, the even octant is read at L - kz
       const int kz0 = j + P * 2 * m, kz1 = kz0 + P;
-      const int o0 = kz0 <= L / 2 ? kz0 : L - kz0, o1 = kz1 <= L / 2 ? kz1 : L - kz1;
+      const int o0 = m < T / 2 ? kz0 : L - kz0, o1 = m < T / 2 ? kz1 : L - kz1;
       const float2 kk = valid ? make_float2(kstage[o0 * TK + t], kstage[o1 * TK + t]) : make_float2(0.f, 0.f);
       const float2 p2 = soa::fma2(z[m].re, z[m].re, soa::mul2(z[m].im, z[m].im));
       e2 = soa::fma2(kk, p2, e2);
@@ -294,10 +296,15 @@ __global__ void __launch_bounds__(16 * T, 2)
     for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * TK + t]);
     soa::dft2<P, 1, false>(y);
     if (valid) {
+      float2* p0 = line + (long long)j * es;
+      float2* p1 = p0 + (long long)T * es;
+      const long long step = (long long)Q * es;
 #pragma unroll
       for (int aa = 0; aa < NA; ++aa) {
-        line[(long long)(j + Q * aa) * es] = make_float2(y[aa].re.x, y[aa].im.x);
-        line[(long long)(j + T + Q * aa) * es] = make_float2(y[aa].re.y, y[aa].im.y);
+        *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+        *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+        p0 += step;
+        p1 += step;
       }
     }
   }
@@ -316,6 +323,137 @@ const void* zpipe_kernel(int L, bool half, int* threads, size_t* smem) {
   *threads = 16 * T;
   *smem = (size_t)T * T * 16 * sizeof(float4) + (size_t)NA * 2 * T * 16 * sizeof(float2) +
           (size_t)(T * T + 1) * 16 * sizeof(float);
+  return fn;
+}
+
+// ---------------------------------------------------------------- packed y passes
+
+// Persistent packed y pass for L2 = 512 (T = 16): KIND 0 forward (n2 inputs,
+// L2 outputs), KIND 1 inverse (L2 inputs, n2 outputs). Same pairs as the z
+// kernel; the next tile's rows land (cp.async) in the exchange buffer once
+// the current tile's exchange has been read.
+template <int KIND, bool HALF>
+__global__ void __launch_bounds__(256, 2)
+    k_ysoa_pipe(const void* src_v, void* dst_v, const float*, const float4* __restrict__ tw4, FastArgs a,
+                double*, unsigned*, double, double*) {
+  constexpr int T = 16, TK = 16, P = T, Q = 2 * T, L = P * Q;
+  constexpr int NA = HALF ? P / 2 : P;
+  constexpr int ROWS = KIND == 0 ? NA * Q : L;
+  extern __shared__ float4 smem4[];
+  float4* sh4 = smem4;                                  // exchange [T * P][TK] float4
+  float2* stage = reinterpret_cast<float2*>(smem4);     // input rows [ROWS][TK] float2 (same space)
+  const float2* src = static_cast<const float2*>(src_v);
+  float2* dst = static_cast<float2*>(dst_v);
+  const int t = threadIdx.x % TK;
+  const int j = threadIdx.x / TK;
+  const int ntk = (a.c + TK - 1) / TK;
+  const int ntiles = ntk * a.nrows;  // nrows = z planes
+
+  auto prefetch = [&](int tile) {
+    const int kx0 = (tile % ntk) * TK;
+    const float2* sp = src + (long long)(tile / ntk) * a.src_plane + kx0;
+    for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
+      const int row = q / (TK / 2), part = q % (TK / 2);
+      cp_async16(stage + row * TK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
+    }
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    const int kx = (tile % ntk) * TK + t;
+    const bool valid = kx < a.c;
+    float2* d = dst + (long long)(tile / ntk) * a.dst_plane + kx;
+    const long long de = a.dst_elem;
+    cp_async_wait_all();
+    __syncthreads();
+    if constexpr (KIND == 0) {
+      c2 y[P];
+#pragma unroll
+      for (int aa = 0; aa < P; ++aa) {
+        y[aa] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (aa < NA && valid) {
+          const float2 u0 = stage[(j + Q * aa) * TK + t];
+          const float2 u1 = stage[(j + T + Q * aa) * TK + t];
+          y[aa] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+        }
+      }
+      __syncthreads();  // inputs read: the space becomes the exchange
+      soa::dft2<P, -1, HALF>(y);
+#pragma unroll
+      for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], __ldg(&tw4[j * P + k1]));
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) sh4[(j * P + k1) * TK + t] = pack(y[k1]);
+      __syncthreads();
+      c2 z[T];
+#pragma unroll
+      for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * TK + t]);
+      __syncthreads();  // exchange read: the next tile's rows may land
+      if (next < ntiles) prefetch(next);
+      cp_async_commit();
+      dif_all<T>(z, std::make_integer_sequence<int, T>{});
+      soa::dft2<T, -1, false>(z);
+      if (valid) {
+        // z[m] = (X[j + 2T m], X[j + T + 2T m])
+        float2* p0 = d + (long long)j * de;
+        float2* p1 = p0 + (long long)T * de;
+        const long long step = (long long)(2 * T) * de;
+#pragma unroll
+        for (int m = 0; m < T; ++m) {
+          *p0 = make_float2(z[m].re.x, z[m].im.x);
+          *p1 = make_float2(z[m].re.y, z[m].im.y);
+          p0 += step;
+          p1 += step;
+        }
+      }
+    } else {
+      c2 z[T];
+#pragma unroll
+      for (int m = 0; m < T; ++m) {
+        const float2 u0 = valid ? stage[(j + 2 * T * m) * TK + t] : make_float2(0.f, 0.f);
+        const float2 u1 = valid ? stage[(j + T + 2 * T * m) * TK + t] : make_float2(0.f, 0.f);
+        z[m] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+      }
+      __syncthreads();  // inputs read: the space becomes the exchange
+      soa::dft2<T, 1, false>(z);
+      dit_all<T>(z, std::make_integer_sequence<int, T>{});
+#pragma unroll
+      for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], __ldg(&tw4[b * P + j]));
+#pragma unroll
+      for (int b = 0; b < T; ++b) sh4[(b * P + j) * TK + t] = pack(z[b]);
+      __syncthreads();
+      c2 y[P];
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * TK + t]);
+      __syncthreads();  // exchange read: the next tile's rows may land
+      if (next < ntiles) prefetch(next);
+      cp_async_commit();
+      soa::dft2<P, 1, false>(y);
+      if (valid) {
+        float2* p0 = d + (long long)j * de;
+        float2* p1 = p0 + (long long)T * de;
+        const long long step = (long long)Q * de;
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+          *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+          *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+          p0 += step;
+          p1 += step;
+        }
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem) {
+  if (L != 512) return nullptr;
+  const void* fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, true> : (const void*)k_ysoa_pipe<0, false>)
+                             : (half ? (const void*)k_ysoa_pipe<1, true> : (const void*)k_ysoa_pipe<1, false>);
+  *threads = 256;
+  *smem = (size_t)16 * 16 * 16 * sizeof(float4);  // exchange; the input rows share it
   return fn;
 }
 

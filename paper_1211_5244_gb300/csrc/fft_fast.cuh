@@ -24,6 +24,9 @@ const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, si
 // per CTA (8 or 16), or nullptr.
 const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem);
 
+// The persistent packed y-pass kernels (L2 = 512), or nullptr.
+const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem);
+
 // The persistent, prefetching y-pass kernels (L2 = 256, 512), or nullptr.
 const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem);
 
