@@ -67,6 +67,12 @@ void free_device(ps_plan_s* p) {
     if (*b) cudaFree(*b);
     *b = nullptr;
   }
+  for (int j = 0; j < 3; ++j) {
+    for (const void** b : {&p->blue[j].twM, &p->blue[j].chirp, &p->blue[j].Bf}) {
+      if (*b) cudaFree(const_cast<void*>(*b));
+      *b = nullptr;
+    }
+  }
   p->built = false;
   p->ws_bytes = 0;
 }
@@ -170,6 +176,30 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
   p->st[0] = factorize(even1 ? p->L[0] / 2 : p->L[0]);
   p->st[1] = factorize(p->L[1]);
   p->st[2] = factorize(p->L[2]);
+  // Bluestein for transform lengths with a prime factor >= 11 (a direct sum
+  // over that factor would cost N * p per line), if M fits the tile
+  for (int j = 0; j < 3; ++j) {
+    const int N = (j == 0 && even1) ? p->L[0] / 2 : p->L[j];
+    int big = 1;
+    for (int r = 0; r < p->st[j].n; ++r) big = p->st[j].R[r] > big ? p->st[j].R[r] : big;
+    p->blue[j] = BlueArgs{};
+    if (big >= 11) {
+      int M = 2 * N - 1;
+      for (;; ++M) {
+        int m = M;
+        for (int q : {2, 3, 5})
+          while (m % q == 0) m /= q;
+        if (m == 1) break;
+      }
+      // two buffers of M rows for a one-line tile (ldt = 2) must fit the
+      // 200 KiB shared-memory budget of the generic kernels
+      const size_t csz = 2 * (p->dtype == PS_F32 ? 4 : 8);
+      if (M <= kMaxLen && (size_t)2 * M * 2 * csz <= 200 * 1024) {
+        p->blue[j].M = M;
+        p->blue[j].st = factorize(M);
+      }
+    }
+  }
   p->ldc = round_up((size_t)p->c, p->dtype == PS_F32 ? 16 : 8);
   p->ldk = round_up((size_t)p->c, 16);
   return PS_OK;
@@ -252,6 +282,22 @@ int ps_kernel_build(ps_plan p, void* stream) {
       return cuda_fail(e, a.what);
     }
     total += a.bytes;
+  }
+  for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+    if (!p->blue[j].M) continue;
+    const int N = (j == 0 && p->L[0] % 2 == 0) ? p->L[0] / 2 : p->L[j];
+    void *twM = nullptr, *ch = nullptr, *bf = nullptr;
+    e = cudaMalloc(&twM, (size_t)p->blue[j].M * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&ch, (size_t)N * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&bf, (size_t)p->blue[j].M * csz);
+    p->blue[j].twM = twM;
+    p->blue[j].chirp = ch;
+    p->blue[j].Bf = bf;
+    total += (size_t)(2 * p->blue[j].M + N) * csz;
+  }
+  if (e != cudaSuccess) {
+    free_device(p);
+    return cuda_fail(e, "Bluestein tables");
   }
   p->ws_bytes = total;
   e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), s);

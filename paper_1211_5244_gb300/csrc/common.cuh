@@ -54,6 +54,16 @@ struct Stages {
 
 enum Pass { P1 = 0, P2 = 1, P3 = 2, P4 = 3, P5 = 4 };
 
+// Bluestein (chirp-z) form of a transform of length N with a large prime
+// factor: a cyclic convolution of length M >= 2N - 1 (factors 2, 3, 5).
+struct BlueArgs {
+  int M;              // 0: the transform runs as plain Stockham stages
+  Stages st;          // stages of the length-M transforms
+  const void* twM;    // W_M^k, k < M
+  const void* chirp;  // c[m] = exp(-i pi m^2 / N), m < N
+  const void* Bf;     // DFT_M of the conjugate chirp, divided by M
+};
+
 // Arguments of the specialised FP32 pass kernels (strides in complex elements).
 struct FastArgs {
   int c;                  // valid kx columns (L1/2 + 1)
@@ -118,6 +128,7 @@ struct ps_plan_s {
   cudaEvent_t hev[7];     // per-slot upload / compute / download events, and a start event
   size_t ws_bytes;
   ps::Stages st[3];     // stages of the 1D transform per axis (x: length L1/2 if L1 even)
+  ps::BlueArgs blue[3]; // Bluestein descriptors per axis (M = 0: off); device pointers owned
   ps::PassCfg cfg[5];
   // per-pass timing (ps_plan_set_profiling): 6 events per recorded solve
   bool profiling;

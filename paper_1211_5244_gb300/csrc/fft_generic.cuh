@@ -190,4 +190,41 @@ __device__ cpx<T>* stockham(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const 
   return a;
 }
 
+// The transform of a tile (as stockham), in Bluestein form when bl.M > 0:
+// with the stored chirp c[m] = exp(-i pi m^2 / N) (its conjugate for the
+// inverse, DIR = +1), X[k] = c[k] sum_m (x[m] c[m]) conj(c[k - m]) since
+// m k = (m^2 + k^2 - (k - m)^2) / 2. The sum is a cyclic convolution of
+// length M >= 2N - 1, done with length-M Stockham transforms and bl.Bf, the
+// transform of the conjugate chirp divided by M. Both buffers hold M rows.
+template <int DIR, typename T>
+__device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const Stages& st,
+                                  const cpx<T>* __restrict__ tw, int tws, const BlueArgs& bl) {
+  using C = cpx<T>;
+  if (bl.M == 0) return stockham<DIR, T>(a, b, N, tk, ldt, st, tw, tws);
+  const int M = bl.M;
+  const C* __restrict__ ch = static_cast<const C*>(bl.chirp);
+  const C* __restrict__ Bf = static_cast<const C*>(bl.Bf);
+  for (int w = threadIdx.x; w < tk * M; w += blockDim.x) {
+    const int t = w % tk, m = w / tk;
+    C v = mk(T(0), T(0));
+    if (m < N) v = DIR < 0 ? cmul(a[m * ldt + t], ch[m]) : cmulc(a[m * ldt + t], ch[m]);
+    a[m * ldt + t] = v;
+  }
+  __syncthreads();
+  C* r = stockham<-1, T>(a, b, M, tk, ldt, bl.st, static_cast<const C*>(bl.twM), 1);
+  C* o = (r == a) ? b : a;
+  for (int w = threadIdx.x; w < tk * M; w += blockDim.x) {
+    const int t = w % tk, m = w / tk;
+    r[m * ldt + t] = DIR < 0 ? cmul(r[m * ldt + t], Bf[m]) : cmulc(r[m * ldt + t], Bf[m]);
+  }
+  __syncthreads();
+  r = stockham<1, T>(r, o, M, tk, ldt, bl.st, static_cast<const C*>(bl.twM), 1);
+  for (int w = threadIdx.x; w < tk * N; w += blockDim.x) {
+    const int t = w % tk, k = w / tk;
+    r[k * ldt + t] = DIR < 0 ? cmul(r[k * ldt + t], ch[k]) : cmulc(r[k * ldt + t], ch[k]);
+  }
+  __syncthreads();
+  return r;
+}
+
 }  // namespace ps

@@ -241,6 +241,41 @@ __global__ void twiddle_pairs_kernel(float4* tw4, int L, int T) {
   }
 }
 
+// Bluestein tables for a transform of length N, convolution length M:
+//   chirp[m] = exp(-i pi m^2 / N), m < N
+//   Bf[k] = (1/M) sum_j b[j] W_M^{jk}, b[j] = conj(chirp[|j|]) for |j| < N (j taken mod M)
+// Phases are reduced exactly in integers (m^2 mod 2N, j k mod M) before sincospi.
+template <typename T>
+__global__ void chirp_kernel(cpx<T>* ch, int N) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
+    const long long q = ((long long)m * m) % (2LL * N);
+    double s, c;
+    sincospi((double)q / N, &s, &c);
+    ch[m] = mk((T)c, (T)(-s));
+  }
+}
+
+template <typename T>
+__global__ void bluestein_bf_kernel(cpx<T>* Bf, int N, int M) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < N; ++j) {
+      const double a = (double)(((long long)j * j) % (2LL * N)) / N;  // exp(+i pi j^2 / N)
+      const double w = 2.0 * (double)(((long long)j * k) % M) / M;   // W_M^{jk}:  exp(-i pi w)
+      double s, c;
+      sincospi(a - w, &s, &c);
+      re += c;
+      im += s;
+      if (j > 0) {  // the mirrored sample at M - j: exp(+i pi j^2 / N) W_M^{(M - j) k}
+        sincospi(a + w, &s, &c);
+        re += c;
+        im += s;
+      }
+    }
+    Bf[k] = mk((T)(re / M), (T)(im / M));
+  }
+}
+
 // ---------------------------------------------------------------- host
 
 static int grid_for(size_t n) {
@@ -256,6 +291,20 @@ cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s) {
       twiddle_kernel<float><<<grid_for(L), 256, 0, s>>>(static_cast<float2*>(p->tw[j]), L);
     else
       twiddle_kernel<double><<<grid_for(L), 256, 0, s>>>(static_cast<double2*>(p->tw[j]), L);
+  }
+  for (int j = 0; j < 3; ++j) {
+    const BlueArgs& b = p->blue[j];
+    if (!b.M) continue;
+    const int N = (j == 0 && p->L[0] % 2 == 0) ? p->L[0] / 2 : p->L[j];
+    if (p->dtype == PS_F32) {
+      twiddle_kernel<float><<<grid_for(b.M), 256, 0, s>>>((float2*)b.twM, b.M);
+      chirp_kernel<float><<<grid_for(N), 256, 0, s>>>((float2*)b.chirp, N);
+      bluestein_bf_kernel<float><<<grid_for(b.M), 256, 0, s>>>((float2*)b.Bf, N, b.M);
+    } else {
+      twiddle_kernel<double><<<grid_for(b.M), 256, 0, s>>>((double2*)b.twM, b.M);
+      chirp_kernel<double><<<grid_for(N), 256, 0, s>>>((double2*)b.chirp, N);
+      bluestein_bf_kernel<double><<<grid_for(b.M), 256, 0, s>>>((double2*)b.Bf, N, b.M);
+    }
   }
   if (p->xP)
     twiddle_matrix_kernel<<<grid_for(p->xP * p->xP), 256, 0, s>>>(static_cast<float2*>(p->twx), p->L[0], p->xP);

@@ -39,7 +39,9 @@ struct GenArgs {
   int tk, ldt;
   int N;    // transform length of this pass
   int tws;  // twiddle-table stride (table length / N)
+  int rows; // rows of each shared-memory buffer (>= N, and >= M in Bluestein form)
   Stages st;
+  BlueArgs bl;
 };
 
 // ---------------------------------------------------------------- P1
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
   using C = cpx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + (a.N + 1) * a.ldt;
+  C* buf1 = buf0 + a.rows * a.ldt;
   const int nrows = a.n2 * a.n3;
   const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
     }
   }
   __syncthreads();
-  C* out = stockham<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  C* out = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   if (even) {
     // X[k] = E[k] + W_L^k O[k],  E = (Z[k] + conj Z[N-k]) / 2,  O = -i (Z[k] - conj Z[N-k]) / 2
     const int N = a.N;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
   using C = cpx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + a.N * a.ldt;
+  C* buf1 = buf0 + a.rows * a.ldt;
   const int kx0 = blockIdx.x * a.tk;
   const int z = blockIdx.y;
   const int nin = DIR < 0 ? a.n2 : a.L2;
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
     buf0[y * a.ldt + t] = v;
   }
   __syncthreads();
-  C* out = stockham<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  C* out = line_transform<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   for (int w = threadIdx.x; w < a.tk * nout; w += blockDim.x) {
     const int t = w % a.tk, y = w / a.tk;
     if (kx0 + t < a.c) d[(size_t)y * a.ldc + t] = out[y * a.ldt + t];
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   using C = cpx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + a.N * a.ldt;
+  C* buf1 = buf0 + a.rows * a.ldt;
   const int kx0 = blockIdx.x * a.tk;
   const int ky = blockIdx.y;
   const size_t zstride = (size_t)a.L2 * a.ldc;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     buf0[z * a.ldt + t] = v;
   }
   __syncthreads();
-  C* spec = stockham<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  C* spec = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   C* other = (spec == buf0) ? buf1 : buf0;
   // multiply by the octant of K^F; accumulate w(kx) K |rho^F|^2 for the energy
   const int kyo = min(ky, a.L2 - ky);
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     spec[kz * a.ldt + t] = v;
   }
   __syncthreads();
-  C* res = stockham<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, tw, a.tws);
+  C* res = line_transform<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   for (int w = threadIdx.x; w < a.tk * a.n3; w += blockDim.x) {
     const int t = w % a.tk, z = w / a.tk;
     if (kx0 + t < a.c) line[z * zstride + t] = res[z * a.ldt + t];
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   using C = cpx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + (a.N + 1) * a.ldt;
+  C* buf1 = buf0 + a.rows * a.ldt;
   const int nrows = a.n2 * a.n3;
   const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
     }
   }
   __syncthreads();
-  C* out = stockham<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, tw, a.tws);
+  C* out = line_transform<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
     const int t = w / a.n1, i = w - t * a.n1;
     const int row = row0 + t;
@@ -292,6 +294,16 @@ static int pick_tk(int rows, int nbuf, size_t csz, int tk0, size_t budget, int* 
   return 0;
 }
 
+// rows of each shared-memory buffer of a generic pass
+static int gen_rows(const ps_plan_s* p, int pass) {
+  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
+  const bool even1 = (p->L[0] % 2) == 0;
+  const int N = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
+  int r = axis == 0 ? N + 1 : N;
+  if (p->blue[axis].M > r) r = p->blue[axis].M;
+  return r;
+}
+
 template <typename T>
 static GenArgs gen_args(const ps_plan_s* p, int pass) {
   GenArgs a;
@@ -306,6 +318,8 @@ static GenArgs gen_args(const ps_plan_s* p, int pass) {
   a.N = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
   a.tws = p->L[axis] / a.N;
   a.st = p->st[axis];
+  a.bl = p->blue[axis];
+  a.rows = gen_rows(p, pass);
   return a;
 }
 
@@ -316,7 +330,8 @@ cudaError_t configure_passes(ps_plan_s* p) {
   const int tk0 = sizeof(T) == 4 ? 16 : 8;
   const bool even1 = (p->L[0] % 2) == 0;
   const int N0 = even1 ? p->L[0] / 2 : p->L[0];
-  const int rows[5] = {N0 + 1, p->L[1], p->L[2], p->L[1], N0 + 1};
+  (void)N0;
+  const int rows[5] = {gen_rows(p, P1), gen_rows(p, P2), gen_rows(p, P3), gen_rows(p, P4), gen_rows(p, P5)};
   for (int k = 0; k < 5; ++k) {
     PassCfg& cf = p->cfg[k];
     cf.threads = 256;

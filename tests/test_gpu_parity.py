@@ -254,3 +254,12 @@ def test_host_stream_matches_device_solves(torch_cuda):
         Vd, Ed = plan.solve(r.cuda())
         assert torch.equal(v, Vd.cpu()) and e == float(Ed.item())
     assert plan.solve_host_stream([]) == ([], [])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,bc", [((1031, 2, 3), "ppp"), ((3, 509, 2), "fpf"), ((2, 3, 257), "ffp")])
+def test_parity_long_prime_axes(torch_cuda, n, bc, dtype):
+    # long prime periodic axes: chirp-z (Bluestein) transforms of length up to 2048
+    rho = synth.random_density(n, seed=sum(n), subtract_mean=True)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.2, dtype)
+    _check(V, E, rho, bc, 0.2, dtype)
