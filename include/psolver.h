@@ -87,6 +87,7 @@ typedef struct {
                                rho in, V out, four intermediate write+read pairs,
                                and one read of the stored K^F octant            */
   size_t workspace_bytes;   /* device bytes the plan allocates at build          */
+  int launches;             /* kernels one ps_solve launches (0 before build)    */
 } ps_plan_info;
 
 /*

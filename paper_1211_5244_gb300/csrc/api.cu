@@ -242,6 +242,7 @@ int ps_plan_query(ps_plan p, ps_plan_info* info) {
   info->alg_bytes = 2.0 * (double)(n1 * n2 * n3) * b + 8.0 * b * (double)(c * n3 * (n2 + L2)) +
                     b * (double)c * (double)(p->H[1] + 1) * (double)(p->H[2] + 1);
   info->workspace_bytes = p->ws_bytes;
+  info->launches = p->built ? 5 : 0;
   return PS_OK;
 }
 

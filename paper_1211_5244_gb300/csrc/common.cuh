@@ -73,7 +73,8 @@ struct FastArgs {
   int ldk;                // kx pitch of the K^F octant
   long long src_plane, src_elem;
   long long dst_plane, dst_elem;
-  long long kz_stride;    // z pass: (L2/2 + 1) * c, the kz stride of the K^F octant
+  long long kz_stride;    // z pass: (L2/2 + 1) * ldk, the kz stride of the K^F octant
+  int kt0, ntk_loc;       // persistent y/z kernels: first kx tile and number of kx tiles walked
 };
 
 struct PassCfg {

@@ -219,11 +219,11 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
   float2* dst = static_cast<float2*>(dst_v);
   const int t = threadIdx.x % kTK;
   const int j = threadIdx.x / kTK;
-  const int ntk = (a.c + kTK - 1) / kTK;
+  const int ntk = a.ntk_loc;  // kx tiles a.kt0 .. a.kt0 + ntk - 1
   const int ntiles = ntk * (int)a.nrows;  // nrows = number of z planes here
 
   auto prefetch = [&](int tile) {
-    const int kx0 = (tile % ntk) * kTK;
+    const int kx0 = (a.kt0 + tile % ntk) * kTK;
     const float2* sp = src + (long long)(tile / ntk) * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (kTK / 2); q += blockDim.x) {
       const int row = q / (kTK / 2), part = q % (kTK / 2);
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
   cpa_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
-    const int kx = (tile % ntk) * kTK + t;
+    const int kx = (a.kt0 + tile % ntk) * kTK + t;
     const bool valid = kx < a.c;
     float2* d = dst + (long long)(tile / ntk) * a.dst_plane + kx;
     cpa_wait_all();

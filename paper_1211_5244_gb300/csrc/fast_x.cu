@@ -222,6 +222,8 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   base.nrows = n2 * n3;
   base.ldc = ldc;
   base.kz_stride = (long long)(p->H[1] + 1) * p->ldk;
+  base.kt0 = 0;
+  base.ntk_loc = (p->c + 15) / 16;
   base.ldk = (int)p->ldk;
   const int ntk = (p->c + 15) / 16;
 

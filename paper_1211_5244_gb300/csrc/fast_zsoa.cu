@@ -199,13 +199,13 @@ __global__ void __launch_bounds__(16 * T, 2)
   float* kstage = reinterpret_cast<float*>(stage + ROWS * TK);      // K^F [KROWS][TK]
   const int t = threadIdx.x % TK;
   const int j = threadIdx.x / TK;
-  const int ntk = (a.c + TK - 1) / TK;
+  const int ntk = a.ntk_loc;  // kx tiles a.kt0 .. a.kt0 + ntk - 1
   const int ntiles = ntk * a.L2;
   float2* const base = static_cast<float2*>(line_v);
   const long long es = a.src_elem;
 
   auto issue_input = [&](int tile) {
-    const int kx0 = (tile % ntk) * TK;
+    const int kx0 = (a.kt0 + tile % ntk) * TK;
     const int ky = paired_ky_soa(tile / ntk, a.L2);
     const float2* src = base + ky * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(16 * T, 2)
     }
   };
   auto issue_k = [&](int tile) {
-    const int kx0 = (tile % ntk) * TK;
+    const int kx0 = (a.kt0 + tile % ntk) * TK;
     const int ky = paired_ky_soa(tile / ntk, a.L2);
     const int kyo = min(ky, a.L2 - ky);
     const float* src = K + (long long)kyo * a.ldk + kx0;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(16 * T, 2)
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
-    const int kx = (tile % ntk) * TK + t;
+    const int kx = (a.kt0 + tile % ntk) * TK + t;
     const bool valid = kx < a.c;
     const int ky = paired_ky_soa(tile / ntk, a.L2);
     float2* line = base + ky * a.src_plane + kx;
@@ -346,11 +346,11 @@ __global__ void __launch_bounds__(256, 2)
   float2* dst = static_cast<float2*>(dst_v);
   const int t = threadIdx.x % TK;
   const int j = threadIdx.x / TK;
-  const int ntk = (a.c + TK - 1) / TK;
+  const int ntk = a.ntk_loc;  // kx tiles a.kt0 .. a.kt0 + ntk - 1
   const int ntiles = ntk * a.nrows;  // nrows = z planes
 
   auto prefetch = [&](int tile) {
-    const int kx0 = (tile % ntk) * TK;
+    const int kx0 = (a.kt0 + tile % ntk) * TK;
     const float2* sp = src + (long long)(tile / ntk) * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
       const int row = q / (TK / 2), part = q % (TK / 2);
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256, 2)
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
-    const int kx = (tile % ntk) * TK + t;
+    const int kx = (a.kt0 + tile % ntk) * TK + t;
     const bool valid = kx < a.c;
     float2* d = dst + (long long)(tile / ntk) * a.dst_plane + kx;
     const long long de = a.dst_elem;

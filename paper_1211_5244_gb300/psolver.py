@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
         ("lines", ctypes.c_longlong * 5), ("line_len", ctypes.c_longlong * 5),
         ("fft_points", ctypes.c_double), ("paper_points", ctypes.c_double),
         ("paper_full_points", ctypes.c_double), ("alg_bytes", ctypes.c_double),
-        ("workspace_bytes", ctypes.c_size_t),
+        ("workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_int),
     ]
 
 
