@@ -127,17 +127,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
 def _density(w, rank=0):
     import numpy as np
-    from paper_1211_5244_gb300 import synth
-    rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"] + rank, noise=w["noise"])
+    from paper_1211_5244_gb300 import replicas, synth
+    rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], replicas.replica_seed(w["seed"], rank),
+                                 noise=w["noise"])
     return rho.astype(np.float32)
 
 
@@ -172,7 +166,8 @@ def run_reference(args):
     import numpy as np
     from oracle import poisson as op
     from paper_1211_5244_gb300 import synth
-    rank, world, _ = _dist_env()
+    from paper_1211_5244_gb300 import replicas
+    rank, world, _ = replicas.dist_env()
     if rank != 0:
         return
     w = dict(synth.WORKLOADS[WORKLOAD])
@@ -206,7 +201,13 @@ def run_batched(args):
     import numpy as np
     import torch
     from paper_1211_5244_gb300 import build as _build
-    from paper_1211_5244_gb300 import psolver, synth
+    from paper_1211_5244_gb300 import psolver, replicas, synth
+    rank, world, local = replicas.dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
     w = synth.WORKLOADS["batched64"]
     shapes = synth.batched_shapes(w["count"], w["nmin"], w["nmax"], w["seed"])
@@ -214,8 +215,8 @@ def run_batched(args):
     plans, rhos = [], []
     for i, (n, bc) in enumerate(shapes):
         plans.append(psolver.Plan(n, bc, w["h"], "f32", autotune=tune))
-        r = synth.gaussian_mixture(n, w["h"], w["n_gauss"], w["seed"] + 1000 + i, noise=w["noise"],
-                                   subtract_mean="p" in bc)
+        r = synth.gaussian_mixture(n, w["h"], w["n_gauss"], replicas.replica_seed(w["seed"] + 1000 * (rank + 1), i),
+                                   noise=w["noise"], subtract_mean="p" in bc)
         rhos.append(torch.from_numpy(r.astype(np.float32)).cuda())
     Vs = [torch.empty_like(r) for r in rhos]
     E = torch.empty(len(plans), dtype=torch.float64, device="cuda")
@@ -227,7 +228,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(local)
+    replicas.barrier(dist)
+    torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.2)
     for i in range(args.steps):
@@ -236,14 +239,17 @@ def run_batched(args):
         psolver.solve_batched(plans, rhos, Vs, stream=stream)
         ends[i].record(stream)
     torch.cuda.synchronize()
+    replicas.barrier(dist)
     clocks = sampler.stop()
-    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     npts = sum(int(np.prod(n)) for n, _ in shapes)
+    value, total_s = replicas.aggregate(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)) / 1e3,
+                                        npts * args.steps, dist, device="cuda")
+    total_ms = total_s * 1e3
     alg = sum(p.info().alg_bytes for p in plans)
     peak, peak_src = _peak_hbm()
     ms = total_ms / args.steps
     line = {"metric": "grid points/s of a batch of 64 uneven mixed-BC Poisson solves", "value":
-            npts * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"64 problems, n ~ U{{24..160}} per axis, BC uniform over fff/pff/ppf/ppp, "
@@ -252,7 +258,10 @@ def run_batched(args):
             "solve_roofline": {"alg_bytes": alg, "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
                                "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
             "gpu_launches": 5 * len(plans) * args.steps, "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
@@ -276,9 +285,9 @@ def main():
     import torch
 
     from paper_1211_5244_gb300 import build as _build
-    from paper_1211_5244_gb300 import psolver, synth
+    from paper_1211_5244_gb300 import psolver, replicas, synth
 
-    rank, world, local = _dist_env()
+    rank, world, local = replicas.dist_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -306,8 +315,7 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     sampler = ClockSampler(local)
-    if dist is not None:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.2)
@@ -317,15 +325,12 @@ def main():
         plan.solve(rho, V, stream=stream, E=E)
         ends[i].record(stream)
     torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+    replicas.barrier(dist)
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    npts = int(np.prod(w["n"]))
+    value, total_s = replicas.aggregate(sum(step_ms) / 1e3, K * npts, dist, device="cuda")
+    total_ms = total_s * 1e3
 
     # ---- per-pass times: the same steps again with an event between passes
     # (passes serialised on the solve stream), for the per-kernel roofline
@@ -338,8 +343,6 @@ def main():
     plan.set_profiling(False)
     pass_ms, nrec = plan.pass_times()
     pass_ms = [t / max(nrec, 1) for t in pass_ms]
-    npts = int(np.prod(w["n"]))
-    value = world * K * npts / (total_ms / 1e3)
     ms_per_step = total_ms / K
 
     # ---- end-to-end through the host-buffer entry point (pinned memory): K
@@ -348,18 +351,13 @@ def main():
     rho_host = torch.from_numpy(rho_np).pin_memory()
     V_hosts = [torch.empty_like(rho_host).pin_memory() for _ in range(2)]
     plan.solve_host_stream([rho_host] * 4, [V_hosts[i % 2] for i in range(4)])
-    if dist is not None:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plan.solve_host_stream([rho_host] * K, [V_hosts[i % 2] for i in range(K)])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * K * npts / e2e_s, "unit": UNIT,
+    e2e_value, _ = replicas.aggregate(time.perf_counter() - t0, K * npts, dist, device="cuda")
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": npts * 4, "d2h_bytes_per_step": npts * 4 + 8,
            "api": "ps_solve_host_stream (pinned host buffers, host wall clock)"}
 
