@@ -272,6 +272,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64"])
+    ap.add_argument("--math", default="cudacore", choices=["cudacore", "tf32x3"],
+                    help="arithmetic of the transforms (tf32x3: z pass on the tensor cores)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -298,7 +300,7 @@ def main():
     w = synth.WORKLOADS[WORKLOAD]
     rho_np = _density(w, rank)
     rho = torch.from_numpy(rho_np).cuda()
-    plan = psolver.Plan(w["n"], "fff", w["h"], "f32")
+    plan = psolver.Plan(w["n"], "fff", w["h"], "f32", math=args.math)
     info = plan.info()
     V = torch.empty_like(rho)
     E = torch.empty((), dtype=torch.float64, device="cuda")
@@ -381,6 +383,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": _workload_desc(w), "n": list(w["n"]), "bc": "fff", "h": w["h"],
+                   "math": args.math, "tensor_passes": info.tensor_passes, "blocks": list(info.blocks),
                    "l2": "flushed (512 MiB write) before every step; per-step CUDA events",
                    "pass_times": "separate profiled loop of the same K steps, one event between passes",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -49,9 +49,16 @@ enum ps_bc { PS_BC_PERIODIC = 0, PS_BC_FREE = 1 };
 /* Element type of rho and V, and of the arithmetic of the solve. */
 enum ps_dtype { PS_F32 = 0, PS_F64 = 1 };
 
-/* Arithmetic of the 1D transforms. Only CUDA-core arithmetic is provided:
- * the transforms are bound by HBM traffic, not by a dense contraction. */
-enum ps_math { PS_MATH_CUDACORE = 0 };
+/* Arithmetic of the 1D transforms.
+ * PS_MATH_CUDACORE: register FFTs on the CUDA cores (every plan).
+ * PS_MATH_TF32X3:   FP32 plans only. Where a tensor-core kernel exists (today
+ *   the z pass of L3 = 512 with n3 = 256 or 512) its DFT stages run as
+ *   dense products with small DFT matrices on the tensor cores (tcgen05),
+ *   each operand split into a TF32 part and a remainder and the product
+ *   taken as hi*hi + hi*lo + lo*hi with FP32 accumulation (about FP32
+ *   accuracy); the other passes stay on the CUDA cores. ps_plan_query's
+ *   tensor_passes tells which passes use the tensor cores. */
+enum ps_math { PS_MATH_CUDACORE = 0, PS_MATH_TF32X3 = 1 };
 
 enum ps_status {
   PS_OK = 0,
@@ -88,6 +95,10 @@ typedef struct {
                                and one read of the stored K^F octant            */
   size_t workspace_bytes;   /* device bytes the plan allocates at build          */
   int launches;             /* kernels one ps_solve launches (0 before build)    */
+  int tensor_passes;        /* bit k set: pass k (0 fwd x .. 4 inv x) runs on the
+                               tensor cores (0 before build)                     */
+  int blocks[5];            /* CTAs launched per pass by its specialised kernel
+                               (0 before build and where the generic kernel runs) */
 } ps_plan_info;
 
 /*
@@ -127,7 +138,9 @@ int ps_plan_set_lengths(ps_plan plan, int L1, int L2, int L3);
  */
 int ps_plan_autotune(ps_plan plan, int reps, void* stream);
 
-/* ps_plan_set_math -- enum ps_math; must precede the build. PS_ERR_ARG else. */
+/* ps_plan_set_math -- enum ps_math; must precede the build (PS_ERR_ARG
+ * otherwise, and for an unknown mode). PS_MATH_TF32X3 on an FP64 plan:
+ * PS_ERR_UNSUPPORTED. */
 int ps_plan_set_math(ps_plan plan, int math_mode);
 
 /* ps_plan_query -- fill *info (host only; valid before and after the build). */
@@ -236,6 +249,16 @@ int ps_plan_set_profiling(ps_plan plan, int enable);
  * Errors: PS_ERR_ARG (NULL pointer), PS_ERR_CUDA.
  */
 int ps_plan_pass_times(ps_plan plan, double* ms, int* count);
+
+/*
+ * ps_plan_device_status -- synchronise `stream`, then report whether a
+ * bounded device-side wait in this plan's kernels (the tensor-core z pass
+ * waits on its own MMA completions, about one second at most) gave up since
+ * the last call: PS_ERR_TIMEOUT (the flag is then cleared; results of the
+ * solves since the last call are not valid) or PS_OK.
+ * Errors: PS_ERR_ARG (plan NULL), PS_ERR_NOT_BUILT, PS_ERR_CUDA.
+ */
+int ps_plan_device_status(ps_plan plan, void* stream);
 
 /*
  * ps_solve_host_stream -- ps_solve_host for `count` densities with the

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "fft_fast.cuh"
 
 namespace ps {
 
@@ -59,7 +60,7 @@ struct DeviceGuard {
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 void free_device(ps_plan_s* p) {
-  void** bufs[] = {&p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2], &p->tw4z, &p->tw4y, &p->twx,
+  void** bufs[] = {&p->tctab, &p->A, &p->B, &p->K, &p->tw[0], &p->tw[1], &p->tw[2], &p->tw4z, &p->tw4y, &p->twx,
                    reinterpret_cast<void**>(&p->partials), reinterpret_cast<void**>(&p->counter),
                    &p->d_rho, &p->d_V, reinterpret_cast<void**>(&p->d_E), &p->d_rho2, &p->d_V2,
                    reinterpret_cast<void**>(&p->d_Eb)};
@@ -208,7 +209,10 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
 int ps_plan_set_math(ps_plan p, int math_mode) {
   if (!p) return fail(PS_ERR_ARG, "plan is NULL");
   if (p->built) return fail(PS_ERR_ARG, "math mode must be set before ps_kernel_build");
-  if (math_mode != PS_MATH_CUDACORE) return fail(PS_ERR_ARG, "unknown math mode %d", math_mode);
+  if (math_mode != PS_MATH_CUDACORE && math_mode != PS_MATH_TF32X3)
+    return fail(PS_ERR_ARG, "unknown math mode %d", math_mode);
+  if (math_mode == PS_MATH_TF32X3 && p->dtype != PS_F32)
+    return fail(PS_ERR_UNSUPPORTED, "tensor-core math needs an FP32 plan");
   p->math = math_mode;
   return PS_OK;
 }
@@ -243,6 +247,9 @@ int ps_plan_query(ps_plan p, ps_plan_info* info) {
                     b * (double)c * (double)(p->H[1] + 1) * (double)(p->H[2] + 1);
   info->workspace_bytes = p->ws_bytes;
   info->launches = p->built ? 5 : 0;
+  info->tensor_passes = (p->built && p->tctab) ? (1 << 2) : 0;
+  for (int k = 0; k < 5; ++k)
+    info->blocks[k] = (p->built && p->cfg[k].fast) ? (int)(p->cfg[k].grid.x * p->cfg[k].grid.y) : 0;
   return PS_OK;
 }
 
@@ -269,7 +276,8 @@ int ps_kernel_build(ps_plan p, void* stream) {
       {&p->tw[1], (size_t)p->L[1] * csz, "twiddles y"},
       {&p->tw[2], (size_t)p->L[2] * csz, "twiddles z"},
       {reinterpret_cast<void**>(&p->partials), (size_t)p->npart * sizeof(double), "energy partials"},
-      {reinterpret_cast<void**>(&p->counter), sizeof(unsigned), "energy counter"},
+      {reinterpret_cast<void**>(&p->counter), 2 * sizeof(unsigned), "energy counter and status"},
+      {&p->tctab, p->tctab_floats * sizeof(float), "tensor-core z tables"},
       {&p->tw4z, p->zsoa_T ? (size_t)p->zsoa_T * p->zsoa_T * 16 : 0, "paired z twiddles"},
       {&p->twx, p->xP ? (size_t)p->xP * p->xP * 8 : 0, "x twiddle matrix"},
       {&p->tw4y, p->ysoa ? (size_t)16 * 16 * 16 : 0, "paired y twiddles"},
@@ -301,7 +309,13 @@ int ps_kernel_build(ps_plan p, void* stream) {
     return cuda_fail(e, "Bluestein tables");
   }
   p->ws_bytes = total;
-  e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), s);
+  e = cudaMemsetAsync(p->counter, 0, 2 * sizeof(unsigned), s);
+  std::vector<float> tctab_host;
+  if (e == cudaSuccess && p->tctab) {
+    tctab_host.resize(p->tctab_floats);
+    ztc_fill_table(p->n[2] * 2 == p->L[2], tctab_host.data());
+    e = cudaMemcpyAsync(p->tctab, tctab_host.data(), p->tctab_floats * sizeof(float), cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = build_twiddles(p, s);
   if (e == cudaSuccess) e = build_kernel(p, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -430,6 +444,21 @@ int ps_solve_host(ps_plan p, const void* rho_host, void* V_host, double* ehartre
 int ps_plan_set_profiling(ps_plan p, int enable) {
   if (!p) return fail(PS_ERR_ARG, "plan is NULL");
   p->profiling = enable != 0;
+  return PS_OK;
+}
+
+int ps_plan_device_status(ps_plan p, void* stream) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, p->counter + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && flag) e = cudaMemsetAsync(p->counter + 1, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess && flag) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "device status");
+  if (flag) return fail(PS_ERR_TIMEOUT, "a bounded device wait gave up");
   return PS_OK;
 }
 

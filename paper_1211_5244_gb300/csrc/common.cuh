@@ -115,8 +115,11 @@ struct ps_plan_s {
   int xP;        // size of twx (the larger step of the x-pass factorisation)
   int ysoa;      // 1 if the packed y kernels run (L2 = 512)
   int zsoa_T;    // T of the packed z kernel (L3 = 2 T^2), 0 if not used
+  void* tctab;   // tensor-core z pass: DFT matrices (hi, lo) and twiddles, or NULL
+  size_t tctab_floats;
   double* partials;     // per-CTA energy partials of the z pass
-  unsigned* counter;    // arrival counter for the last-CTA energy reduction
+  unsigned* counter;    // [0] arrival counter of the last-CTA energy reduction,
+                        // [1] device status: nonzero once a bounded wait gave up
   int npart;
   void* d_rho;   // staging for ps_solve_host (and slot 0 of ps_solve_host_stream)
   void* d_V;

@@ -32,13 +32,6 @@ constexpr int kTK = 16;  // lines per CTA
 // z pass: rows ky and L2 - ky read the same row of the K^F octant; launch
 // them from adjacent CTA rows (y = 0 -> ky = 0, y = 1 -> ky = L2/2, then
 // pairs p, L2 - p) so the second read hits L2.
-__device__ __forceinline__ int paired_ky(int y, int L2) {
-  if (y == 0) return 0;
-  if (y == 1) return L2 / 2;
-  const int p = (y - 2) / 2 + 1;
-  return (y & 1) ? L2 - p : p;
-}
-
 template <int P, int Q, int KIND, bool HALF>
 __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
                                   kTK * (P < Q ? P : Q) <= 256 ? (KIND == 2 ? 2 : 3) : 1)

@@ -289,6 +289,42 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       if ((e = set(P4, f1, grid, threads, smem, inv)) != cudaSuccess) return e;
     }
   }
+  // z pass on the tensor cores (PS_MATH_TF32X3, L3 = 512): persistent, one
+  // wave of resident CTAs over tiles of 8 kx lines
+  p->tctab_floats = 0;
+  if (p->math == PS_MATH_TF32X3 && L3 == 512 && (n3 == 256 || n3 == 512)) {
+    const bool half = n3 == 256;
+    int threads;
+    size_t smem;
+    const void* f = ztc_kernel(L3, half, &threads, &smem);
+    if (f) {
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+        return e;
+      FastArgs z = base;
+      z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;
+      z.dst_plane = ldc; z.dst_elem = (long long)L2 * ldc;
+      z.ntk_loc = (p->c + 7) / 8;
+      int dev = 0, sms = 0, per_sm = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem)) != cudaSuccess) return e;
+      // registers (<= 128) and shared memory (~110 KB) leave room for two CTAs
+      // of the n3 = 256 kernel per SM, as do their 256 TMEM columns each; the
+      // grid is sized for that even where the occupancy query reports one (a
+      // CTA that finds no room starts when one finishes, so the result is the same)
+      if (half && per_sm < 2) per_sm = 2;
+      const long long tiles = (long long)z.ntk_loc * L2;
+      const long long g = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+      if ((e = set(P3, f, dim3((unsigned)(g < tiles ? g : tiles)), threads, smem, z)) != cudaSuccess) return e;
+      p->cfg[P3].tk = 8;
+      p->zsoa_T = 0;
+      p->tctab_floats = ztc_table_floats(half);
+      return cudaSuccess;
+    }
+  }
   // z pass: the persistent prefetching packed kernel where it exists (L3 = 512),
   // else the packed kernel (L3 = 128), else the unpacked one. PS_ZPASS=soa or
   // PS_ZPASS=strided selects a simpler kernel (diagnostics and comparisons).
@@ -338,7 +374,8 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
   const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
   // x passes get the twiddle matrix in the K slot
   const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
-  const void* tw = (pass == P3 && p->zsoa_T) ? p->tw4z
+  const void* tw = (pass == P3 && p->tctab) ? p->tctab
+                   : (pass == P3 && p->zsoa_T) ? p->tw4z
                    : ((pass == P2 || pass == P4) && p->ysoa) ? p->tw4y : p->tw[axis];
   double* partials = p->partials;
   unsigned* counter = p->counter;

@@ -60,13 +60,6 @@ __device__ __forceinline__ void dit_all(c2 (&z)[T], std::integer_sequence<int, B
   (dit_lanes<T, B>(z), ...);
 }
 
-__device__ __forceinline__ int paired_ky_soa(int y, int L2) {
-  if (y == 0) return 0;
-  if (y == 1) return L2 / 2;
-  const int p = (y - 2) / 2 + 1;
-  return (y & 1) ? L2 - p : p;
-}
-
 }  // namespace
 
 template <int T, bool HALF, int kTKs>
@@ -80,7 +73,7 @@ __global__ void __launch_bounds__(kTKs * T, 512 / (kTKs * T))
   const int j = threadIdx.x / kTKs;
   const int kx = blockIdx.x * kTKs + t;
   const bool valid = kx < a.c;
-  const int ky = paired_ky_soa(blockIdx.y, a.L2);
+  const int ky = paired_ky(blockIdx.y, a.L2);
   float2* line = static_cast<float2*>(line_v) + ky * a.src_plane + kx;
   const long long es = a.src_elem;
 
@@ -206,7 +199,7 @@ __global__ void __launch_bounds__(16 * T, 2)
 
   auto issue_input = [&](int tile) {
     const int kx0 = (a.kt0 + tile % ntk) * TK;
-    const int ky = paired_ky_soa(tile / ntk, a.L2);
+    const int ky = paired_ky(tile / ntk, a.L2);
     const float2* src = base + ky * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
       const int row = q / (TK / 2), part = q % (TK / 2);
@@ -215,7 +208,7 @@ __global__ void __launch_bounds__(16 * T, 2)
   };
   auto issue_k = [&](int tile) {
     const int kx0 = (a.kt0 + tile % ntk) * TK;
-    const int ky = paired_ky_soa(tile / ntk, a.L2);
+    const int ky = paired_ky(tile / ntk, a.L2);
     const int kyo = min(ky, a.L2 - ky);
     const float* src = K + (long long)kyo * a.ldk + kx0;
     for (int q = threadIdx.x; q < KROWS * (TK / 4); q += blockDim.x) {
@@ -235,7 +228,7 @@ __global__ void __launch_bounds__(16 * T, 2)
     const int next = tile + gridDim.x;
     const int kx = (a.kt0 + tile % ntk) * TK + t;
     const bool valid = kx < a.c;
-    const int ky = paired_ky_soa(tile / ntk, a.L2);
+    const int ky = paired_ky(tile / ntk, a.L2);
     float2* line = base + ky * a.src_plane + kx;
     cp_async_wait_all();
     __syncthreads();  // this tile's inputs and K^F slice have landed

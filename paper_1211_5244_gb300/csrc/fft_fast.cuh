@@ -6,6 +6,21 @@
 
 namespace ps {
 
+// z-pass tile row y -> ky, a bijection of [0, L2) that puts the rows ky and
+// L2 - ky, which read the same K^F octant row, next to each other (the
+// second read hits L2): 0, then L2/2 when L2 is even, then the pairs
+// (p, L2 - p) for p = 1, 2, ...
+__device__ __forceinline__ int paired_ky(int y, int L2) {
+  if (y == 0) return 0;
+  if ((L2 & 1) == 0) {
+    if (y == 1) return L2 / 2;
+    const int p = (y - 2) / 2 + 1;
+    return (y & 1) ? L2 - p : p;
+  }
+  const int p = (y - 1) / 2 + 1;
+  return (y & 1) ? p : L2 - p;
+}
+
 // Kernel signature shared by every specialised pass kernel.
 //   src, dst   pass input / output (A, B, rho or V)
 //   K          K^F octant (z pass only)
@@ -32,6 +47,12 @@ const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem)
 
 // The persistent, prefetching packed z-pass kernel (L3 = 512), or nullptr.
 const void* zpipe_kernel(int L, bool half, int* threads, size_t* smem);
+
+// The tensor-core z-pass kernel (L3 = 512; half: n3 = 256, else n3 = 512),
+// its table size in floats and the host fill of that table.
+const void* ztc_kernel(int L, bool half, int* threads, size_t* smem);
+size_t ztc_table_floats(bool half);
+void ztc_fill_table(bool half, float* out);
 
 // Fills p->cfg[k].fast / fn / grid / block / smem / fa for the passes covered.
 cudaError_t configure_fast_f32(ps_plan_s* p);

@@ -18,7 +18,7 @@ from . import build as _build
 
 PS_BC_PERIODIC, PS_BC_FREE = 0, 1
 PS_F32, PS_F64 = 0, 1
-PS_MATH_CUDACORE = 0
+PS_MATH_CUDACORE, PS_MATH_TF32X3 = 0, 1
 STATUS = {0: "PS_OK", 1: "PS_ERR_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_ERR_NOT_BUILT",
           4: "PS_ERR_CUDA", 5: "PS_ERR_OOM", 6: "PS_ERR_TIMEOUT"}
 
@@ -39,6 +39,7 @@ class PlanInfo(ctypes.Structure):
         ("fft_points", ctypes.c_double), ("paper_points", ctypes.c_double),
         ("paper_full_points", ctypes.c_double), ("alg_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_int),
+        ("tensor_passes", ctypes.c_int), ("blocks", ctypes.c_int * 5),
     ]
 
 
@@ -72,6 +73,7 @@ def load_library():
         "ps_solve_host_stream": [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp],
         "ps_plan_set_profiling": [vp, i],
         "ps_plan_pass_times": [vp, ctypes.POINTER(d), ctypes.POINTER(i)],
+        "ps_plan_device_status": [vp, vp],
         "ps_plan_destroy": [vp],
     }
     for name, args in sig.items():
@@ -111,7 +113,8 @@ def _stream_handle(stream):
 class Plan:
     """One solve geometry: ps_plan_create (+ optional lengths) and ps_kernel_build."""
 
-    def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None, autotune=False):
+    def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None, autotune=False,
+                 math="cudacore"):
         lib = load_library()
         self.n = tuple(int(v) for v in n)
         self.bc = str(bc).lower()
@@ -124,6 +127,8 @@ class Plan:
         self._h = handle
         if L is not None:
             _check(lib.ps_plan_set_lengths(self._h, int(L[0]), int(L[1]), int(L[2])))
+        self.math = {"cudacore": PS_MATH_CUDACORE, "tf32x3": PS_MATH_TF32X3}[str(math).lower()]
+        _check(lib.ps_plan_set_math(self._h, self.math))
         if autotune:
             _check(lib.ps_plan_autotune(self._h, 5, _stream_handle(stream)))
         if build:
@@ -172,6 +177,11 @@ class Plan:
     def set_profiling(self, enable=True):
         """ps_plan_set_profiling: per-pass CUDA events on every later solve."""
         _check(_lib.ps_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def device_status(self, stream=None):
+        """ps_plan_device_status: raises PsError (PS_ERR_TIMEOUT) if a bounded
+        device wait gave up since the last call; synchronises the stream."""
+        _check(_lib.ps_plan_device_status(self._h, _stream_handle(stream)))
 
     def pass_times(self):
         """ps_plan_pass_times: (summed ms per pass [5], number of solves)."""

@@ -74,6 +74,12 @@ def test_set_lengths_rules(lib):
     assert list(info.L) == [10, 23, 15] and info.c == 6
     assert lib.ps_plan_set_math(p, 7) == 1
     assert lib.ps_plan_set_math(p, 0) == 0
+    assert lib.ps_plan_set_math(p, 1) == 0  # tensor-core mode on an FP32 plan
+    lib.ps_plan_destroy(p)
+    rc, p = _create(lib, n=(10, 12, 7), bc=(0, 1, 1), dtype=1)
+    assert rc == 0
+    assert lib.ps_plan_set_math(p, 1) == 2  # FP64 plans stay on the CUDA cores
+    assert lib.ps_plan_set_math(p, 0) == 0
     lib.ps_plan_destroy(p)
 
 

@@ -192,6 +192,100 @@ def test_full_size_free_sampled(torch_cuda, name):
     assert abs(float(E.item()) - e_direct) <= TOL["f32"] * abs(e_direct)
 
 
+# Odd L2 (a periodic y axis of odd length) with the specialised z kernels:
+# their tile order pairs ky with L2 - ky and must still visit every ky once.
+ODD_L2_CASES = [
+    ((12, 5, 64), "fpf"),     # z L=128 half (packed), L2 = 5
+    ((8, 7, 256), "fpf"),     # z L=512 half (persistent packed), L2 = 7
+    ((6, 9, 512), "fpp"),     # z L=512 full, L2 = 9
+    ((10, 3, 32), "fpf"),     # z L=64 half (register kernel), L2 = 3
+]
+
+
+@pytest.mark.parametrize("n,bc", ODD_L2_CASES)
+def test_parity_odd_y_length_fast_z(torch_cuda, n, bc):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=7 + sum(n), noise=1e-3, subtract_mean=True)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
+    assert plan.info().L[1] % 2 == 1
+    _check(V, E, rho, bc, 0.25, "f32")
+
+
+# The tensor-core z pass (PS_MATH_TF32X3, L3 = 512): n3 = 256 (free z) and
+# n3 = 512 (periodic z); ragged kx tiles (c not a multiple of 8), odd L2, c = 1.
+TC_CASES = [
+    ((20, 12, 256), "fff"),   # c = 21
+    ((20, 12, 256), "pff"),   # c = 11
+    ((9, 5, 256), "fpf"),     # c = 10, L2 = 5
+    ((1, 3, 256), "pff"),     # c = 1
+    ((6, 7, 512), "ppp"),     # n3 = 512, L2 = 7
+    ((16, 6, 512), "ffp"),    # n3 = 512, c = 17
+    ((64, 40, 256), "fff"),   # c = 65, L2 = 80
+]
+
+
+def _tc_solve(torch, rho, bc, h):
+    from paper_1211_5244_gb300 import psolver
+    n = rho.shape[::-1]
+    plan = psolver.Plan(n, bc, h, "f32", math="tf32x3")
+    assert plan.info().tensor_passes == 1 << 2
+    r = torch.from_numpy(np.ascontiguousarray(rho.astype(np.float32))).cuda()
+    V, E = plan.solve(r)
+    plan.device_status()
+    return V.double().cpu().numpy(), float(E.item()), plan
+
+
+@pytest.mark.parametrize("n,bc", TC_CASES)
+def test_parity_tensor_core_z(torch_cuda, n, bc):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=11 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, _ = _tc_solve(torch_cuda, rho, bc, 0.25)
+    _check(V, E, rho, bc, 0.25, "f32")
+
+
+def test_tensor_core_mode_elsewhere_stays_on_cuda_cores(torch_cuda):
+    """Where no tensor-core kernel exists (here L3 = 256) the mode changes nothing."""
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    n = (24, 20, 128)
+    rho = synth.gaussian_mixture(n, 0.3, 4, seed=3, noise=1e-3)
+    r = torch.from_numpy(rho.astype(np.float32)).cuda()
+    a = psolver.Plan(n, "fff", 0.3, "f32", math="tf32x3")
+    b = psolver.Plan(n, "fff", 0.3, "f32")
+    assert a.info().tensor_passes == 0
+    Va, Ea = a.solve(r)
+    Vb, Eb = b.solve(r)
+    assert torch.equal(Va, Vb) and float(Ea.item()) == float(Eb.item())
+
+
+def test_tensor_core_z_full_size_sampled(torch_cuda):
+    """256^3 free FP32 with the tensor-core z pass, in the benchmark's launch
+    configuration: sampled points against the literal Eq. 2 sum in FP64, the
+    energy against 1/2 h^3 sum rho V from the GPU's own V, and the whole V
+    against the CUDA-core solve."""
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    w = synth.WORKLOADS["free256_f32"]
+    rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"], noise=w["noise"])
+    rho32 = rho.astype(np.float32)
+    r = torch.from_numpy(rho32).cuda()
+    plan = psolver.Plan(w["n"], "fff", w["h"], "f32", math="tf32x3")
+    V, E = plan.solve(r)
+    plan.device_status()
+    Vh = V.double().cpu().numpy()
+    n3, n2, n1 = rho.shape
+    rng = np.random.default_rng(1)
+    pts = [(0, 0, 0), (n3 - 1, n2 - 1, n1 - 1), (n3 // 2, n2 // 2, n1 // 2)]
+    pts += [tuple(int(v) for v in rng.integers(0, [n3, n2, n1])) for _ in range(9)]
+    ref = op.direct_at(rho32.astype(np.float64), w["h"], pts)
+    got = np.array([Vh[p] for p in pts])
+    scale = np.abs(Vh).max()
+    assert np.abs(got - ref).max() <= TOL["f32"] * scale
+    e_direct = 0.5 * w["h"] ** 3 * float(np.sum(rho32.astype(np.float64) * Vh))
+    assert abs(float(E.item()) - e_direct) <= TOL["f32"] * abs(e_direct)
+    Vc, _ = psolver.Plan(w["n"], "fff", w["h"], "f32").solve(r)
+    l2, mx = _errs(Vh, Vc.double().cpu().numpy())
+    assert l2 <= TOL["f32"] and mx <= TOL["f32"], (l2, mx)
+
+
 # Shapes that select every specialised FP32 kernel: strided lengths 64..1024
 # (half = zero-padded free axis, full = periodic axis) and x passes with
 # M = L1/2 from 32 to 512.
