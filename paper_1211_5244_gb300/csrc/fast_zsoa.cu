@@ -28,9 +28,8 @@ __device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.x, v.re.y
 template <int DIR>
 __device__ __forceinline__ c2 cmul_pair(c2 v, float4 w) {
   const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
-  const float2 nwi = make_float2(-w.z, -w.w);
-  if (DIR < 0) return {soa::fma2(v.im, nwi, soa::mul2(v.re, wr)), soa::fma2(v.re, wi, soa::mul2(v.im, wr))};
-  return {soa::fma2(v.im, wi, soa::mul2(v.re, wr)), soa::fma2(v.re, nwi, soa::mul2(v.im, wr))};
+  if (DIR < 0) return {soa::sub2(soa::mul2(v.re, wr), soa::mul2(v.im, wi)), soa::fma2(v.re, wi, soa::mul2(v.im, wr))};
+  return {soa::fma2(v.im, wi, soa::mul2(v.re, wr)), soa::sub2(soa::mul2(v.im, wr), soa::mul2(v.re, wi))};
 }
 
 // radix-2 DIF stage of a 2T-point forward DFT across the lanes of z[b]
