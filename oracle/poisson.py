@@ -272,6 +272,66 @@ def brute_force(rho, bc, h):
     return Vhat.real
 
 
+def kernel_fourier_from_real(kernel, n, bc, L=None):
+    """K^F of a convolution kernel given in real space (§5: the same zero-padded
+    convolution serves kernels other than the Poisson kernel, e.g. a local
+    potential applied to wave functions).
+
+    ``kernel`` has shape (L3//2 + 1, L2//2 + 1, L1//2 + 1): kernel[d3, d2, d1] is
+    the value at the offset (d1, d2, d3), and the kernel is even in every offset,
+    K(..., -d_j, ...) = K(..., d_j, ...). The full kernel on the padded grid takes
+    at index i_j the value at offset min(i_j, L_j - i_j); its full FFT is K^F
+    (real, since the kernel is even). Along a periodic axis (L_j = n_j) this is a
+    kernel of period n_j; along a free axis the offsets |d_j| <= n_j - 1 couple
+    physical points and the others are never used.
+    """
+    bc = _bc_tuple(bc)
+    Ls = padded_lengths(n, bc, L)
+    kernel = np.asarray(kernel, dtype=np.float64)
+    want = (Ls[2] // 2 + 1, Ls[1] // 2 + 1, Ls[0] // 2 + 1)
+    if kernel.shape != want:
+        raise ValueError(f"kernel octant must have shape {want}, got {kernel.shape}")
+    idx = [np.minimum(np.arange(Lj), Lj - np.arange(Lj)) for Lj in Ls]
+    full = kernel[np.ix_(idx[2], idx[1], idx[0])]
+    return np.fft.fftn(full)
+
+
+def convolve(rho, bc, h, kernel, L=None):
+    """V = K * rho (Eq. 2 with a caller's kernel, no h^3 factor added) and
+    E = 1/2 h^3 sum rho V, by the zero-padded FFT of ``solve``."""
+    rho = np.asarray(rho, dtype=np.float64)
+    n = rho.shape[::-1]
+    KF = kernel_fourier_from_real(kernel, n, bc, L)
+    return solve(rho, bc, h, L=L, KF=KF)
+
+
+def convolve_direct(rho, bc, kernel):
+    """The literal sum V(r) = sum_r' K(r - r') rho(r') for tiny grids, with the
+    kernel's octant values: along a free axis the offset is r_j - r'_j, along a
+    periodic axis it is taken modulo n_j; either way the value used is the one at
+    |offset| folded into [0, L_j // 2] (L_j = 2 n_j free, n_j periodic)."""
+    bc = _bc_tuple(bc)
+    rho = np.asarray(rho, dtype=np.float64)
+    n3, n2, n1 = rho.shape
+    n = (n1, n2, n3)
+    Ls = padded_lengths(n, bc)
+    kernel = np.asarray(kernel, dtype=np.float64)
+    V = np.zeros_like(rho)
+    tgt = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    for s3, s2, s1 in itertools.product(range(n3), range(n2), range(n1)):
+        off = []
+        for j, (t, sj) in enumerate(zip(tgt[::-1], (s1, s2, s3))):
+            d = t - sj
+            if bc[j] == "p":
+                d = np.mod(d, n[j])
+                d = np.minimum(d, n[j] - d)
+            else:
+                d = np.abs(d)
+            off.append(d)
+        V += rho[s3, s2, s1] * kernel[off[2], off[1], off[0]]
+    return V
+
+
 def direct_at(rho, h, points):
     """Eq. 2 evaluated literally at selected grid points, free BCs on all axes:
     V(t) = sum_r' K(t - r') rho(r') for each t = (k, j, i) in ``points``

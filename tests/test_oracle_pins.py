@@ -308,3 +308,57 @@ def test_direct_at_matches_brute_force():
     pts = [(0, 0, 0), (5, 4, 6), (2, 3, 1)]
     got = op.direct_at(rho, 0.3, pts)
     assert np.abs(got - np.array([Vb[p] for p in pts])).max() < 1e-13 * np.abs(Vb).max()
+
+
+# ---- convolution with a caller's kernel (§5: the same zero-padded convolution
+# for other kernels, e.g. a local potential applied to wave functions)
+
+def _kernel_octant(rng, n, bc):
+    L = op.padded_lengths(n, bc)
+    return rng.standard_normal((L[2] // 2 + 1, L[1] // 2 + 1, L[0] // 2 + 1))
+
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+@pytest.mark.parametrize("n", [(5, 4, 3), (3, 6, 7), (1, 5, 4)])
+def test_convolve_matches_literal_sum(bc, n):
+    """FFT convolution with a random even kernel == the literal double sum
+    (odd periodic lengths included: n = 5, 3, 7)."""
+    rng = np.random.default_rng(sum(n) + ALL_BCS.index(bc))
+    k = _kernel_octant(rng, n, bc)
+    rho = rng.standard_normal(n[::-1])
+    V, E = op.convolve(rho, bc, 0.3, k)
+    Vd = op.convolve_direct(rho, bc, k)
+    assert np.abs(V - Vd).max() <= 1e-13 * np.abs(Vd).max()
+    assert abs(E - 0.5 * 0.3 ** 3 * np.sum(rho * Vd)) <= 1e-13 * abs(E)
+
+
+@pytest.mark.parametrize("bc", ["fff", "pfp", "ppp"])
+def test_convolve_delta_kernel_is_identity(bc):
+    n = (6, 5, 4)
+    L = op.padded_lengths(n, bc)
+    k = np.zeros((L[2] // 2 + 1, L[1] // 2 + 1, L[0] // 2 + 1))
+    k[0, 0, 0] = 1.0
+    rho = np.random.default_rng(3).standard_normal(n[::-1])
+    V, _ = op.convolve(rho, bc, 0.5, k)
+    assert np.abs(V - rho).max() < 1e-14 * np.abs(rho).max()
+
+
+def test_convolve_with_sampled_free_kernel_is_the_free_solve():
+    """The free-space Poisson kernel sampled on the octant (Eq. 2 with K = h^3 G
+    and the cell-averaged K(0)) reproduces the free-BC solve."""
+    n = (6, 5, 7)
+    h = 0.4
+    L = op.padded_lengths(n, "fff")
+    d = [np.arange(Lj // 2 + 1) for Lj in L]
+    dist = np.sqrt(d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2)
+    k = op.green_mixed(0, 0.0, dist, h)
+    rho = np.random.default_rng(4).standard_normal(n[::-1])
+    V, E = op.convolve(rho, "fff", h, k)
+    Vs, Es = op.solve(rho, "fff", h)
+    assert np.abs(V - Vs).max() < 1e-13 * np.abs(Vs).max()
+    assert abs(E - Es) < 1e-13 * abs(Es)
+
+
+def test_convolve_rejects_wrong_octant_shape():
+    with pytest.raises(ValueError):
+        op.convolve(np.zeros((3, 4, 5)), "fff", 0.3, np.zeros((4, 5, 5)))
