@@ -135,13 +135,24 @@ def _density(w, rank=0):
     return rho.astype(np.float32)
 
 
-def _oracle_baseline(w, rho32, V_gpu, E_gpu):
+def _localpot_octant(w):
+    """Even kernel of the local-potential workload: a Gaussian of width 2 grid
+    steps over the offsets (a stand-in for the convolution kernel of a local
+    potential applied to wave functions, §5), on its octant (L/2 + 1)^3."""
+    import numpy as np
+    d = np.arange(w["n"][0] + 1, dtype=np.float64)
+    r2 = d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2
+    return np.exp(-r2 / 8.0)
+
+
+def _oracle_baseline(w, rho32, V_gpu, E_gpu, kernel=None):
     """The FP64 oracle as it stands, timed on the host on one full solve of the
     workload (K^F built before the timed region, like the GPU's kernel build)."""
     import numpy as np
     from oracle import poisson as op
     rho = rho32.astype(np.float64)
-    KF = op.kernel_fourier(w["n"], "fff", w["h"])
+    KF = (op.kernel_fourier(w["n"], "fff", w["h"]) if kernel is None
+          else op.kernel_fourier_from_real(kernel, w["n"], "fff"))
     t0 = time.perf_counter()
     Vo, Eo = op.solve(rho, "fff", w["h"], KF=KF)
     dt = time.perf_counter() - t0
@@ -271,7 +282,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64", "localpot256"],
+                    help="localpot256: the 256^3 free solve with a caller's even kernel (ps_kernel_set_real)")
     ap.add_argument("--math", default="cudacore", choices=["cudacore", "tf32x3"],
                     help="arithmetic of the transforms (tf32x3: z pass on the tensor cores)")
     args = ap.parse_args()
@@ -301,6 +313,10 @@ def main():
     rho_np = _density(w, rank)
     rho = torch.from_numpy(rho_np).cuda()
     plan = psolver.Plan(w["n"], "fff", w["h"], "f32", math=args.math)
+    kernel = None
+    if args.workload == "localpot256":
+        kernel = _localpot_octant(w)
+        plan.set_kernel_real(kernel)
     info = plan.info()
     V = torch.empty_like(rho)
     E = torch.empty((), dtype=torch.float64, device="cuda")
@@ -382,7 +398,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": _workload_desc(w), "n": list(w["n"]), "bc": "fff", "h": w["h"],
+        "config": {"workload": _workload_desc(w) + ("; caller's kernel: Gaussian of width 2 steps (ps_kernel_set_real)"
+                                                    if kernel is not None else ""),
+                   "n": list(w["n"]), "bc": "fff", "h": w["h"],
                    "math": args.math, "tensor_passes": info.tensor_passes, "blocks": list(info.blocks),
                    "l2": "flushed (512 MiB write) before every step; per-step CUDA events",
                    "pass_times": "separate profiled loop of the same K steps, one event between passes",
@@ -397,7 +415,7 @@ def main():
         "kernel_src": _src_hash(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base, err = _oracle_baseline(w, rho_np, V.double().cpu().numpy(), float(E.item()))
+        base, err = _oracle_baseline(w, rho_np, V.double().cpu().numpy(), float(E.item()), kernel)
         line["cpu_baseline"] = base
         line["error_vs_oracle"] = err
     if rank == 0:

@@ -165,6 +165,26 @@ int ps_kernel_build(ps_plan plan, void* stream);
 int ps_kernel_get(ps_plan plan, void* dst, void* stream);
 
 /*
+ * ps_kernel_set_real -- replace the plan's kernel by a caller's convolution
+ * kernel given in real space, so that ps_solve and the other solve calls
+ * compute V(r) = sum_r' K(r - r') rho(r') with it (§5: the same zero-padded
+ * convolution serves other kernels, e.g. a local potential applied to many
+ * wave functions; a complex field is two real solves). No h^3 factor is
+ * added; the energy output is still 1/2 h^3 sum rho V.
+ *   kernel  host pointer, FP64, the kernel's even octant of offsets,
+ *           kernel[d1 + D1*(d2 + D2*d3)], d_j = 0 .. L_j/2 (floor), D_j = L_j/2 + 1;
+ *           the kernel must be even in every offset (K(-d) = K(d)), which is
+ *           what makes K^F real. Along a free axis |d_j| <= n_j - 1 couple
+ *           physical points (larger offsets are never used); along a periodic
+ *           axis the kernel has period n_j.
+ * K^F is formed on the device in FP64 (even-cosine transforms along all three
+ * axes), scaled by 1/(L1 L2 L3) and stored in the plan's dtype. The plan must
+ * be built; synchronises `stream`. The previous kernel is overwritten.
+ * Errors: PS_ERR_ARG (NULL), PS_ERR_NOT_BUILT, PS_ERR_CUDA.
+ */
+int ps_kernel_set_real(ps_plan plan, const double* kernel, void* stream);
+
+/*
  * ps_solve -- V = K * rho (Eq. 2 via Eq. 3 on the padded grid), and
  * optionally the Hartree energy E = 1/2 h^3 sum rho V.
  *   rho           device pointer, n1*n2*n3 dtype elements (read only)

@@ -327,6 +327,16 @@ int ps_kernel_build(ps_plan p, void* stream) {
   return PS_OK;
 }
 
+int ps_kernel_set_real(ps_plan p, const double* kernel, void* stream) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
+  if (!kernel) return fail(PS_ERR_ARG, "kernel is NULL");
+  DeviceGuard g(p->device);
+  cudaError_t e = build_kernel_from_real(p, kernel, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "kernel from real space");
+  return PS_OK;
+}
+
 int ps_kernel_get(ps_plan p, void* dst, void* stream) {
   if (!p) return fail(PS_ERR_ARG, "plan is NULL");
   if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");

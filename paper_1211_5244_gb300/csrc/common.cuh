@@ -163,5 +163,7 @@ cudaError_t batch_solve_graph(int count, ps_plan_s* const* plans, const void* co
                               double* E, int device, cudaStream_t s);
 void batch_forget_plan(const ps_plan_s* p);
 cudaError_t build_kernel(ps_plan_s* p, cudaStream_t s);
+// K^F from a caller's real-space kernel on its even octant (host, FP64)
+cudaError_t build_kernel_from_real(ps_plan_s* p, const double* host_octant, cudaStream_t s);
 
 }  // namespace ps

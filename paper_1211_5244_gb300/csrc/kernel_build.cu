@@ -369,4 +369,44 @@ done:
   return e;
 }
 
+// A caller's kernel given in real space on its even octant, octant[d1 + D0 (d2
+// + D1 d3)] = K(d1, d2, d3), d_j <= L_j / 2: the even-cosine transform along
+// every axis (free and periodic alike: an even sequence of period L_j) gives
+// K^F on the octant of wavenumber indices, stored like build_kernel's.
+cudaError_t build_kernel_from_real(ps_plan_s* p, const double* host_octant, cudaStream_t s) {
+  const int D0 = p->H[0] + 1, D1 = p->H[1] + 1, D2 = p->H[2] + 1;
+  const size_t total = (size_t)D0 * D1 * D2;
+  double *M0 = nullptr, *M1 = nullptr, *tab = nullptr;
+  int maxL = 0;
+  for (int j = 0; j < 3; ++j) maxL = p->L[j] > maxL ? p->L[j] : maxL;
+  cudaError_t e = cudaMalloc(&M0, total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&M1, total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&tab, (size_t)maxL * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(M0, host_octant, total * sizeof(double), cudaMemcpyHostToDevice, s);
+  for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+    cos_table_kernel<<<grid_for(p->L[j]), 256, 0, s>>>(tab, p->L[j]);
+    cos_transform_kernel<<<grid_for(total), 256, 0, s>>>(M0, M1, D0, D1, D2, j, p->L[j], tab);
+    double* t = M0; M0 = M1; M1 = t;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const double scale = 1.0 / ((double)p->L[0] * (double)p->L[1] * (double)p->L[2]);
+    e = cudaMemsetAsync(p->K, 0, p->ldk * (size_t)D1 * D2 * p->esz, s);
+    if (e == cudaSuccess) {
+      if (p->dtype == PS_F32)
+        store_kernel<float><<<grid_for(total), 256, 0, s>>>(M0, static_cast<float*>(p->K), total, D0, p->ldk, scale);
+      else
+        store_kernel<double><<<grid_for(total), 256, 0, s>>>(M0, static_cast<double*>(p->K), total, D0, p->ldk,
+                                                              scale);
+      e = cudaGetLastError();
+    }
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  if (M0) cudaFree(M0);
+  if (M1) cudaFree(M1);
+  if (tab) cudaFree(tab);
+  return e;
+}
+
 }  // namespace ps

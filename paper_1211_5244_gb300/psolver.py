@@ -65,6 +65,7 @@ def load_library():
         "ps_plan_query": [vp, ctypes.POINTER(PlanInfo)],
         "ps_kernel_build": [vp, vp],
         "ps_kernel_get": [vp, vp, vp],
+        "ps_kernel_set_real": [vp, vp, vp],
         "ps_solve": [vp, vp, vp, vp, vp],
         "ps_solve_adjoint": [vp, vp, vp, vp],
         "ps_solve_vjp": [vp, vp, vp, vp, vp, vp],
@@ -269,6 +270,19 @@ class Plan:
         E = (ctypes.c_double * max(count, 1))() if energy else None
         _check(_lib.ps_solve_host_stream(self._h, count, rp, vp, E, _stream_handle(stream)))
         return V_hosts, (list(E)[:count] if energy else None)
+
+    def set_kernel_real(self, kernel, stream=None):
+        """ps_kernel_set_real: use a caller's even real-space kernel, given as a
+        float64 array of shape (L3//2 + 1, L2//2 + 1, L1//2 + 1) of the values at
+        the offsets (d1, d2, d3), for every later solve."""
+        import numpy as np
+        L = self.info().L
+        want = (L[2] // 2 + 1, L[1] // 2 + 1, L[0] // 2 + 1)
+        k = np.ascontiguousarray(kernel, dtype=np.float64)
+        if k.shape != want:
+            raise ValueError(f"kernel octant must have shape {want}, got {k.shape}")
+        _check(_lib.ps_kernel_set_real(self._h, k.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
+        return self
 
     def kernel_octant(self, stream=None):
         """ps_kernel_get: the stored K^F / (L1 L2 L3) octant, shape (L3/2+1, L2/2+1, c)."""

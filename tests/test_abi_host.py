@@ -89,6 +89,9 @@ def test_solve_on_unbuilt_plan_is_rejected_before_any_launch(lib):
     assert lib.ps_solve(p, fake_in, fake_out, None, None) == 3
     assert lib.ps_solve_adjoint(p, fake_in, fake_out, None) == 3
     assert lib.ps_kernel_get(p, fake_out, None) == 3
+    assert lib.ps_kernel_set_real(p, fake_in, None) == 3
+    assert lib.ps_kernel_set_real(None, fake_in, None) == 1
+    assert lib.ps_plan_device_status(p, None) == 3
     assert lib.ps_solve(p, None, fake_out, None, None) == 1
     assert lib.ps_solve(None, fake_in, fake_out, None, None) == 1
     arr = ctypes.c_void_p * 1
