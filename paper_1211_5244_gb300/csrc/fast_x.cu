@@ -88,16 +88,19 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   }
   __syncthreads();
   if (!valid) return;
+  // outputs k and M - k from the same pair Z[k], Z[M - k]: E[M-k] = conj E[k],
+  // O[M-k] = conj O[k] and W_L1^{M-k} = -conj W_L1^k, so X[M-k] = conj(E[k] - W^k O[k])
 #pragma unroll
-  for (int i = 0; i <= M / T; ++i) {
+  for (int i = 0; i <= M / (2 * T); ++i) {
     const int k = j + T * i;
-    if (k > M) break;
-    const float2 zk = zr[k == M ? 0 : k];
+    if (k > M / 2) break;
+    const float2 zk = zr[k];
     const float2 zm = zr[k == 0 ? 0 : M - k];
     const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
     const float2 wo = xmul(o, __ldg(&tw[k]));
     X[k] = make_float2(e.x + wo.x, e.y + wo.y);
+    if (2 * k != M) X[M - k] = make_float2(e.x - wo.x, wo.y - e.y);
   }
 }
 
@@ -246,23 +249,23 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   if (pow2(L2) && (n2 == L2 / 2 || n2 == L2)) {
     const bool half = n2 == L2 / 2;
     int threads;
-    size_t smem;
+    size_t smem0 = 0, smem1 = 0;  // the forward and inverse kernels may differ
     // the persistent prefetching kernels where they exist (PS_YPASS=plain keeps
     // the non-persistent ones)
     const char* yp = getenv("PS_YPASS");
     const bool ypipe = !(yp && strcmp(yp, "plain") == 0);
     const bool ysoa = yp && strcmp(yp, "soa") == 0;
-    const void* f0 = ysoa ? ysoa_kernel(L2, 0, half, &threads, &smem) : nullptr;
-    const void* f1 = ysoa ? ysoa_kernel(L2, 1, half, &threads, &smem) : nullptr;
+    const void* f0 = ysoa ? ysoa_kernel(L2, 0, half, &threads, &smem0) : nullptr;
+    const void* f1 = ysoa ? ysoa_kernel(L2, 1, half, &threads, &smem1) : nullptr;
     p->ysoa = (f0 && f1) ? 1 : 0;
     if (!p->ysoa) {
-      f0 = ypipe ? ypipe_kernel(L2, 0, half, &threads, &smem) : nullptr;
-      f1 = ypipe ? ypipe_kernel(L2, 1, half, &threads, &smem) : nullptr;
+      f0 = ypipe ? ypipe_kernel(L2, 0, half, &threads, &smem0) : nullptr;
+      f1 = ypipe ? ypipe_kernel(L2, 1, half, &threads, &smem1) : nullptr;
     }
     const bool ypersist = f0 && f1;
     if (!ypersist) {
-      f0 = strided_kernel(L2, 0, half, &threads, &smem);
-      f1 = strided_kernel(L2, 1, half, &threads, &smem);
+      f0 = strided_kernel(L2, 0, half, &threads, &smem0);
+      f1 = strided_kernel(L2, 1, half, &threads, &smem1);
     }
     if (f0 && f1) {
       FastArgs fwd = base, inv = base;
@@ -270,23 +273,30 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       fwd.dst_plane = (long long)L2 * ldc; fwd.dst_elem = ldc;   // B[z][ky][kx]
       inv.src_plane = (long long)L2 * ldc; inv.src_elem = ldc;
       inv.dst_plane = (long long)n2 * ldc; inv.dst_elem = ldc;
-      dim3 grid(ntk, n3);
+      dim3 grid0(ntk, n3), grid1(ntk, n3);
       if (ypersist) {
         fwd.nrows = inv.nrows = n3;  // z planes walked by the persistent CTAs
-        if (smem > 48 * 1024 &&
-            ((e = cudaFuncSetAttribute(f0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-             (e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess))
-          return e;
-        int dev = 0, sms = 0, per_sm = 0;
+        int dev = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f0, threads, smem)) != cudaSuccess) return e;
         const long long tiles = (long long)ntk * n3;
-        const long long g = (long long)(per_sm > 0 ? per_sm : 1) * sms;
-        grid = dim3((unsigned)(g < tiles ? g : tiles), 1);
+        auto persistent_grid = [&](const void* f, size_t smem, dim3* grid) -> cudaError_t {
+          cudaError_t err = cudaSuccess;
+          if (smem > 48 * 1024 &&
+              (err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return err;
+          int per_sm = 0;
+          if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem)) != cudaSuccess)
+            return err;
+          const long long g = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+          *grid = dim3((unsigned)(g < tiles ? g : tiles), 1);
+          return cudaSuccess;
+        };
+        if ((e = persistent_grid(f0, smem0, &grid0)) != cudaSuccess) return e;
+        if ((e = persistent_grid(f1, smem1, &grid1)) != cudaSuccess) return e;
       }
-      if ((e = set(P2, f0, grid, threads, smem, fwd)) != cudaSuccess) return e;
-      if ((e = set(P4, f1, grid, threads, smem, inv)) != cudaSuccess) return e;
+      if ((e = set(P2, f0, grid0, threads, smem0, fwd)) != cudaSuccess) return e;
+      if ((e = set(P4, f1, grid1, threads, smem1, inv)) != cudaSuccess) return e;
     }
   }
   // z pass on the tensor cores (PS_MATH_TF32X3, L3 = 512): persistent, one
