@@ -37,18 +37,22 @@ PASS_NAMES = ["p1_fwd_x_r2c", "p2_fwd_y", "p3_z_fwd_mul_inv", "p4_inv_y", "p5_in
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the named kernel on this workload, with the hash of the
-# kernel sources it was taken on; reported as null once the sources change.
+# source files that kernel is built from; reported as null once they change.
+Z_KERNEL_FILES = ("fast_zsoa.cu", "fft_soa.cuh", "fft_regs.cuh", "fft_fast.cuh", "reduce.cuh", "common.cuh",
+                  "../../include/psolver.h")
 TRAFFIC = {
-    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 362058496 + 214589952, "src": "ee541696908cc6df"},
+    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 362058496 + 214589952, "files": Z_KERNEL_FILES,
+                                          "src": "244bcdafa2332f41"},
 }
 
 
-def _src_hash():
+def _src_hash(files=None):
+    """Hash of the CUDA sources (all of them, or the named files)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1211_5244_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    names = files if files is not None else sorted(n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh")))
+    for name in names:
+        h.update(open(os.path.normpath(os.path.join(csrc, name)), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -387,7 +391,8 @@ def main():
     dom = max(range(5), key=lambda k: pass_ms[k])
     achieved = pbytes[dom] / (pass_ms[dom] / 1e3) / 1e9
     tr = TRAFFIC.get((PASS_NAMES[dom], WORKLOAD))
-    traffic = tr["bytes"] if tr and tr["src"] == _src_hash() else None
+    traffic = tr["bytes"] if (tr and args.math == "cudacore" and args.workload == WORKLOAD
+                              and tr["src"] == _src_hash(tr["files"])) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": PASS_NAMES[dom], "alg_bytes_per_launch": pbytes[dom],
             "peak_source": peak_src}
