@@ -75,6 +75,8 @@ struct FastArgs {
   long long dst_plane, dst_elem;
   long long kz_stride;    // z pass: (L2/2 + 1) * ldk, the kz stride of the K^F octant
   int kt0, ntk_loc;       // persistent y/z kernels: first kx tile and number of kx tiles walked
+  int nl;                 // y/z passes: physical points along the line (n2 or n3); rows at and
+                          // beyond nl are zero on input and not stored on output
 };
 
 struct PassCfg {

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
 #pragma unroll
       for (int aa = 0; aa < P; ++aa) {
         y[u][aa] = make_float2(0.f, 0.f);
-        if (aa < NA && valid) y[u][aa] = s[(long long)(b + Q * aa) * a.src_elem];
+        if (aa < NA && valid && b + Q * aa < a.nl) y[u][aa] = s[(long long)(b + Q * aa) * a.src_elem];
       }
     }
 #pragma unroll
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
       rdft<P, 1, false>(y);
       if (valid) {
 #pragma unroll
-        for (int aa = 0; aa < NA; ++aa) d[(long long)(b + Q * aa) * a.dst_elem] = y[aa];
+        for (int aa = 0; aa < NA; ++aa)
+          if (b + Q * aa < a.nl) d[(long long)(b + Q * aa) * a.dst_elem] = y[aa];
       }
     }
     if constexpr (KIND == 2) {
@@ -188,6 +189,11 @@ __device__ __forceinline__ void cpa16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// 16 bytes of zeros into shared memory through the same async path (no global read)
+__device__ __forceinline__ void cpa16_zero(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -220,7 +226,10 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
     const float2* sp = src + (long long)(tile / ntk) * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (kTK / 2); q += blockDim.x) {
       const int row = q / (kTK / 2), part = q % (kTK / 2);
-      cpa16(sh + row * kTK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
+      if (KIND == 1 || row < a.nl)
+        cpa16(sh + row * kTK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
+      else  // beyond the physical rows of the plane: zeros
+        cpa16_zero(sh + row * kTK + 2 * part, sp);
     }
   };
 
@@ -310,7 +319,8 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
         rdft<P, 1, false>(y[u]);
         if (valid) {
 #pragma unroll
-          for (int aa = 0; aa < NA; ++aa) d[(long long)(b + Q * aa) * a.dst_elem] = y[u][aa];
+          for (int aa = 0; aa < NA; ++aa)
+            if (b + Q * aa < a.nl) d[(long long)(b + Q * aa) * a.dst_elem] = y[u][aa];
         }
       }
     }

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
 #pragma unroll
     for (int aa = 0; aa < P; ++aa) {
       y[aa] = make_float2(0.f, 0.f);
-      if (aa < NA && valid) y[aa] = z[b + Q * aa];
+      if (aa < NA && valid && 2 * (b + Q * aa) < a.n1) y[aa] = z[b + Q * aa];
     }
     rdft<P, -1, HALF>(y);
 #pragma unroll
@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     rdft<P, 1, false>(y);
     if (valid) {
 #pragma unroll
-      for (int aa = 0; aa < NA; ++aa) z[b + Q * aa] = y[aa];
+      for (int aa = 0; aa < NA; ++aa)
+        if (2 * (b + Q * aa) < a.n1) z[b + Q * aa] = y[aa];
     }
   }
 }
@@ -231,9 +232,12 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   const int ntk = (p->c + 15) / 16;
 
   // x passes: L1 = 2M, n1 = M (free) or 2M (periodic)
-  if (L1 % 2 == 0 && pow2(L1 / 2) && (n1 == L1 / 2 || n1 == L1) && n1 % 2 == 0) {
+  // x passes: L1 = 2M; n1 <= M (zero padding: inputs beyond n1 are zero,
+  // outputs beyond n1 are not stored) or n1 = L1 (periodic); n1 even, so the
+  // rows of rho and V stay aligned for the 8-byte pair loads
+  if (L1 % 2 == 0 && pow2(L1 / 2) && (n1 <= L1 / 2 || n1 == L1) && n1 % 2 == 0) {
     const int M = L1 / 2;
-    const bool half = n1 == M;
+    const bool half = n1 <= M;
     int threads, rows;
     size_t smem;
     const void* f0 = xline_kernel(M, 0, half, &threads, &rows, &smem);
@@ -246,15 +250,16 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     }
   }
   // y passes
-  if (pow2(L2) && (n2 == L2 / 2 || n2 == L2)) {
-    const bool half = n2 == L2 / 2;
+  // y passes: n2 <= L2/2 (zero padding) or n2 = L2 (periodic)
+  if (pow2(L2) && (n2 <= L2 / 2 || n2 == L2)) {
+    const bool half = n2 <= L2 / 2;
     int threads;
     size_t smem0 = 0, smem1 = 0;  // the forward and inverse kernels may differ
     // the persistent prefetching kernels where they exist (PS_YPASS=plain keeps
     // the non-persistent ones)
     const char* yp = getenv("PS_YPASS");
     const bool ypipe = !(yp && strcmp(yp, "plain") == 0);
-    const bool ysoa = yp && strcmp(yp, "soa") == 0;
+    const bool ysoa = yp && strcmp(yp, "soa") == 0 && (2 * n2 == L2 || n2 == L2);
     const void* f0 = ysoa ? ysoa_kernel(L2, 0, half, &threads, &smem0) : nullptr;
     const void* f1 = ysoa ? ysoa_kernel(L2, 1, half, &threads, &smem1) : nullptr;
     p->ysoa = (f0 && f1) ? 1 : 0;
@@ -269,6 +274,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     }
     if (f0 && f1) {
       FastArgs fwd = base, inv = base;
+      fwd.nl = inv.nl = n2;
       fwd.src_plane = (long long)n2 * ldc; fwd.src_elem = ldc;   // A[z][y][kx]
       fwd.dst_plane = (long long)L2 * ldc; fwd.dst_elem = ldc;   // B[z][ky][kx]
       inv.src_plane = (long long)L2 * ldc; inv.src_elem = ldc;
@@ -314,6 +320,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
                                     (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
         return e;
       FastArgs z = base;
+      z.nl = n3;
       z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;
       z.dst_plane = ldc; z.dst_elem = (long long)L2 * ldc;
       z.ntk_loc = (p->c + 7) / 8;
@@ -338,8 +345,8 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   // z pass: the persistent prefetching packed kernel where it exists (L3 = 512),
   // else the packed kernel (L3 = 128), else the unpacked one. PS_ZPASS=soa or
   // PS_ZPASS=strided selects a simpler kernel (diagnostics and comparisons).
-  if (pow2(L3) && (n3 == L3 / 2 || n3 == L3)) {
-    const bool half = n3 == L3 / 2;
+  if (pow2(L3) && (n3 <= L3 / 2 || n3 == L3)) {
+    const bool half = n3 <= L3 / 2;
     int threads;
     size_t smem;
     const char* zp = getenv("PS_ZPASS");
@@ -355,6 +362,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     if (!f) f = strided_kernel(L3, 2, half, &threads, &smem);
     if (f) {
       FastArgs z = base;
+      z.nl = n3;
       z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;      // B[z][ky][kx], line along z
       z.dst_plane = ldc; z.dst_elem = (long long)L2 * ldc;
       dim3 grid((p->c + ztile - 1) / ztile, L2);

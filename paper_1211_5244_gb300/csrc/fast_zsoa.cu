@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(kTKs * T, 512 / (kTKs * T))
   for (int aa = 0; aa < P; ++aa) {
     y[aa] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     if (aa < NA && valid) {
-      const float2 u0 = line[(long long)(j + Q * aa) * es];
-      const float2 u1 = line[(long long)(j + T + Q * aa) * es];
+      const int r0 = j + Q * aa, r1 = r0 + T;
+      const float2 u0 = r0 < a.nl ? line[(long long)r0 * es] : make_float2(0.f, 0.f);
+      const float2 u1 = r1 < a.nl ? line[(long long)r1 * es] : make_float2(0.f, 0.f);
       y[aa] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
     }
   }
@@ -136,8 +137,9 @@ __global__ void __launch_bounds__(kTKs * T, 512 / (kTKs * T))
   if (valid) {
 #pragma unroll
     for (int aa = 0; aa < NA; ++aa) {
-      line[(long long)(j + Q * aa) * es] = make_float2(y[aa].re.x, y[aa].im.x);
-      line[(long long)(j + T + Q * aa) * es] = make_float2(y[aa].re.y, y[aa].im.y);
+      const int r0 = j + Q * aa, r1 = r0 + T;
+      if (r0 < a.nl) line[(long long)r0 * es] = make_float2(y[aa].re.x, y[aa].im.x);
+      if (r1 < a.nl) line[(long long)r1 * es] = make_float2(y[aa].re.y, y[aa].im.y);
     }
   }
   if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
@@ -167,6 +169,10 @@ const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16_zero(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -202,7 +208,10 @@ __global__ void __launch_bounds__(16 * T, 2)
     const float2* src = base + ky * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
       const int row = q / (TK / 2), part = q % (TK / 2);
-      cp_async16(stage + row * TK + 2 * part, src + (long long)row * es + 2 * part);
+      if (row < a.nl)
+        cp_async16(stage + row * TK + 2 * part, src + (long long)row * es + 2 * part);
+      else  // beyond the physical z rows: zeros
+        cp_async16_zero(stage + row * TK + 2 * part, src);
     }
   };
   auto issue_k = [&](int tile) {
@@ -293,8 +302,8 @@ __global__ void __launch_bounds__(16 * T, 2)
       const long long step = (long long)Q * es;
 #pragma unroll
       for (int aa = 0; aa < NA; ++aa) {
-        *p0 = make_float2(y[aa].re.x, y[aa].im.x);
-        *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+        if (j + Q * aa < a.nl) *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+        if (j + T + Q * aa < a.nl) *p1 = make_float2(y[aa].re.y, y[aa].im.y);
         p0 += step;
         p1 += step;
       }

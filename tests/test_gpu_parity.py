@@ -192,6 +192,32 @@ def test_full_size_free_sampled(torch_cuda, name):
     assert abs(float(E.item()) - e_direct) <= TOL["f32"] * abs(e_direct)
 
 
+# Power-of-two padded lengths above 2n (any L >= 2n - 1 is exact, §2): the
+# specialised kernels then see physical counts below L/2, inputs beyond them
+# zero and outputs beyond them not stored.
+PADDED_CASES = [
+    ((42, 50, 100), "fff", (128, 128, 256)),  # x M=64 (n1=42), y L=128 (n2=50), z L=256 (n3=100)
+    ((30, 45, 200), "pff", (30, 128, 512)),   # y odd n2=45, z persistent packed (n3=200)
+    ((60, 33, 130), "fff", (128, 128, 512)),  # n3=130 with the persistent z kernel
+    ((100, 64, 7), "fff", (256, 128, 14)),    # x M=128 (n1=100), z generic
+    ((8, 300, 8), "ffp", (16, 1024, 8)),      # y L=1024 (n2=300)
+    ((16, 100, 16), "fff", (32, 256, 32)),    # y persistent L=256 (n2=100)
+    ((24, 20, 60), "fff", (64, 64, 128)),     # z packed L=128 (n3=60), x M=32 (n1=24)
+    ((18, 9, 31), "fff", (64, 64, 64)),       # odd n2, n3; L=64 y and z
+]
+
+
+@pytest.mark.parametrize("n,bc,L", PADDED_CASES)
+def test_parity_padded_below_half(torch_cuda, n, bc, L):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=13 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L)
+    assert list(plan.info().L) == list(L)
+    # the specialised kernels take the padded passes
+    blocks = list(plan.info().blocks)
+    assert blocks[1] > 0 and blocks[3] > 0, blocks
+    _check(V, E, rho, bc, 0.25, "f32", L=L)
+
+
 # Odd L2 (a periodic y axis of odd length) with the specialised z kernels:
 # their tile order pairs ky with L2 - ky and must still visit every ky once.
 ODD_L2_CASES = [
