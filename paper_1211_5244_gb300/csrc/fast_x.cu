@@ -351,18 +351,24 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     size_t smem;
     const char* zp = getenv("PS_ZPASS");
     const bool allow_soa = !(zp && strcmp(zp, "strided") == 0);
+    // lines per tile: 8 for the persistent kernel (four CTAs of 42 KB per SM;
+    // at 256^3 228 us against 251 us for 16 lines and 280 us for 4), 16 for
+    // the non-persistent packed kernel; PS_ZTK=8/16 overrides (comparisons)
     const char* ztk = getenv("PS_ZTK");
-    const int zsoa_tk = (ztk && atoi(ztk) == 8) ? 8 : 16;
+    const int ztk_env = ztk ? atoi(ztk) : 0;
+    const int pipe_tk = ztk_env == 16 ? 16 : 8;
+    const int zsoa_tk = ztk_env == 8 ? 8 : 16;
     const bool pipe = allow_soa && !(zp && strcmp(zp, "soa") == 0);
-    const void* f = pipe ? zpipe_kernel(L3, half, &threads, &smem) : nullptr;
+    const void* f = pipe ? zpipe_kernel(L3, half, pipe_tk, &threads, &smem) : nullptr;
     const bool persistent = f != nullptr;
     if (!f && allow_soa) f = zsoa_kernel(L3, half, zsoa_tk, &threads, &smem);
     p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;
-    const int ztile = f && !persistent ? zsoa_tk : 16;
+    const int ztile = persistent ? pipe_tk : (f ? zsoa_tk : 16);
     if (!f) f = strided_kernel(L3, 2, half, &threads, &smem);
     if (f) {
       FastArgs z = base;
       z.nl = n3;
+      z.ntk_loc = (p->c + ztile - 1) / ztile;
       z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;      // B[z][ky][kx], line along z
       z.dst_plane = ldc; z.dst_elem = (long long)L2 * ldc;
       dim3 grid((p->c + ztile - 1) / ztile, L2);

@@ -182,21 +182,28 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // input rows and its K^F octant slice into shared memory with cp.async while
 // it computes the current tile, so the global-load latency of one tile
 // overlaps the arithmetic of the previous one.
-template <int T, bool HALF>
-__global__ void __launch_bounds__(16 * T, 2)
+template <int T, bool HALF, int TK>
+__global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     k_zconv_pipe(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
                  FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
-  constexpr int TK = 16;
   constexpr int P = T, Q = 2 * T, L = P * Q;
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = NA * Q;          // input rows per line (n3)
   constexpr int KROWS = L / 2 + 1;      // rows of the K^F octant
+  // 16 lines per tile: the next tile's input rows land in a stage of their own
+  // as soon as the current ones are in registers. 8 lines per tile: they land
+  // in the exchange buffer once its last use in the tile has been read, which
+  // keeps a CTA at 42 KB of shared memory (four CTAs per SM).
+  constexpr bool SEP = TK == 16;
   extern __shared__ float4 smem4[];
   float4* sh4 = smem4;                                              // exchange [T * P][TK]
-  float2* stage = reinterpret_cast<float2*>(smem4 + T * P * TK);    // inputs [ROWS][TK]
-  float* kstage = reinterpret_cast<float*>(stage + ROWS * TK);      // K^F [KROWS][TK]
+  float2* stage = SEP ? reinterpret_cast<float2*>(smem4 + T * P * TK)  // inputs [ROWS][TK]
+                      : reinterpret_cast<float2*>(smem4);
+  float* kstage = SEP ? reinterpret_cast<float*>(stage + ROWS * TK)    // K^F [KROWS][TK]
+                      : reinterpret_cast<float*>(smem4 + T * P * TK);
   const int t = threadIdx.x % TK;
   const int j = threadIdx.x / TK;
+  auto xi = [](int r, int c) { return (r * P + c) * TK; };  // exchange slot (r, c) of line t: xi(r, c) + t
   const int ntk = a.ntk_loc;  // kx tiles a.kt0 .. a.kt0 + ntk - 1
   const int ntiles = ntk * a.L2;
   float2* const base = static_cast<float2*>(line_v);
@@ -252,19 +259,21 @@ __global__ void __launch_bounds__(16 * T, 2)
       }
     }
     __syncthreads();  // the input stage is free
-    if (next < ntiles) issue_input(next);
-    cp_async_commit();
+    if constexpr (SEP) {
+      if (next < ntiles) issue_input(next);
+      cp_async_commit();
+    }
 
     soa::dft2<P, -1, HALF>(y);
 #pragma unroll
     for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], __ldg(&tw4[j * P + k1]));
 #pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) sh4[(j * P + k1) * TK + t] = pack(y[k1]);
+    for (int k1 = 0; k1 < P; ++k1) sh4[xi(j, k1) + t] = pack(y[k1]);
     __syncthreads();
 
     c2 z[T];
 #pragma unroll
-    for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * TK + t]);
+    for (int b = 0; b < T; ++b) z[b] = unpack(sh4[xi(b, j) + t]);
     dif_all<T>(z, std::make_integer_sequence<int, T>{});
     soa::dft2<T, -1, false>(z);
 
@@ -290,11 +299,16 @@ __global__ void __launch_bounds__(16 * T, 2)
     if (next < ntiles) issue_k(next);
     cp_async_commit();
 #pragma unroll
-    for (int b = 0; b < T; ++b) sh4[(b * P + j) * TK + t] = pack(z[b]);
+    for (int b = 0; b < T; ++b) sh4[xi(b, j) + t] = pack(z[b]);
     __syncthreads();
 
 #pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * TK + t]);
+    for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[xi(j, k1) + t]);
+    if constexpr (!SEP) {
+      __syncthreads();  // the exchange has been read: the next tile's rows may land in it
+      if (next < ntiles) issue_input(next);
+      cp_async_commit();
+    }
     soa::dft2<P, 1, false>(y);
     if (valid) {
       float2* p0 = line + (long long)j * es;
@@ -313,17 +327,25 @@ __global__ void __launch_bounds__(16 * T, 2)
   if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
 }
 
-const void* zpipe_kernel(int L, bool half, int* threads, size_t* smem) {
+const void* zpipe_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
   const void* fn = nullptr;
   int T = 0;
+  if (tk != 8 && tk != 16) return nullptr;
   switch (L) {
-    case 512: fn = half ? (const void*)k_zconv_pipe<16, true> : (const void*)k_zconv_pipe<16, false>; T = 16; break;
+    case 512:
+      if (tk == 16)
+        fn = half ? (const void*)k_zconv_pipe<16, true, 16> : (const void*)k_zconv_pipe<16, false, 16>;
+      else
+        fn = half ? (const void*)k_zconv_pipe<16, true, 8> : (const void*)k_zconv_pipe<16, false, 8>;
+      T = 16;
+      break;
     default: return nullptr;
   }
   const int NA = half ? T / 2 : T;
-  *threads = 16 * T;
-  *smem = (size_t)T * T * 16 * sizeof(float4) + (size_t)NA * 2 * T * 16 * sizeof(float2) +
-          (size_t)(T * T + 1) * 16 * sizeof(float);
+  *threads = tk * T;
+  // exchange, input stage (16 lines only; 8 lines reuse the exchange), K^F slice
+  *smem = (size_t)T * T * tk * sizeof(float4) + (tk == 16 ? (size_t)NA * 2 * T * tk * sizeof(float2) : 0) +
+          (size_t)(T * T + 1) * tk * sizeof(float);
   return fn;
 }
 

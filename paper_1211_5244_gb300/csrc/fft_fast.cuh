@@ -46,7 +46,8 @@ const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem);
 const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem);
 
 // The persistent, prefetching packed z-pass kernel (L3 = 512), or nullptr.
-const void* zpipe_kernel(int L, bool half, int* threads, size_t* smem);
+// tk lines per tile (8 or 16).
+const void* zpipe_kernel(int L, bool half, int tk, int* threads, size_t* smem);
 
 // The tensor-core z-pass kernel (L3 = 512; half: n3 = 256, else n3 = 512),
 // its table size in floats and the host fill of that table.
