@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
                                   kTK * (P < Q ? P : Q) <= 256 ? (KIND == 2 ? 2 : 3) : 1)
     k_strided(const void* src_v, void* dst_v, const float* __restrict__ K, const float2* __restrict__ tw,
               FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
+  pdl_wait();
   constexpr int L = P * Q;
   constexpr int T = P < Q ? P : Q;
   constexpr int NB = Q / T;            // step-1 transforms per thread
@@ -207,6 +208,7 @@ template <int P, int Q, int KIND, bool HALF>
 __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
     k_ypipe(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a, double*,
             unsigned*, double, double*) {
+  pdl_wait();
   constexpr int L = P * Q;
   constexpr int T = P < Q ? P : Q;
   constexpr int NB = Q / T;

@@ -42,6 +42,7 @@ template <int P, int Q, int TR, bool HALF>
 __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     k_x_r2c(const void* src_v, void* dst_v, const float* twm_v, const float2* __restrict__ tw, FastArgs a,
             double*, unsigned*, double, double*) {
+  pdl_wait();
   // twm: the matrix W_M^{r c} (r, c < P), laid out so lanes read consecutive entries
   const float2* __restrict__ twm = reinterpret_cast<const float2*>(twm_v);
   using S = XShape<P, Q>;
@@ -108,6 +109,7 @@ template <int P, int Q, int TR, bool HALF>
 __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     k_x_c2r(const void* src_v, void* dst_v, const float* twm_v, const float2* __restrict__ tw, FastArgs a,
             double*, unsigned*, double, double*) {
+  pdl_wait();
   const float2* __restrict__ twm = reinterpret_cast<const float2*>(twm_v);
   using S = XShape<P, Q>;
   constexpr int M = S::M, T = S::T, NB = Q / T, NK = P / T;
@@ -405,7 +407,23 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
   unsigned* counter = p->counter;
   void* args[] = {(void*)&src, (void*)&dst, (void*)&K, (void*)&tw, (void*)&cf.fa,
                   (void*)&partials, (void*)&counter, (void*)&escale, (void*)&E};
-  return cudaLaunchKernel(cf.fn, cf.grid, cf.block, args, cf.smem, s);
+  // programmatic dependent launch: the kernel may start while the previous one
+  // in the stream drains (it waits for it before touching memory); PS_PDL=0 off
+  static const bool pdl = [] {
+    const char* v = getenv("PS_PDL");
+    return !(v && atoi(v) == 0);
+  }();
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = cf.grid;
+  lc.blockDim = cf.block;
+  lc.dynamicSmemBytes = cf.smem;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelExC(&lc, cf.fn, args);
 }
 
 }  // namespace ps

@@ -65,6 +65,7 @@ template <int T, bool HALF, int kTKs>
 __global__ void __launch_bounds__(kTKs * T, 512 / (kTKs * T))
     k_zconv_soa(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
                 FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
+  pdl_wait();
   constexpr int P = T, Q = 2 * T, L = P * Q;
   constexpr int NA = HALF ? P / 2 : P;
   extern __shared__ float4 sh4[];  // [T * P][kTKs]: slot (r, c) of line t at (r * P + c) * kTKs + t
@@ -186,6 +187,7 @@ template <int T, bool HALF, int TK>
 __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     k_zconv_pipe(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
                  FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
+  pdl_wait();
   constexpr int P = T, Q = 2 * T, L = P * Q;
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = NA * Q;          // input rows per line (n3)
@@ -359,6 +361,7 @@ template <int KIND, bool HALF>
 __global__ void __launch_bounds__(256, 2)
     k_ysoa_pipe(const void* src_v, void* dst_v, const float*, const float4* __restrict__ tw4, FastArgs a,
                 double*, unsigned*, double, double*) {
+  pdl_wait();
   constexpr int T = 16, TK = 16, P = T, Q = 2 * T, L = P * Q;
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = KIND == 0 ? NA * Q : L;

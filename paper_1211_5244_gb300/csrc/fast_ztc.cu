@@ -187,6 +187,7 @@ template <int NZ>
 __global__ void __launch_bounds__(256, NZ == 8 ? 2 : 1)
     k_ztc(const void*, void* line_v, const float* __restrict__ K, const float2* __restrict__ tab, FastArgs a,
           double* partials, unsigned* counter, double escale, double* E) {
+  pdl_wait();
   using Lay = TcLayout<NZ>;
   constexpr int TK = kTcLines, ROWS = Lay::ROWS;
   extern __shared__ __align__(1024) unsigned char smem[];

@@ -21,6 +21,12 @@ __device__ __forceinline__ int paired_ky(int y, int L2) {
   return (y & 1) ? p : L2 - p;
 }
 
+// Every specialised kernel starts with this wait: it is launched with
+// programmatic stream serialisation, so its CTAs may start while the previous
+// kernel of the stream finishes; the wait returns once that kernel has
+// completed and its writes are visible (immediately for an ordinary launch).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Kernel signature shared by every specialised pass kernel.
 //   src, dst   pass input / output (A, B, rho or V)
 //   K          K^F octant (z pass only)
