@@ -28,14 +28,19 @@ __device__ __forceinline__ float2 xmulc(float2 a, float2 b) {
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// shared memory per row: the exchange tile P x (Q + 1) and the row spectrum
-// (M + 1) share one region (a barrier separates their uses)
+// shared memory per row: the exchange tile P x QP and the row spectrum (M + 1)
+// share one region (a barrier separates their uses). The row pitch QP = Q + 2
+// is even, so every exchange row starts on 16 bytes and a thread moves its Q
+// contiguous values as Q/2 128-bit accesses; a quarter-warp of them (8 rows,
+// 16 (Q + 2) bytes apart) falls on 8 different bank groups.
 template <int P, int Q>
 struct XShape {
   static constexpr int M = P * Q;
   static constexpr int T = P < Q ? P : Q;
-  static constexpr int EX = P * (Q + 1);
+  static constexpr int QP = Q + 2;
+  static constexpr int EX = P * QP;
   static constexpr int ROW = EX > M + 1 ? EX : M + 1;
+  static_assert(EX > M + 1 && EX % 2 == 0, "the exchange region must be even and hold the row spectrum");
 };
 
 template <int P, int Q, int TR, bool HALF>
@@ -48,7 +53,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   using S = XShape<P, Q>;
   constexpr int M = S::M, T = S::T, NB = Q / T, NK = P / T;
   constexpr int NA = HALF ? P / 2 : P;
-  extern __shared__ float2 sh[];
+  extern __shared__ __align__(16) float2 sh[];
   const int r = threadIdx.x / T, j = threadIdx.x % T;
   const int row = blockIdx.x * TR + r;
   const bool valid = row < a.nrows;
@@ -70,14 +75,19 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
 #pragma unroll
     for (int k1 = 1; k1 < P; ++k1) y[k1] = xmul(y[k1], __ldg(&twm[k1 * P + b]));  // W_M^{b k1}
 #pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) ex[k1 * (Q + 1) + b] = y[k1];
+    for (int k1 = 0; k1 < P; ++k1) ex[k1 * S::QP + b] = y[k1];
   }
   __syncthreads();
   float2 x[NK][Q];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
+    const float4* r4 = reinterpret_cast<const float4*>(ex + (j + T * v) * S::QP);
 #pragma unroll
-    for (int b = 0; b < Q; ++b) x[v][b] = ex[(j + T * v) * (Q + 1) + b];
+    for (int b2 = 0; b2 < Q / 2; ++b2) {
+      const float4 q4 = r4[b2];
+      x[v][2 * b2] = make_float2(q4.x, q4.y);
+      x[v][2 * b2 + 1] = make_float2(q4.z, q4.w);
+    }
   }
   __syncthreads();  // the exchange has been read: its space takes the row spectrum
 #pragma unroll
@@ -114,7 +124,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   using S = XShape<P, Q>;
   constexpr int M = S::M, T = S::T, NB = Q / T, NK = P / T;
   constexpr int NA = HALF ? P / 2 : P;
-  extern __shared__ float2 sh[];
+  extern __shared__ __align__(16) float2 sh[];
   const int r = threadIdx.x / T, j = threadIdx.x % T;
   const int row = blockIdx.x * TR + r;
   const bool valid = row < a.nrows;
@@ -154,8 +164,10 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     rdft<Q, 1, false>(x[v]);
 #pragma unroll
     for (int b = 1; b < Q; ++b) x[v][b] = xmulc(x[v][b], __ldg(&twm[b * P + k1]));
+    float4* w4 = reinterpret_cast<float4*>(ex + k1 * S::QP);
 #pragma unroll
-    for (int b = 0; b < Q; ++b) ex[k1 * (Q + 1) + b] = x[v][b];
+    for (int b2 = 0; b2 < Q / 2; ++b2)
+      w4[b2] = make_float4(x[v][2 * b2].x, x[v][2 * b2].y, x[v][2 * b2 + 1].x, x[v][2 * b2 + 1].y);
   }
   __syncthreads();
 #pragma unroll
@@ -163,7 +175,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     const int b = j + T * u;
     float2 y[P];
 #pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) y[k1] = ex[k1 * (Q + 1) + b];
+    for (int k1 = 0; k1 < P; ++k1) y[k1] = ex[k1 * S::QP + b];
     rdft<P, 1, false>(y);
     if (valid) {
 #pragma unroll
