@@ -115,7 +115,7 @@ struct ps_plan_s {
   void* tw4y;    // paired y twiddles of the packed y kernels (16*16 float4), or NULL
   void* twx;     // x passes: W_M^{r c}, r, c < xP (float2, M = L1/2), or NULL
   int xP;        // size of twx (the larger step of the x-pass factorisation)
-  int ysoa;      // 1 if the packed y kernels run (L2 = 512)
+  int ysoa;      // packed y kernels (L2 = 512): bit 0 forward, bit 1 inverse
   int zsoa_T;    // T of the packed z kernel (L3 = 2 T^2), 0 if not used
   void* tctab;   // tensor-core z pass: DFT matrices (hi, lo) and twiddles, or NULL
   size_t tctab_floats;

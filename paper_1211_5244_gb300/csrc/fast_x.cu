@@ -267,24 +267,28 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   // y passes: n2 <= L2/2 (zero padding) or n2 = L2 (periodic)
   if (pow2(L2) && (n2 <= L2 / 2 || n2 == L2)) {
     const bool half = n2 <= L2 / 2;
-    int threads;
+    int threads0 = 0, threads1 = 0;
     size_t smem0 = 0, smem1 = 0;  // the forward and inverse kernels may differ
-    // the persistent prefetching kernels where they exist (PS_YPASS=plain keeps
-    // the non-persistent ones)
+    // persistent prefetching kernels where they exist; the forward pass takes
+    // the packed FP32x2 kernel (L2 = 512 at n2 = L2/2 or L2: 80 us against
+    // 83 us at 256^3), the inverse the unpacked one (80 us against 81 us).
+    // PS_YPASS=soa: packed for both; PS_YPASS=pipe: unpacked for both;
+    // PS_YPASS=plain: the non-persistent kernels
     const char* yp = getenv("PS_YPASS");
-    const bool ypipe = !(yp && strcmp(yp, "plain") == 0);
-    const bool ysoa = yp && strcmp(yp, "soa") == 0 && (2 * n2 == L2 || n2 == L2);
-    const void* f0 = ysoa ? ysoa_kernel(L2, 0, half, &threads, &smem0) : nullptr;
-    const void* f1 = ysoa ? ysoa_kernel(L2, 1, half, &threads, &smem1) : nullptr;
-    p->ysoa = (f0 && f1) ? 1 : 0;
-    if (!p->ysoa) {
-      f0 = ypipe ? ypipe_kernel(L2, 0, half, &threads, &smem0) : nullptr;
-      f1 = ypipe ? ypipe_kernel(L2, 1, half, &threads, &smem1) : nullptr;
-    }
+    const bool plain = yp && strcmp(yp, "plain") == 0;
+    const bool exact = 2 * n2 == L2 || n2 == L2;
+    const bool soa0 = !plain && exact && !(yp && strcmp(yp, "pipe") == 0);
+    const bool soa1 = exact && yp && strcmp(yp, "soa") == 0;
+    const void* f0 = soa0 ? ysoa_kernel(L2, 0, half, &threads0, &smem0) : nullptr;
+    const void* f1 = soa1 ? ysoa_kernel(L2, 1, half, &threads1, &smem1) : nullptr;
+    p->ysoa = (f0 ? 1 : 0) | (f1 ? 2 : 0);
+    if (!f0 && !plain) f0 = ypipe_kernel(L2, 0, half, &threads0, &smem0);
+    if (!f1 && !plain) f1 = ypipe_kernel(L2, 1, half, &threads1, &smem1);
     const bool ypersist = f0 && f1;
     if (!ypersist) {
-      f0 = strided_kernel(L2, 0, half, &threads, &smem0);
-      f1 = strided_kernel(L2, 1, half, &threads, &smem1);
+      p->ysoa = 0;
+      f0 = strided_kernel(L2, 0, half, &threads0, &smem0);
+      f1 = strided_kernel(L2, 1, half, &threads1, &smem1);
     }
     if (f0 && f1) {
       FastArgs fwd = base, inv = base;
@@ -300,7 +304,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         const long long tiles = (long long)ntk * n3;
-        auto persistent_grid = [&](const void* f, size_t smem, dim3* grid) -> cudaError_t {
+        auto persistent_grid = [&](const void* f, int threads, size_t smem, dim3* grid) -> cudaError_t {
           cudaError_t err = cudaSuccess;
           if (smem > 48 * 1024 &&
               (err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -312,11 +316,11 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
           *grid = dim3((unsigned)(g < tiles ? g : tiles), 1);
           return cudaSuccess;
         };
-        if ((e = persistent_grid(f0, smem0, &grid0)) != cudaSuccess) return e;
-        if ((e = persistent_grid(f1, smem1, &grid1)) != cudaSuccess) return e;
+        if ((e = persistent_grid(f0, threads0, smem0, &grid0)) != cudaSuccess) return e;
+        if ((e = persistent_grid(f1, threads1, smem1, &grid1)) != cudaSuccess) return e;
       }
-      if ((e = set(P2, f0, grid0, threads, smem0, fwd)) != cudaSuccess) return e;
-      if ((e = set(P4, f1, grid1, threads, smem1, inv)) != cudaSuccess) return e;
+      if ((e = set(P2, f0, grid0, threads0, smem0, fwd)) != cudaSuccess) return e;
+      if ((e = set(P4, f1, grid1, threads1, smem1, inv)) != cudaSuccess) return e;
     }
   }
   // z pass on the tensor cores (PS_MATH_TF32X3, L3 = 512): persistent, one
@@ -414,7 +418,7 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
   const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
   const void* tw = (pass == P3 && p->tctab) ? p->tctab
                    : (pass == P3 && p->zsoa_T) ? p->tw4z
-                   : ((pass == P2 || pass == P4) && p->ysoa) ? p->tw4y : p->tw[axis];
+                   : ((pass == P2 && (p->ysoa & 1)) || (pass == P4 && (p->ysoa & 2))) ? p->tw4y : p->tw[axis];
   double* partials = p->partials;
   unsigned* counter = p->counter;
   void* args[] = {(void*)&src, (void*)&dst, (void*)&K, (void*)&tw, (void*)&cf.fa,
