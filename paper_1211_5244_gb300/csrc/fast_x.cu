@@ -44,7 +44,7 @@ struct XShape {
 };
 
 template <int P, int Q, int TR, bool HALF>
-__global__ void __launch_bounds__(TR*(P < Q ? P : Q))
+__global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
     k_x_r2c(const void* src_v, void* dst_v, const float* twm_v, const float2* __restrict__ tw, FastArgs a,
             double*, unsigned*, double, double*) {
   pdl_wait();
@@ -89,6 +89,29 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
       x[v][2 * b2 + 1] = make_float2(q4.z, q4.w);
     }
   }
+  if constexpr (P == Q) {
+    // P = Q = T: thread j holds Z[k] for k = j + P k2, and Z[M - k] sits in
+    // lane (P - j) mod P of the same row at index Q - 1 - k2 (k2' = (Q - k2) mod Q
+    // in the thread's own registers for j = 0), so the pairs meet by shuffles
+    rdft<Q, -1, false>(x[0]);
+    const int jp = (P - j) & (P - 1);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const float2 sv = x[0][Q - 1 - k2];
+      const float2 tv = make_float2(__shfl_sync(0xffffffffu, sv.x, jp, T), __shfl_sync(0xffffffffu, sv.y, jp, T));
+      const float2 zm = j == 0 ? x[0][(Q - k2) & (Q - 1)] : tv;
+      const float2 zk = x[0][k2];
+      const int k = j + P * k2;
+      const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      const float2 wo = xmul(o, __ldg(&tw[k]));
+      if (valid) {
+        X[k] = make_float2(e.x + wo.x, e.y + wo.y);
+        if (k == 0) X[M] = make_float2(e.x - wo.x, wo.y - e.y);  // X[M] = conj(E[0] - O[0])
+      }
+    }
+    return;
+  }
   __syncthreads();  // the exchange has been read: its space takes the row spectrum
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
@@ -116,7 +139,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
 }
 
 template <int P, int Q, int TR, bool HALF>
-__global__ void __launch_bounds__(TR*(P < Q ? P : Q))
+__global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
     k_x_c2r(const void* src_v, void* dst_v, const float* twm_v, const float2* __restrict__ tw, FastArgs a,
             double*, unsigned*, double, double*) {
   pdl_wait();
@@ -133,6 +156,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
   const float2* X = static_cast<const float2*>(src_v) + (long long)row * a.ldc;
   float2* z = reinterpret_cast<float2*>(static_cast<float*>(dst_v) + (long long)row * a.n1);
 
+  float2 x[NK][Q];
   {
     // all loads of the row first (independent, in flight together), then the stores to shared memory
     float2 xin[M / T];
@@ -144,7 +168,6 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     if (j == 0) xr[M] = xny;
   }
   __syncthreads();
-  float2 x[NK][Q];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
     const int k1 = j + T * v;
@@ -158,6 +181,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q))
     }
   }
   __syncthreads();  // the row spectrum has been read: its space takes the exchange
+
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
     const int k1 = j + T * v;
