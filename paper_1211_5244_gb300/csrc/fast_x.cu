@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
   }
 }
 
-template <int P, int Q, int TR, bool HALF>
-__global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
+template <int P, int Q, int TR, bool HALF, bool SH = false>
+__global__ void __launch_bounds__(TR*(P < Q ? P : Q), SH ? 3 : 4)
     k_x_c2r(const void* src_v, void* dst_v, const float* twm_v, const float2* __restrict__ tw, FastArgs a,
             double*, unsigned*, double, double*) {
   pdl_wait();
@@ -157,6 +157,27 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
   float2* z = reinterpret_cast<float2*>(static_cast<float*>(dst_v) + (long long)row * a.n1);
 
   float2 x[NK][Q];
+  if constexpr (SH && P == Q) {
+    // P = Q = T: thread j loads X[k] for k = j + P k2 (the k of its first
+    // transform); X[M - k] comes from lane (P - j) mod P (index Q - 1 - k2), or
+    // from its own registers for j = 0
+    float2 xin[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) xin[i] = valid ? X[j + P * i] : make_float2(0.f, 0.f);
+    const float2 xny = (valid && j == 0) ? X[M] : make_float2(0.f, 0.f);
+    const int jp = (P - j) & (P - 1);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const float2 sv = xin[Q - 1 - k2];
+      const float2 tv = make_float2(__shfl_sync(0xffffffffu, sv.x, jp, T), __shfl_sync(0xffffffffu, sv.y, jp, T));
+      const float2 xm = j != 0 ? tv : (k2 == 0 ? xny : xin[(Q - k2) & (Q - 1)]);
+      const float2 xk = xin[k2];
+      const int k = j + P * k2;
+      const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
+      const float2 o = xmulc(make_float2(xk.x - xm.x, xk.y + xm.y), __ldg(&tw[k]));
+      x[0][k2] = make_float2(e.x - o.y, e.y + o.x);
+    }
+  } else {
   {
     // all loads of the row first (independent, in flight together), then the stores to shared memory
     float2 xin[M / T];
@@ -181,6 +202,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
     }
   }
   __syncthreads();  // the row spectrum has been read: its space takes the exchange
+  }
 
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
@@ -212,6 +234,11 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
 template <int P, int Q, int TR>
 static const void* pick_x(int kind, bool half) {
   if (kind == 0) return half ? (const void*)k_x_r2c<P, Q, TR, true> : (const void*)k_x_r2c<P, Q, TR, false>;
+  // P = Q: the untangling by shuffles (three CTAs per SM; 44.4 against 45.7 us
+  // at 256^3); PS_XC2R=smem keeps the shared-memory form
+  const char* v = getenv("PS_XC2R");
+  if (P == Q && !(v && strcmp(v, "smem") == 0))
+    return half ? (const void*)k_x_c2r<P, Q, TR, true, true> : (const void*)k_x_c2r<P, Q, TR, false, true>;
   return half ? (const void*)k_x_c2r<P, Q, TR, true> : (const void*)k_x_c2r<P, Q, TR, false>;
 }
 
