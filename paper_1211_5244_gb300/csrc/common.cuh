@@ -77,6 +77,8 @@ struct FastArgs {
   int kt0, ntk_loc;       // persistent y/z kernels: first kx tile and number of kx tiles walked
   int nl;                 // y/z passes: physical points along the line (n2 or n3); rows at and
                           // beyond nl are zero on input and not stored on output
+  int rev;                // walk the z planes (y passes) or rows (x passes) from the last one:
+                          // the previous pass wrote them last, so they are still in L2
 };
 
 struct PassCfg {

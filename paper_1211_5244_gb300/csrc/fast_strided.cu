@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
   const int j = threadIdx.x / kTK;
   const int kx = blockIdx.x * kTK + t;
   const bool valid = kx < a.c;
-  const int yblk = KIND == 2 ? paired_ky(blockIdx.y, a.L2) : (int)blockIdx.y;
+  const int yblk = KIND == 2 ? paired_ky(blockIdx.y, a.L2)
+                             : (a.rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y);
   const float2* s = src + yblk * a.src_plane + kx;
   float2* d = dst + yblk * a.dst_plane + kx;
   float2 X[NK][Q];  // X[v][k2] = spectrum at k1 + P k2, k1 = j + T v
@@ -225,7 +226,8 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
 
   auto prefetch = [&](int tile) {
     const int kx0 = (a.kt0 + tile % ntk) * kTK;
-    const float2* sp = src + (long long)(tile / ntk) * a.src_plane + kx0;
+    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
+    const float2* sp = src + (long long)zp * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (kTK / 2); q += blockDim.x) {
       const int row = q / (kTK / 2), part = q % (kTK / 2);
       if (KIND == 1 || row < a.nl)
@@ -242,7 +244,8 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
     const int next = tile + gridDim.x;
     const int kx = (a.kt0 + tile % ntk) * kTK + t;
     const bool valid = kx < a.c;
-    float2* d = dst + (long long)(tile / ntk) * a.dst_plane + kx;
+    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
+    float2* d = dst + (long long)zp * a.dst_plane + kx;
     cpa_wait_all();
     __syncthreads();  // the tile's rows have landed
     float2 X[NK][Q];

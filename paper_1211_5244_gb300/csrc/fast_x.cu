@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
   constexpr int NA = HALF ? P / 2 : P;
   extern __shared__ __align__(16) float2 sh[];
   const int r = threadIdx.x / T, j = threadIdx.x % T;
-  const int row = blockIdx.x * TR + r;
+  const int row = (a.rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * TR + r;
   const bool valid = row < a.nrows;
   float2* ex = sh + r * S::ROW;
   float2* zr = ex;  // reused for the row spectrum once the exchange has been read
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), SH ? 3 : 4)
   constexpr int NA = HALF ? P / 2 : P;
   extern __shared__ __align__(16) float2 sh[];
   const int r = threadIdx.x / T, j = threadIdx.x % T;
-  const int row = blockIdx.x * TR + r;
+  const int row = (a.rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * TR + r;
   const bool valid = row < a.nrows;
   float2* ex = sh + r * S::ROW;
   float2* xr = ex;  // the row spectrum first, the exchange tile after a barrier
@@ -284,6 +284,9 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     return cudaSuccess;
   };
   FastArgs base{};
+  // passes that read what the previous pass wrote last first (PS_L2ORDER=0: off)
+  const char* l2o = getenv("PS_L2ORDER");
+  const int l2order = (l2o && atoi(l2o) == 0) ? 0 : 1;
   base.c = p->c;
   base.L1 = L1;
   base.L2 = L2;
@@ -310,8 +313,10 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     if (f0 && f1) {
       p->xP = M == 32 ? 8 : (M == 64 ? 8 : (M == 128 ? 16 : (M == 256 ? 16 : 32)));
       dim3 grid((n2 * n3 + rows - 1) / rows);
+      FastArgs xinv = base;
+      xinv.rev = l2order;  // the inverse y pass wrote the last z planes last
       if ((e = set(P1, f0, grid, threads, smem, base)) != cudaSuccess) return e;
-      if ((e = set(P5, f1, grid, threads, smem, base)) != cudaSuccess) return e;
+      if ((e = set(P5, f1, grid, threads, smem, xinv)) != cudaSuccess) return e;
     }
   }
   // y passes
@@ -344,6 +349,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     if (f0 && f1) {
       FastArgs fwd = base, inv = base;
       fwd.nl = inv.nl = n2;
+      fwd.rev = l2order;  // the x pass wrote the last z planes last
       fwd.src_plane = (long long)n2 * ldc; fwd.src_elem = ldc;   // A[z][y][kx]
       fwd.dst_plane = (long long)L2 * ldc; fwd.dst_elem = ldc;   // B[z][ky][kx]
       inv.src_plane = (long long)L2 * ldc; inv.src_elem = ldc;

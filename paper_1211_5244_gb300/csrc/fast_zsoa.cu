@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(256, 2)
 
   auto prefetch = [&](int tile) {
     const int kx0 = (a.kt0 + tile % ntk) * TK;
-    const float2* sp = src + (long long)(tile / ntk) * a.src_plane + kx0;
+    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
+    const float2* sp = src + (long long)zp * a.src_plane + kx0;
     for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
       const int row = q / (TK / 2), part = q % (TK / 2);
       cp_async16(stage + row * TK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
@@ -391,7 +392,8 @@ __global__ void __launch_bounds__(256, 2)
     const int next = tile + gridDim.x;
     const int kx = (a.kt0 + tile % ntk) * TK + t;
     const bool valid = kx < a.c;
-    float2* d = dst + (long long)(tile / ntk) * a.dst_plane + kx;
+    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
+    float2* d = dst + (long long)zp * a.dst_plane + kx;
     const long long de = a.dst_elem;
     cp_async_wait_all();
     __syncthreads();
