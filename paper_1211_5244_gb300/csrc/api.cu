@@ -310,6 +310,11 @@ int ps_kernel_build(ps_plan p, void* stream) {
   }
   p->ws_bytes = total;
   e = cudaMemsetAsync(p->counter, 0, 2 * sizeof(unsigned), s);
+  // the row padding of the work arrays (kx from c to the pitch) is read by the
+  // tile copies of the y and z passes but never written: zero it once, so that
+  // it holds finite values (the z pass multiplies it by K^F = 0 in the energy)
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->A, 0, szA, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->B, 0, szB, s);
   std::vector<float> tctab_host;
   if (e == cudaSuccess && p->tctab) {
     tctab_host.resize(p->tctab_floats);

@@ -187,7 +187,6 @@ template <int T, bool HALF, int TK>
 __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     k_zconv_pipe(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
                  FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
-  pdl_wait();
   constexpr int P = T, Q = 2 * T, L = P * Q;
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = NA * Q;          // input rows per line (n3)
@@ -236,10 +235,11 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
 
   float eacc = 0.f;
   int tile = blockIdx.x;
-  if (tile < ntiles) {
-    issue_input(tile);
-    issue_k(tile);
-  }
+  // the first K^F slice does not depend on the previous pass: its copy starts
+  // before the wait for that pass (programmatic dependent launch)
+  if (tile < ntiles) issue_k(tile);
+  pdl_wait();
+  if (tile < ntiles) issue_input(tile);
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
