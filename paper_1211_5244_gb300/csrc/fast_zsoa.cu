@@ -202,6 +202,14 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
                       : reinterpret_cast<float2*>(smem4);
   float* kstage = SEP ? reinterpret_cast<float*>(stage + ROWS * TK)    // K^F [KROWS][TK]
                       : reinterpret_cast<float*>(smem4 + T * P * TK);
+  // 8 lines per tile: the paired twiddle table also sits in shared memory,
+  // rows padded to P + 1 so that the 4 rows a warp reads at once fall on
+  // different banks (16 lines per tile read it through L1)
+  float4* tws = reinterpret_cast<float4*>(kstage + KROWS * TK);
+  if constexpr (!SEP) {
+    for (int i = threadIdx.x; i < T * P; i += blockDim.x) tws[(i / P) * (P + 1) + i % P] = __ldg(&tw4[i]);
+  }
+  auto twid = [&](int r, int c) { return SEP ? __ldg(&tw4[r * P + c]) : tws[r * (P + 1) + c]; };
   const int t = threadIdx.x % TK;
   const int j = threadIdx.x / TK;
   auto xi = [](int r, int c) { return (r * P + c) * TK; };  // exchange slot (r, c) of line t: xi(r, c) + t
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
 
     soa::dft2<P, -1, HALF>(y);
 #pragma unroll
-    for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], __ldg(&tw4[j * P + k1]));
+    for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], twid(j, k1));
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) sh4[xi(j, k1) + t] = pack(y[k1]);
     __syncthreads();
@@ -296,7 +304,7 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     soa::dft2<T, 1, false>(z);
     dit_all<T>(z, std::make_integer_sequence<int, T>{});
 #pragma unroll
-    for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], __ldg(&tw4[b * P + j]));
+    for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], twid(b, j));
     __syncthreads();  // the forward exchange and the K^F stage have been read
     if (next < ntiles) issue_k(next);
     cp_async_commit();
@@ -345,9 +353,10 @@ const void* zpipe_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
   }
   const int NA = half ? T / 2 : T;
   *threads = tk * T;
-  // exchange, input stage (16 lines only; 8 lines reuse the exchange), K^F slice
+  // exchange, input stage (16 lines only; 8 lines reuse the exchange), K^F
+  // slice, twiddle table (8 lines only)
   *smem = (size_t)T * T * tk * sizeof(float4) + (tk == 16 ? (size_t)NA * 2 * T * tk * sizeof(float2) : 0) +
-          (size_t)(T * T + 1) * tk * sizeof(float);
+          (size_t)(T * T + 1) * tk * sizeof(float) + (tk == 8 ? (size_t)T * (T + 1) * sizeof(float4) : 0);
   return fn;
 }
 
