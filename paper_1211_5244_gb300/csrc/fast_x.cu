@@ -325,16 +325,16 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const bool half = n2 <= L2 / 2;
     int threads0 = 0, threads1 = 0;
     size_t smem0 = 0, smem1 = 0;  // the forward and inverse kernels may differ
-    // persistent prefetching kernels where they exist; the forward pass takes
-    // the packed FP32x2 kernel (L2 = 512 at n2 = L2/2 or L2: 80 us against
-    // 83 us at 256^3), the inverse the unpacked one (80 us against 81 us).
-    // PS_YPASS=soa: packed for both; PS_YPASS=pipe: unpacked for both;
-    // PS_YPASS=plain: the non-persistent kernels
+    // persistent prefetching kernels where they exist: the packed FP32x2 ones
+    // at L2 = 512 (n2 = L2/2 or L2; at 256^3 forward 76.5 against 83 us for
+    // the unpacked kernel, inverse 79.9 against 80.2 us), the unpacked ones at
+    // L2 = 256 and counts below L2/2. PS_YPASS=pipe: unpacked for both
+    // directions; PS_YPASS=plain: the non-persistent kernels
     const char* yp = getenv("PS_YPASS");
     const bool plain = yp && strcmp(yp, "plain") == 0;
     const bool exact = 2 * n2 == L2 || n2 == L2;
     const bool soa0 = !plain && exact && !(yp && strcmp(yp, "pipe") == 0);
-    const bool soa1 = exact && yp && strcmp(yp, "soa") == 0;
+    const bool soa1 = soa0;
     const void* f0 = soa0 ? ysoa_kernel(L2, 0, half, &threads0, &smem0) : nullptr;
     const void* f1 = soa1 ? ysoa_kernel(L2, 1, half, &threads1, &smem1) : nullptr;
     p->ysoa = (f0 ? 1 : 0) | (f1 ? 2 : 0);

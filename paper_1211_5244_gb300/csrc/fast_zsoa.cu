@@ -370,13 +370,17 @@ template <int KIND, bool HALF>
 __global__ void __launch_bounds__(256, 2)
     k_ysoa_pipe(const void* src_v, void* dst_v, const float*, const float4* __restrict__ tw4, FastArgs a,
                 double*, unsigned*, double, double*) {
-  pdl_wait();
   constexpr int T = 16, TK = 16, P = T, Q = 2 * T, L = P * Q;
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = KIND == 0 ? NA * Q : L;
   extern __shared__ float4 smem4[];
   float4* sh4 = smem4;                                  // exchange [T * P][TK] float4
   float2* stage = reinterpret_cast<float2*>(smem4);     // input rows [ROWS][TK] float2 (same space)
+  // the paired twiddle table in shared memory, rows padded to P + 1 (the two
+  // rows a warp reads at once fall on different banks)
+  float4* tws = smem4 + T * P * TK;
+  for (int i = threadIdx.x; i < T * P; i += blockDim.x) tws[(i / P) * (P + 1) + i % P] = __ldg(&tw4[i]);
+  pdl_wait();
   const float2* src = static_cast<const float2*>(src_v);
   float2* dst = static_cast<float2*>(dst_v);
   const int t = threadIdx.x % TK;
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(256, 2)
       __syncthreads();  // inputs read: the space becomes the exchange
       soa::dft2<P, -1, HALF>(y);
 #pragma unroll
-      for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], __ldg(&tw4[j * P + k1]));
+      for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], tws[j * (P + 1) + k1]);
 #pragma unroll
       for (int k1 = 0; k1 < P; ++k1) sh4[(j * P + k1) * TK + t] = pack(y[k1]);
       __syncthreads();
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(256, 2)
       soa::dft2<T, 1, false>(z);
       dit_all<T>(z, std::make_integer_sequence<int, T>{});
 #pragma unroll
-      for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], __ldg(&tw4[b * P + j]));
+      for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], tws[b * (P + 1) + j]);
 #pragma unroll
       for (int b = 0; b < T; ++b) sh4[(b * P + j) * TK + t] = pack(z[b]);
       __syncthreads();
@@ -490,7 +494,8 @@ const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem) 
   const void* fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, true> : (const void*)k_ysoa_pipe<0, false>)
                              : (half ? (const void*)k_ysoa_pipe<1, true> : (const void*)k_ysoa_pipe<1, false>);
   *threads = 256;
-  *smem = (size_t)16 * 16 * 16 * sizeof(float4);  // exchange; the input rows share it
+  *smem = (size_t)16 * 16 * 16 * sizeof(float4) + (size_t)16 * 17 * sizeof(float4);  // exchange (the input
+                                                                                      // rows share it), twiddles
   return fn;
 }
 
