@@ -178,11 +178,11 @@ __device__ __forceinline__ void cp_async16_zero(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Persistent version of k_zconv_soa (16 lines per tile): each CTA walks tiles
-// (kx tile fastest, then the paired ky rows) and copies the next tile's n3
-// input rows and its K^F octant slice into shared memory with cp.async while
-// it computes the current tile, so the global-load latency of one tile
-// overlaps the arithmetic of the previous one.
+// Persistent version of k_zconv_soa with TK lines per tile (8 by default, 16
+// for comparisons): each CTA walks tiles (kx tile fastest, then the paired ky
+// rows) and copies the next tile's n3 input rows and its K^F octant slice into
+// shared memory with cp.async while it computes the current tile, so the
+// global-load latency of one tile overlaps the arithmetic of the previous one.
 template <int T, bool HALF, int TK>
 __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     k_zconv_pipe(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
