@@ -42,7 +42,7 @@ Z_KERNEL_FILES = ("fast_zsoa.cu", "fft_soa.cuh", "fft_regs.cuh", "fft_fast.cuh",
                   "../../include/psolver.h")
 TRAFFIC = {
     ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 364009728 + 218435840, "files": Z_KERNEL_FILES,
-                                          "src": "fe2151893dae4d31"},
+                                          "src": "213c0231c8cc41d5"},
 }
 
 
