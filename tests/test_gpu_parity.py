@@ -383,3 +383,25 @@ def test_parity_long_prime_axes(torch_cuda, n, bc, dtype):
     rho = synth.random_density(n, seed=sum(n), subtract_mean=True)
     V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.2, dtype)
     _check(V, E, rho, bc, 0.2, dtype)
+
+
+# The kernel alternatives behind the environment switches (each measured
+# slower at 256^3 than the default, kept for comparisons) against the oracle.
+SWITCHES = [
+    {"PS_ZTK": "16"},                        # 16 lines per z tile, separate input stage
+    {"PS_YPASS": "pipe"},                    # unpacked persistent y kernels
+    {"PS_YPASS": "plain", "PS_ZPASS": "soa"},  # non-persistent y and z kernels
+    {"PS_ZPASS": "strided"},                 # unpacked z kernel
+    {"PS_XC2R": "smem"},                     # C2R untangling through shared memory
+    {"PS_L2ORDER": "0"},                     # every pass in forward plane order
+]
+
+
+@pytest.mark.parametrize("env", SWITCHES, ids=lambda e: ",".join(f"{k}={v}" for k, v in e.items()))
+@pytest.mark.parametrize("n,bc", [((64, 48, 256), "fff"), ((20, 17, 256), "pff"), ((30, 256, 40), "fff")])
+def test_parity_kernel_switches(torch_cuda, monkeypatch, env, n, bc):
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=17 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
+    _check(V, E, rho, bc, 0.25, "f32")
