@@ -60,10 +60,30 @@ __device__ __forceinline__ c2 twc2(c2 v) {
     // forward m = 16 and inverse m = 48 multiply by -i: (re, im) -> (im, -re)
     constexpr bool minus_i = (m == 16) == (DIR < 0);
     return minus_i ? c2{v.im, make_float2(-v.re.x, -v.re.y)} : c2{make_float2(-v.im.x, -v.im.y), v.re};
+  } else if constexpr (m == 8 || m == 24 || m == 40 || m == 56) {
+    // (cos, sin) = (+-s, +-s): sums and differences of the pair times s
+    constexpr float s = 0.70710678118654752440f;
+    constexpr float c = (float)regs::cos64(m), sn = (float)regs::sin64(m);
+    const float2 S = make_float2(s, s), NS = make_float2(-s, -s);
+    const float2 apb = add2(v.re, v.im), amb = sub2(v.re, v.im), bma = sub2(v.im, v.re);
+    if constexpr (DIR < 0) {  // (a + ib)(c - i sn)
+      if constexpr (c > 0 && sn > 0) return {mul2(apb, S), mul2(bma, S)};
+      else if constexpr (c < 0 && sn > 0) return {mul2(bma, S), mul2(apb, NS)};
+      else if constexpr (c < 0 && sn < 0) return {mul2(apb, NS), mul2(amb, S)};
+      else return {mul2(amb, S), mul2(apb, S)};
+    } else {  // (a + ib)(c + i sn)
+      if constexpr (c > 0 && sn > 0) return {mul2(amb, S), mul2(apb, S)};
+      else if constexpr (c < 0 && sn > 0) return {mul2(apb, NS), mul2(amb, S)};
+      else if constexpr (c < 0 && sn < 0) return {mul2(bma, S), mul2(apb, NS)};
+      else return {mul2(apb, S), mul2(bma, S)};
+    }
   } else {
-    const float2 a = regs::twc<N, K, DIR>(make_float2(v.re.x, v.im.x));
-    const float2 b = regs::twc<N, K, DIR>(make_float2(v.re.y, v.im.y));
-    return {make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    // both lanes at once: (a + ib)(c -+ i sn) as packed products with the
+    // constants in register pairs
+    constexpr float c = (float)regs::cos64(m), sn = (float)regs::sin64(m);
+    const float2 C = make_float2(c, c), SN = make_float2(sn, sn), NSN = make_float2(-sn, -sn);
+    if constexpr (DIR < 0) return {fma2(v.im, SN, mul2(v.re, C)), fma2(v.re, NSN, mul2(v.im, C))};
+    else return {fma2(v.im, NSN, mul2(v.re, C)), fma2(v.re, SN, mul2(v.im, C))};
   }
 }
 
