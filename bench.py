@@ -11,6 +11,15 @@ HBM roofline of the dominant kernel and of the whole solve.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+Other workloads (one JSON line each, same keys):
+    --workload free512      512^3 free FP32 (padded FFT 1024^3)
+    --workload bc128 --bc B 128^3, B in fff / pff (wire) / ppf (surface) / ppp
+    --workload hartree192   192^3 free: forward solve + adjoint backward
+                            (torch.autograd through ps_solve_vjp) per step
+    --workload localpot256  the 256^3 solve with a caller's even kernel
+    --workload batched64    64 uneven mixed-BC problems per step
+    --dtype f64             FP64 plans (reported against the FP64 ALU roof)
+
 Multi-GPU (torchrun): every rank solves its own density (replicas, weak
 scaling, no collective on the data path); rank 0 prints the JSON line.
 """
@@ -33,6 +42,10 @@ METRIC = "grid points/s per Poisson solve (free BCs, 256³) and % of HBM rooflin
 UNIT = "grid points/s"
 WORKLOAD = "free256_f32"
 FALLBACK_HBM_GBS = 6800.0
+# FP64 arithmetic roof of the GB300: 1.25 TFLOP/s dense FP64 (nominal; the
+# FP64 pipe is a small fraction of the FP32 one on this part)
+FP64_PEAK_TFLOPS = 1.25
+BC_NAMES = {"fff": "free", "pff": "wire", "ppf": "surface", "ppp": "periodic"}
 PASS_NAMES = ["p1_fwd_x_r2c", "p2_fwd_y", "p3_z_fwd_mul_inv", "p4_inv_y", "p5_inv_x_c2r"]
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
@@ -65,10 +78,31 @@ def _peak_hbm():
         return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
 
 
-def _workload_desc(w):
+def _workload_desc(w, bc="fff", dtype="f32", L=None):
     n = w["n"]
-    return (f"free-BC Poisson solve {n[0]}x{n[1]}x{n[2]} FP32 (padded FFT {2*n[0]}^3), "
-            f"{w['n_gauss']}-Gaussian density + {w['noise']:g} noise, h={w['h']}, seed {w['seed']}")
+    L = L or [2 * v if b == "f" else v for v, b in zip(n, bc)]
+    neutral = ", mean subtracted" if "p" in bc else ""
+    return (f"{BC_NAMES.get(bc, bc)}-BC ({bc}) Poisson solve {n[0]}x{n[1]}x{n[2]} {'FP32' if dtype == 'f32' else 'FP64'} "
+            f"(padded FFT {L[0]}x{L[1]}x{L[2]}), {w['n_gauss']}-Gaussian density + {w['noise']:g} noise"
+            f"{neutral}, h={w['h']}, seed {w['seed']}")
+
+
+def _pass_flops(info):
+    """Nominal FLOPs of each pass by the usual FFT benchmark count: 5 L log2 L
+    per complex line transform, 2.5 L log2 L per real one, no credit for the
+    pruned zero inputs and discarded outputs; the z pass adds its inverse
+    transforms and 2 FLOPs per point for the multiply by the real K^F."""
+    import math
+    out = []
+    for k in range(5):
+        lines, L = info.lines[k], info.line_len[k]
+        per = 5.0 * L * math.log2(max(L, 2))
+        if k in (0, 4):
+            per *= 0.5
+        if k == 2:
+            per = 2 * per + 2 * L
+        out.append(lines * per)
+    return out
 
 
 def _pass_bytes(info, esz):
@@ -133,12 +167,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _density(w, rank=0):
+def _density(w, rank=0, bc="fff", dtype="f32"):
     import numpy as np
     from paper_1211_5244_gb300 import replicas, synth
     rho = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], replicas.replica_seed(w["seed"], rank),
-                                 noise=w["noise"])
-    return rho.astype(np.float32)
+                                 noise=w["noise"], subtract_mean="p" in bc)
+    return rho.astype(np.float32 if dtype == "f32" else np.float64)
 
 
 def _localpot_octant(w):
@@ -151,27 +185,55 @@ def _localpot_octant(w):
     return np.exp(-r2 / 8.0)
 
 
-def _oracle_baseline(w, rho32, V_gpu, E_gpu, kernel=None):
+def _errors(V_gpu, Vo, E_gpu=None, Eo=None, vs="FP64 oracle, full grid"):
+    import numpy as np
+    err = {"rel_l2": float(np.linalg.norm(V_gpu - Vo) / np.linalg.norm(Vo)),
+           "rel_max": float(np.abs(V_gpu - Vo).max() / np.abs(Vo).max()), "vs": vs}
+    if E_gpu is not None:
+        err["energy_rel"] = float(abs(E_gpu - Eo) / abs(Eo))
+    return err
+
+
+def _oracle_baseline(w, bc, rho_in, V_gpu, E_gpu, kernel=None, max_full=256):
     """The FP64 oracle as it stands, timed on the host on one full solve of the
-    workload (K^F built before the timed region, like the GPU's kernel build)."""
+    workload (K^F built before the timed region, like the GPU's kernel build),
+    and the GPU result's error against it. Grids above ``max_full`` per axis
+    are too large for a full oracle solve within the bench: the oracle is then
+    timed on the same recipe at max_full^3 and the error is taken on sampled
+    points of Eq. 2 evaluated directly (free BCs)."""
     import numpy as np
     from oracle import poisson as op
-    rho = rho32.astype(np.float64)
-    KF = (op.kernel_fourier(w["n"], "fff", w["h"]) if kernel is None
-          else op.kernel_fourier_from_real(kernel, w["n"], "fff"))
+    from paper_1211_5244_gb300 import synth
+    rho = rho_in.astype(np.float64)
+    full = max(w["n"]) <= max_full
+    if full:
+        rs, ns = rho, w["n"]
+    else:
+        ns = (max_full,) * 3
+        rs = synth.gaussian_mixture(ns, w["h"], w["n_gauss"], w["seed"], noise=w["noise"],
+                                    subtract_mean="p" in bc).astype(rho_in.dtype).astype(np.float64)
+    KF = (op.kernel_fourier(ns, bc, w["h"]) if kernel is None
+          else op.kernel_fourier_from_real(kernel, ns, bc))
     t0 = time.perf_counter()
-    Vo, Eo = op.solve(rho, "fff", w["h"], KF=KF)
+    Vo, Eo = op.solve(rs, bc, w["h"], KF=KF)
     dt = time.perf_counter() - t0
-    npts = rho.size
-    err = {
-        "rel_l2": float(np.linalg.norm(V_gpu - Vo) / np.linalg.norm(Vo)),
-        "rel_max": float(np.abs(V_gpu - Vo).max() / np.abs(Vo).max()),
-        "energy_rel": float(abs(E_gpu - Eo) / abs(Eo)),
-        "vs": "FP64 oracle, full grid",
-    }
-    base = {"value": npts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full {w['n'][0]}^3 free-BC oracle solve (numpy FFT of the padded "
-                      f"{2*w['n'][0]}^3 grid, FP64, single thread), {dt:.1f} s; K^F built untimed"}
+    Ls = "x".join(str(2 * v if b == "f" else v) for v, b in zip(ns, bc))
+    base = {"value": rs.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full {ns[0]}x{ns[1]}x{ns[2]} {bc} oracle solve (numpy FFT of the padded "
+                      f"{Ls} grid, FP64, single thread), {dt:.1f} s; K^F built untimed"
+                      + ("" if full else f"; a bounded sample of the {w['n'][0]}^3 workload (same recipe)")}
+    if full:
+        return base, _errors(V_gpu, Vo, E_gpu, Eo)
+    assert bc == "fff" and kernel is None
+    n1, n2, n3 = w["n"]
+    rng = np.random.default_rng(7)
+    pts = [(n3 // 2, n2 // 2, n1 // 2), (0, 0, 0), (n3 - 1, n2 - 1, n1 - 1)]
+    pts += [tuple(int(v) for v in rng.integers(0, [n3, n2, n1])) for _ in range(3)]
+    ref = op.direct_at(rho, w["h"], pts)
+    got = np.array([V_gpu[p] for p in pts])
+    scale = np.abs(V_gpu).max()
+    err = {"rel_max_sampled": float(np.abs(got - ref).max() / scale),
+           "points": len(pts), "vs": "Eq. 2 summed directly in FP64 at sampled points (relative to max|V|)"}
     return base, err
 
 
@@ -281,6 +343,214 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def _spec(args):
+    """(workload parameters, bc, description suffix, caller's kernel) of a solve workload."""
+    from paper_1211_5244_gb300 import synth
+    if args.workload in (WORKLOAD, "localpot256"):
+        w, bc = dict(synth.WORKLOADS[WORKLOAD]), "fff"
+    elif args.workload == "free512":
+        w, bc = dict(synth.WORKLOADS["free512_f32"]), "fff"
+    elif args.workload == "hartree192":
+        w, bc = dict(synth.WORKLOADS["hartree192_f32"]), "fff"
+    else:
+        w0 = synth.WORKLOADS["bc128"]
+        if args.bc not in w0["bcs"]:
+            raise SystemExit(f"--bc must be one of {w0['bcs']}")
+        w, bc = {k: w0[k] for k in ("n", "h", "n_gauss", "noise", "seed")}, args.bc
+    kernel = _localpot_octant(w) if args.workload == "localpot256" else None
+    return w, bc, kernel
+
+
+def _timed_steps(step, K, flush, stream, sampler, dist):
+    """K steps, each after an L2 flush, with CUDA events around the step on the
+    solve stream; returns per-step ms and the clock record."""
+    import torch
+    from paper_1211_5244_gb300 import replicas
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    replicas.barrier(dist)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    replicas.barrier(dist)
+    clocks = sampler.stop()
+    return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)], clocks
+
+
+def _rooflines(info, pass_ms, dtype, workload, math_mode):
+    """The dominant kernel's roofline (HBM bytes for FP32, FP64 ALU for FP64 plans)
+    and the per-pass table."""
+    peak, peak_src = _peak_hbm()
+    esz = 4 if dtype == "f32" else 8
+    pbytes = _pass_bytes(info, esz)
+    pflops = _pass_flops(info)
+    dom = max(range(5), key=lambda k: pass_ms[k])
+    passes = {PASS_NAMES[k]: {"ms": pass_ms[k], "alg_bytes": pbytes[k],
+                              "GB/s": pbytes[k] / (pass_ms[k] / 1e3) / 1e9,
+                              "frac_hbm": pbytes[k] / (pass_ms[k] / 1e3) / 1e9 / peak,
+                              "nominal_flops": pflops[k],
+                              "TFLOP/s": pflops[k] / (pass_ms[k] / 1e3) / 1e12} for k in range(5)}
+    if dtype == "f32":
+        achieved = pbytes[dom] / (pass_ms[dom] / 1e3) / 1e9
+        tr = TRAFFIC.get((PASS_NAMES[dom], workload))
+        traffic = tr["bytes"] if (tr and math_mode == "cudacore" and tr["src"] == _src_hash(tr["files"])) else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": PASS_NAMES[dom], "alg_bytes_per_launch": pbytes[dom],
+                "peak_source": peak_src}
+    else:
+        achieved = pflops[dom] / (pass_ms[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": PASS_NAMES[dom],
+                "nominal_flops_per_launch": pflops[dom],
+                "peak_source": "nominal dense FP64 of the GB300 (1.25 TFLOP/s); FLOPs by the 5 L log2 L count",
+                "hbm_frac": pbytes[dom] / (pass_ms[dom] / 1e3) / 1e9 / peak}
+    return roof, passes
+
+
+def run_hartree(args):
+    """Differentiable Hartree energy at 192^3 free (padded 384^3 = 2^7 3 per
+    axis): each step is the forward solve (V, E) through the autograd
+    function and the backward pass with incoming gradients (Vbar, 1) on (V, E),
+    i.e. rhobar = K Vbar + h^3 V through ps_solve_vjp (an adjoint solve and the
+    energy term's axpy). Metric: grid points per second of forward + backward
+    steps."""
+    import numpy as np
+    import torch
+    from paper_1211_5244_gb300 import build as _build
+    from paper_1211_5244_gb300 import psolver, replicas, synth
+    from paper_1211_5244_gb300.autograd import hartree
+    rank, world, local = replicas.dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    w, bc, _ = _spec(args)
+    dt = args.dtype
+    rho_np = _density(w, rank, bc, dt)
+    vbar_np = _density(dict(w, seed=w["seed"] + 77), rank, bc, dt)
+    rho = torch.from_numpy(rho_np).cuda()
+    vbar = torch.from_numpy(vbar_np).cuda()
+    gE = torch.ones((), dtype=torch.float64, device="cuda")
+    # the free-axis lengths are the autotuner's choice among 2n and the smallest
+    # 2-, 2*3- and 2*3*5*7-smooth lengths >= 2n - 1 (all give the same result);
+    # --no-autotune keeps L = 2n (384 = 2^7 * 3 at n = 192)
+    plan = psolver.Plan(w["n"], bc, w["h"], dt, autotune=not args.no_autotune)
+    info = plan.info()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def step():
+        r = rho.detach().requires_grad_(True)
+        V, E = hartree(r, plan)
+        torch.autograd.backward([E, V], [gE, vbar])
+        out["V"], out["E"], out["g"] = V, E, r.grad
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    step_ms, clocks = _timed_steps(step, K, flush, stream, ClockSampler(local), dist)
+    npts = int(np.prod(w["n"]))
+    value, total_s = replicas.aggregate(sum(step_ms) / 1e3, K * npts, dist, device="cuda")
+    ms_per_step = total_s * 1e3 / K
+
+    plan.set_profiling(True)
+    plan.pass_times()
+    for _ in range(K):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    plan.set_profiling(False)
+    pass_ms, nrec = plan.pass_times()
+    pass_ms = [t / max(nrec, 1) for t in pass_ms]   # per solve (forward and adjoint alike)
+    roof, passes = _rooflines(info, pass_ms, dt, args.workload, "cudacore")
+    peak, _ = _peak_hbm()
+    esz = 4 if dt == "f32" else 8
+    step_bytes = 2 * info.alg_bytes + 3 * npts * esz      # two solves + the axpy (read 2, write 1)
+    gbs = step_bytes / (ms_per_step / 1e3) / 1e9
+
+    # end to end through the public API from pinned host memory: upload rho and
+    # Vbar, forward + backward, download V, E and the gradient
+    rho_h = torch.from_numpy(rho_np).pin_memory()
+    vbar_h = torch.from_numpy(vbar_np).pin_memory()
+    V_h = torch.empty_like(rho_h).pin_memory()
+    g_h = torch.empty_like(rho_h).pin_memory()
+    E_h = torch.empty((), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        r = rho_h.to("cuda", non_blocking=True).requires_grad_(True)
+        vb = vbar_h.to("cuda", non_blocking=True)
+        V, E = hartree(r, plan)
+        torch.autograd.backward([E, V], [gE, vb])
+        V_h.copy_(V, non_blocking=True)
+        g_h.copy_(r.grad, non_blocking=True)
+        E_h.copy_(E, non_blocking=True)
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    replicas.barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_value, _ = replicas.aggregate(time.perf_counter() - t0, K * npts, dist, device="cuda")
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * npts * esz,
+           "d2h_bytes_per_step": 2 * npts * esz + 8,
+           "api": "torch.autograd through hartree() (ps_solve + ps_solve_vjp), pinned host buffers, host wall clock"}
+
+    line = {
+        "metric": "grid points/s of a differentiable Hartree step (forward solve + adjoint backward)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dt, "data": "synthetic",
+        "config": {"workload": _workload_desc(w, bc, dt, list(info.L)) +
+                   "; step = forward (V, E) + backward with (Vbar, 1) through ps_solve_vjp",
+                   "n": list(w["n"]), "bc": bc, "h": w["h"], "L": list(info.L), "autotuned": not args.no_autotune,
+                   "blocks": list(info.blocks),
+                   "l2": "flushed (512 MiB write) before every step; per-step CUDA events",
+                   "pass_times": "separate profiled loop, per solve (forward and adjoint solves averaged)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "solve_roofline": {"alg_bytes": step_bytes, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                           "frac": gbs / peak, "per": "step (two solves + the energy term's axpy)"},
+        "passes": passes, "e2e": e2e, "gpu_launches": (2 * info.launches + 1) * K, "clocks": clocks,
+        "kernel_src": _src_hash(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import numpy as _np
+        from oracle import poisson as op
+        r64 = rho_np.astype(_np.float64)
+        vb64 = vbar_np.astype(_np.float64)
+        KF = op.kernel_fourier(w["n"], bc, w["h"])
+        t0 = time.perf_counter()
+        Vo, Eo = op.solve(r64, bc, w["h"], KF=KF)
+        KVb, _ = op.solve(vb64, bc, w["h"], KF=KF)
+        go = KVb + w["h"] ** 3 * Vo
+        tcpu = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": npts / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one full forward + backward step in the FP64 oracle (two numpy FFT "
+                                          f"solves of the padded grid and the energy term), single thread, "
+                                          f"{tcpu:.1f} s; K^F built untimed"}
+        err = _errors(out["V"].detach().double().cpu().numpy(), Vo, float(out["E"].item()), Eo)
+        gerr = _errors(out["g"].detach().double().cpu().numpy(), go)
+        err["grad_rel_l2"], err["grad_rel_max"] = gerr["rel_l2"], gerr["rel_max"]
+        line["error_vs_oracle"] = err
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,8 +558,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64", "localpot256"],
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "free512", "bc128", "hartree192", "localpot256", "batched64"],
                     help="localpot256: the 256^3 free solve with a caller's even kernel (ps_kernel_set_real)")
+    ap.add_argument("--bc", default="fff", help="boundary conditions of --workload bc128 (fff, pff, ppf, ppp)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="hartree192: padded lengths 2n instead of the autotuner's choice")
     ap.add_argument("--math", default="cudacore", choices=["cudacore", "tf32x3"],
                     help="arithmetic of the transforms (tf32x3: z pass on the tensor cores)")
     args = ap.parse_args()
@@ -300,12 +575,15 @@ def main():
     if args.workload == "batched64":
         run_batched(args)
         return
+    if args.workload == "hartree192":
+        run_hartree(args)
+        return
 
     import numpy as np
     import torch
 
     from paper_1211_5244_gb300 import build as _build
-    from paper_1211_5244_gb300 import psolver, replicas, synth
+    from paper_1211_5244_gb300 import psolver, replicas
 
     rank, world, local = replicas.dist_env()
     torch.cuda.set_device(local)
@@ -315,13 +593,13 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
 
-    w = synth.WORKLOADS[WORKLOAD]
-    rho_np = _density(w, rank)
+    w, bc, kernel = _spec(args)
+    dt = args.dtype
+    esz = 4 if dt == "f32" else 8
+    rho_np = _density(w, rank, bc, dt)
     rho = torch.from_numpy(rho_np).cuda()
-    plan = psolver.Plan(w["n"], "fff", w["h"], "f32", math=args.math)
-    kernel = None
-    if args.workload == "localpot256":
-        kernel = _localpot_octant(w)
+    plan = psolver.Plan(w["n"], bc, w["h"], dt, math=args.math)
+    if kernel is not None:
         plan.set_kernel_real(kernel)
     info = plan.info()
     V = torch.empty_like(rho)
@@ -329,32 +607,20 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    def step():
+        plan.solve(rho, V, stream=stream, E=E)
+
     for _ in range(args.warmup):
         flush.zero_()
-        plan.solve(rho, V, stream=stream, E=E)
+        step()
     torch.cuda.synchronize()
 
     # ---- timed region (device-resident inputs) ----
     K = args.steps
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    sampler = ClockSampler(local)
-    replicas.barrier(dist)
-    torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.2)
-    for i in range(K):
-        flush.zero_()
-        starts[i].record(stream)
-        plan.solve(rho, V, stream=stream, E=E)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    replicas.barrier(dist)
-    clocks = sampler.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms, clocks = _timed_steps(step, K, flush, stream, ClockSampler(local), dist)
     npts = int(np.prod(w["n"]))
     value, total_s = replicas.aggregate(sum(step_ms) / 1e3, K * npts, dist, device="cuda")
-    total_ms = total_s * 1e3
+    ms_per_step = total_s * 1e3 / K
 
     # ---- per-pass times: the same steps again with an event between passes
     # (passes serialised on the solve stream), for the per-kernel roofline
@@ -362,12 +628,11 @@ def main():
     plan.pass_times()  # forget anything recorded earlier
     for i in range(K):
         flush.zero_()
-        plan.solve(rho, V, stream=stream, E=E)
+        step()
     torch.cuda.synchronize()
     plan.set_profiling(False)
     pass_ms, nrec = plan.pass_times()
     pass_ms = [t / max(nrec, 1) for t in pass_ms]
-    ms_per_step = total_ms / K
 
     # ---- end-to-end through the host-buffer entry point (pinned memory): K
     # densities, each uploaded, solved and downloaded (with its energy), the
@@ -382,39 +647,36 @@ def main():
     torch.cuda.synchronize()
     e2e_value, _ = replicas.aggregate(time.perf_counter() - t0, K * npts, dist, device="cuda")
     e2e = {"value": e2e_value, "unit": UNIT,
-           "h2d_bytes_per_step": npts * 4, "d2h_bytes_per_step": npts * 4 + 8,
+           "h2d_bytes_per_step": npts * esz, "d2h_bytes_per_step": npts * esz + 8,
            "api": "ps_solve_host_stream (pinned host buffers, host wall clock)"}
 
     # ---- roofline ----
-    peak, peak_src = _peak_hbm()
-    pbytes = _pass_bytes(info, 4)
-    dom = max(range(5), key=lambda k: pass_ms[k])
-    achieved = pbytes[dom] / (pass_ms[dom] / 1e3) / 1e9
-    tr = TRAFFIC.get((PASS_NAMES[dom], WORKLOAD))
-    traffic = tr["bytes"] if (tr and args.math == "cudacore" and args.workload == WORKLOAD
-                              and tr["src"] == _src_hash(tr["files"])) else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": PASS_NAMES[dom], "alg_bytes_per_launch": pbytes[dom],
-            "peak_source": peak_src}
+    wl_key = WORKLOAD if (args.workload == WORKLOAD and dt == "f32") else args.workload
+    roof, passes = _rooflines(info, pass_ms, dt, wl_key, args.math)
+    peak, _ = _peak_hbm()
     solve_gbs = info.alg_bytes / (ms_per_step / 1e3) / 1e9
-    passes = {PASS_NAMES[k]: {"ms": pass_ms[k], "alg_bytes": pbytes[k],
-                              "GB/s": pbytes[k] / (pass_ms[k] / 1e3) / 1e9,
-                              "frac": pbytes[k] / (pass_ms[k] / 1e3) / 1e9 / peak} for k in range(5)}
+    n = w["n"]
+    compulsory = 2 * npts * esz + info.c * (info.L[1] // 2 + 1) * (info.L[2] // 2 + 1) * esz
 
+    desc = _workload_desc(w, bc, dt, list(info.L))
+    if kernel is not None:
+        desc += "; caller's kernel: Gaussian of width 2 steps (ps_kernel_set_real)"
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "metric": METRIC if (args.workload in (WORKLOAD, "localpot256") and dt == "f32")
+        else f"grid points/s per Poisson solve ({BC_NAMES.get(bc, bc)} BCs, {n[0]}x{n[1]}x{n[2]}, {dt.upper()})",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": _workload_desc(w) + ("; caller's kernel: Gaussian of width 2 steps (ps_kernel_set_real)"
-                                                    if kernel is not None else ""),
-                   "n": list(w["n"]), "bc": "fff", "h": w["h"],
+        "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
+        "config": {"workload": desc, "n": list(n), "bc": bc, "h": w["h"], "L": list(info.L),
                    "math": args.math, "tensor_passes": info.tensor_passes, "blocks": list(info.blocks),
                    "l2": "flushed (512 MiB write) before every step; per-step CUDA events",
                    "pass_times": "separate profiled loop of the same K steps, one event between passes",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roof,
         "solve_roofline": {"alg_bytes": info.alg_bytes, "achieved": solve_gbs, "peak": peak,
-                           "unit": "GB/s", "frac": solve_gbs / peak},
+                           "unit": "GB/s", "frac": solve_gbs / peak,
+                           "compulsory_bytes": compulsory,
+                           "compulsory_frac": compulsory / (ms_per_step / 1e3) / 1e9 / peak},
         "passes": passes,
         "e2e": e2e,
         "gpu_launches": info.launches * K,
@@ -422,7 +684,7 @@ def main():
         "kernel_src": _src_hash(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base, err = _oracle_baseline(w, rho_np, V.double().cpu().numpy(), float(E.item()), kernel)
+        base, err = _oracle_baseline(w, bc, rho_np, V.double().cpu().numpy(), float(E.item()), kernel)
         line["cpu_baseline"] = base
         line["error_vs_oracle"] = err
     if rank == 0:

@@ -218,42 +218,78 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
   float2* const base = static_cast<float2*>(line_v);
   const long long es = a.src_elem;
 
-  auto issue_input = [&](int tile) {
-    const int kx0 = (a.kt0 + tile % ntk) * TK;
-    const int ky = paired_ky(tile / ntk, a.L2);
-    const float2* src = base + ky * a.src_plane + kx0;
-    for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
-      const int row = q / (TK / 2), part = q % (TK / 2);
-      if (row < a.nl)
-        cp_async16(stage + row * TK + 2 * part, src + (long long)row * es + 2 * part);
-      else  // beyond the physical z rows: zeros
-        cp_async16_zero(stage + row * TK + 2 * part, src);
+  // Copies of a tile's rows, with trip counts fixed at compile time and the
+  // per-thread offsets computed once: the input rows (n3 rows of TK float2,
+  // 16-byte pieces) and the K^F slice (KROWS rows of TK floats).
+  constexpr int NT = TK * T;            // threads per CTA
+  constexpr int IPR = TK / 2;           // 16-byte pieces per input row
+  constexpr int ISTEP = NT / IPR;       // rows per sweep of the CTA
+  static_assert(NT % IPR == 0 && ROWS % ISTEP == 0, "input copy shape");
+  constexpr int IIT = ROWS / ISTEP;
+  const int irow0 = threadIdx.x / IPR;
+  const long long igoff = (long long)irow0 * es + 2 * (threadIdx.x % IPR);
+  const long long igstep = (long long)ISTEP * es;
+  float2* const is0 = stage + irow0 * TK + 2 * (threadIdx.x % IPR);
+  const int ivalid = a.nl - irow0;      // sweep i copies a physical row iff ISTEP * i < ivalid
+  constexpr int KPR = TK / 4;           // 16-byte pieces per K^F row
+  constexpr int KSTEP = NT / KPR;
+  static_assert(NT % KPR == 0, "K copy shape");
+  constexpr int KIT = (KROWS + KSTEP - 1) / KSTEP;
+  const int krow0 = threadIdx.x / KPR;
+  const long long kgoff = (long long)krow0 * a.kz_stride + 4 * (threadIdx.x % KPR);
+  const long long kgstep = (long long)KSTEP * a.kz_stride;
+  float* const ks0 = kstage + krow0 * TK + 4 * (threadIdx.x % KPR);
+
+  // tile = kt + ntk * yi (kx tile fastest); the CTA steps by gridDim.x tiles
+  const int dkt = gridDim.x % ntk, dyi = gridDim.x / ntk;
+  auto step_tile = [&](int& kt, int& yi) {
+    kt += dkt;
+    yi += dyi;
+    if (kt >= ntk) {
+      kt -= ntk;
+      ++yi;
     }
   };
-  auto issue_k = [&](int tile) {
-    const int kx0 = (a.kt0 + tile % ntk) * TK;
-    const int ky = paired_ky(tile / ntk, a.L2);
+
+  auto issue_input = [&](int kt, int yi) {
+    const float2* src0 = base + paired_ky(yi, a.L2) * a.src_plane + (a.kt0 + kt) * TK;
+    const float2* src = src0 + igoff;
+#pragma unroll
+    for (int i = 0; i < IIT; ++i) {
+      if (ISTEP * i < ivalid)
+        cp_async16(is0 + i * ISTEP * TK, src);
+      else  // beyond the physical z rows: zeros (nothing is read)
+        cp_async16_zero(is0 + i * ISTEP * TK, src0);
+      src += igstep;
+    }
+  };
+  auto issue_k = [&](int kt, int yi) {
+    const int ky = paired_ky(yi, a.L2);
     const int kyo = min(ky, a.L2 - ky);
-    const float* src = K + (long long)kyo * a.ldk + kx0;
-    for (int q = threadIdx.x; q < KROWS * (TK / 4); q += blockDim.x) {
-      const int row = q / (TK / 4), part = q % (TK / 4);
-      cp_async16(kstage + row * TK + 4 * part, src + (long long)row * a.kz_stride + 4 * part);
+    const float* src = K + (long long)kyo * a.ldk + (a.kt0 + kt) * TK + kgoff;
+#pragma unroll
+    for (int i = 0; i < KIT; ++i) {
+      if ((i + 1) * KSTEP <= KROWS || krow0 + i * KSTEP < KROWS) cp_async16(ks0 + i * KSTEP * TK, src);
+      src += kgstep;
     }
   };
 
   float eacc = 0.f;
   int tile = blockIdx.x;
+  int kt = tile % ntk, yi = tile / ntk;  // this tile
+  int nkt = kt, nyi = yi;                // the next one
+  step_tile(nkt, nyi);
   // the first K^F slice does not depend on the previous pass: its copy starts
   // before the wait for that pass (programmatic dependent launch)
-  if (tile < ntiles) issue_k(tile);
+  if (tile < ntiles) issue_k(kt, yi);
   pdl_wait();
-  if (tile < ntiles) issue_input(tile);
+  if (tile < ntiles) issue_input(kt, yi);
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
-    const int kx = (a.kt0 + tile % ntk) * TK + t;
+    const int kx = (a.kt0 + kt) * TK + t;
     const bool valid = kx < a.c;
-    const int ky = paired_ky(tile / ntk, a.L2);
+    const int ky = paired_ky(yi, a.L2);
     float2* line = base + ky * a.src_plane + kx;
     cp_async_wait_all();
     __syncthreads();  // this tile's inputs and K^F slice have landed
@@ -270,7 +306,7 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     }
     __syncthreads();  // the input stage is free
     if constexpr (SEP) {
-      if (next < ntiles) issue_input(next);
+      if (next < ntiles) issue_input(nkt, nyi);
       cp_async_commit();
     }
 
@@ -306,7 +342,7 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
 #pragma unroll
     for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], twid(b, j));
     __syncthreads();  // the forward exchange and the K^F stage have been read
-    if (next < ntiles) issue_k(next);
+    if (next < ntiles) issue_k(nkt, nyi);
     cp_async_commit();
 #pragma unroll
     for (int b = 0; b < T; ++b) sh4[xi(b, j) + t] = pack(z[b]);
@@ -316,7 +352,7 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[xi(j, k1) + t]);
     if constexpr (!SEP) {
       __syncthreads();  // the exchange has been read: the next tile's rows may land in it
-      if (next < ntiles) issue_input(next);
+      if (next < ntiles) issue_input(nkt, nyi);
       cp_async_commit();
     }
     soa::dft2<P, 1, false>(y);
@@ -324,14 +360,27 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
       float2* p0 = line + (long long)j * es;
       float2* p1 = p0 + (long long)T * es;
       const long long step = (long long)Q * es;
+      if (a.nl >= ROWS) {  // every output row is physical
 #pragma unroll
-      for (int aa = 0; aa < NA; ++aa) {
-        if (j + Q * aa < a.nl) *p0 = make_float2(y[aa].re.x, y[aa].im.x);
-        if (j + T + Q * aa < a.nl) *p1 = make_float2(y[aa].re.y, y[aa].im.y);
-        p0 += step;
-        p1 += step;
+        for (int aa = 0; aa < NA; ++aa) {
+          *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+          *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+          p0 += step;
+          p1 += step;
+        }
+      } else {
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+          if (j + Q * aa < a.nl) *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+          if (j + T + Q * aa < a.nl) *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+          p0 += step;
+          p1 += step;
+        }
       }
     }
+    kt = nkt;
+    yi = nyi;
+    step_tile(nkt, nyi);
   }
   cp_async_wait_all();
   if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
@@ -388,25 +437,47 @@ __global__ void __launch_bounds__(256, 2)
   const int ntk = a.ntk_loc;  // kx tiles a.kt0 .. a.kt0 + ntk - 1
   const int ntiles = ntk * a.nrows;  // nrows = z planes
 
-  auto prefetch = [&](int tile) {
-    const int kx0 = (a.kt0 + tile % ntk) * TK;
-    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
-    const float2* sp = src + (long long)zp * a.src_plane + kx0;
-    for (int q = threadIdx.x; q < ROWS * (TK / 2); q += blockDim.x) {
-      const int row = q / (TK / 2), part = q % (TK / 2);
-      cp_async16(stage + row * TK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
+  // the input copy: ROWS rows of TK float2 in 16-byte pieces, a fixed number
+  // of sweeps of the CTA, per-thread offsets computed once
+  constexpr int NT = TK * T;
+  constexpr int IPR = TK / 2;
+  constexpr int ISTEP = NT / IPR;
+  static_assert(NT % IPR == 0 && ROWS % ISTEP == 0, "input copy shape");
+  const int irow0 = threadIdx.x / IPR;
+  const long long igoff = (long long)irow0 * a.src_elem + 2 * (threadIdx.x % IPR);
+  const long long igstep = (long long)ISTEP * a.src_elem;
+  float2* const is0 = stage + irow0 * TK + 2 * (threadIdx.x % IPR);
+  auto plane = [&](int zi) { return a.rev ? (int)a.nrows - 1 - zi : zi; };
+  auto prefetch = [&](int kt, int zi) {
+    const float2* sp = src + (long long)plane(zi) * a.src_plane + (a.kt0 + kt) * TK + igoff;
+#pragma unroll
+    for (int i = 0; i < ROWS / ISTEP; ++i) {
+      cp_async16(is0 + i * ISTEP * TK, sp);
+      sp += igstep;
+    }
+  };
+  // tile = kt + ntk * zi (kx tile fastest); the CTA steps by gridDim.x tiles
+  const int dkt = gridDim.x % ntk, dzi = gridDim.x / ntk;
+  auto step_tile = [&](int& kt, int& zi) {
+    kt += dkt;
+    zi += dzi;
+    if (kt >= ntk) {
+      kt -= ntk;
+      ++zi;
     }
   };
 
   int tile = blockIdx.x;
-  if (tile < ntiles) prefetch(tile);
+  int kt = tile % ntk, zi = tile / ntk;
+  int nkt = kt, nzi = zi;
+  step_tile(nkt, nzi);
+  if (tile < ntiles) prefetch(kt, zi);
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
-    const int kx = (a.kt0 + tile % ntk) * TK + t;
+    const int kx = (a.kt0 + kt) * TK + t;
     const bool valid = kx < a.c;
-    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
-    float2* d = dst + (long long)zp * a.dst_plane + kx;
+    float2* d = dst + (long long)plane(zi) * a.dst_plane + kx;
     const long long de = a.dst_elem;
     cp_async_wait_all();
     __syncthreads();
@@ -432,7 +503,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * TK + t]);
       __syncthreads();  // exchange read: the next tile's rows may land
-      if (next < ntiles) prefetch(next);
+      if (next < ntiles) prefetch(nkt, nzi);
       cp_async_commit();
       dif_all<T>(z, std::make_integer_sequence<int, T>{});
       soa::dft2<T, -1, false>(z);
@@ -469,7 +540,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * TK + t]);
       __syncthreads();  // exchange read: the next tile's rows may land
-      if (next < ntiles) prefetch(next);
+      if (next < ntiles) prefetch(nkt, nzi);
       cp_async_commit();
       soa::dft2<P, 1, false>(y);
       if (valid) {
@@ -485,6 +556,9 @@ __global__ void __launch_bounds__(256, 2)
         }
       }
     }
+    kt = nkt;
+    zi = nzi;
+    step_tile(nkt, nzi);
   }
   cp_async_wait_all();
 }
