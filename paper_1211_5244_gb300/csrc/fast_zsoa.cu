@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kTKs * T, 512 / (kTKs * T))
   // step C for the lanes b = j and b = j + T: P-point inverses over k1
 #pragma unroll
   for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * kTKs + t]);
-  soa::dft2<P, 1, false>(y);
+  soa::dft2<P, 1, false, HALF>(y);  // only the NA stored outputs when HALF
   if (valid) {
 #pragma unroll
     for (int aa = 0; aa < NA; ++aa) {
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
       if (next < ntiles) issue_input(nkt, nyi);
       cp_async_commit();
     }
-    soa::dft2<P, 1, false>(y);
+    soa::dft2<P, 1, false, HALF>(y);  // only the NA stored outputs when HALF
     if (valid) {
       float2* p0 = line + (long long)j * es;
       float2* p1 = p0 + (long long)T * es;
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(256, 2)
       __syncthreads();  // exchange read: the next tile's rows may land
       if (next < ntiles) prefetch(nkt, nzi);
       cp_async_commit();
-      soa::dft2<P, 1, false>(y);
+      soa::dft2<P, 1, false, HALF>(y);  // only the NA stored outputs when HALF
       if (valid) {
         float2* p0 = d + (long long)j * de;
         float2* p1 = p0 + (long long)T * de;

@@ -87,10 +87,11 @@ __device__ __forceinline__ c2 twc2(c2 v) {
   }
 }
 
-template <int N, int DIR, bool HZ>
+template <int N, int DIR, bool HZ, bool HO = false>
 __device__ __forceinline__ void dft2(c2 (&x)[N]);
 
-template <int N, int K, int DIR>
+// HO: only the outputs below N/2 are formed
+template <int N, int K, int DIR, bool HO>
 __device__ __forceinline__ void bfly4(c2 (&x)[N], const c2 (&s0)[N / 4], const c2 (&s1)[N / 4],
                                       const c2 (&s2)[N / 4], const c2 (&s3)[N / 4]) {
   constexpr int m2 = (2 * K * (64 / N)) & 63;
@@ -109,22 +110,26 @@ __device__ __forceinline__ void bfly4(c2 (&x)[N], const c2 (&s0)[N / 4], const c
   }
   const c2 c = t1 + t3, d = t1 - t3;
   x[K] = a + c;
-  x[K + N / 2] = a - c;
   x[K + N / 4] = add_i<DIR>(b, d);
-  x[K + 3 * N / 4] = sub_i<DIR>(b, d);
+  if constexpr (!HO) {
+    x[K + N / 2] = a - c;
+    x[K + 3 * N / 4] = sub_i<DIR>(b, d);
+  }
 }
 
-template <int N, int DIR, int... K>
+template <int N, int DIR, bool HO, int... K>
 __device__ __forceinline__ void combine4(c2 (&x)[N], const c2 (&s0)[N / 4], const c2 (&s1)[N / 4],
                                          const c2 (&s2)[N / 4], const c2 (&s3)[N / 4],
                                          std::integer_sequence<int, K...>) {
-  (bfly4<N, K, DIR>(x, s0, s1, s2, s3), ...);
+  (bfly4<N, K, DIR, HO>(x, s0, s1, s2, s3), ...);
 }
 
 // In-place N-point DFTs of both lanes (N a power of two <= 64), natural order.
-// HZ: the upper half of the input is zero.
-template <int N, int DIR, bool HZ>
+// HZ: the upper half of the input is zero. HO: only the lower half of the
+// output is needed (N >= 8; the upper half is left undefined).
+template <int N, int DIR, bool HZ, bool HO>
 __device__ __forceinline__ void dft2(c2 (&x)[N]) {
+  static_assert(!HO || N >= 8, "output pruning needs the radix-4 combine");
   if constexpr (N == 1) {
   } else if constexpr (N == 2) {
     if constexpr (HZ) {
@@ -154,7 +159,7 @@ __device__ __forceinline__ void dft2(c2 (&x)[N]) {
     dft2<M, DIR, HZ>(s1);
     dft2<M, DIR, HZ>(s2);
     dft2<M, DIR, HZ>(s3);
-    combine4<N, DIR>(x, s0, s1, s2, s3, std::make_integer_sequence<int, M>{});
+    combine4<N, DIR, HO>(x, s0, s1, s2, s3, std::make_integer_sequence<int, M>{});
   }
 }
 

@@ -236,6 +236,24 @@ def test_parity_odd_y_length_fast_z(torch_cuda, n, bc):
     _check(V, E, rho, bc, 0.25, "f32")
 
 
+# c - 1 a multiple of the kx tile width: the last kx column (kx = L1/2) is the
+# only valid line of its tile in the persistent packed y and z kernels; odd
+# plane and ky-row counts.
+LAST_COLUMN_CASES = [
+    ((32, 256, 13), "fff"),   # y L=512 half, c = 33, 13 z planes in one last-column tile
+    ((64, 512, 20), "fpf"),   # y L=512 full, c = 65, 20 z planes
+    ((32, 13, 256), "fpf"),   # z L=512 half, c = 33, L2 = 13 ky rows
+    ((64, 6, 512), "ffp"),    # z L=512 full, c = 65, L2 = 12
+]
+
+
+@pytest.mark.parametrize("n,bc", LAST_COLUMN_CASES)
+def test_parity_last_column_tiles(torch_cuda, n, bc):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=29 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
+    _check(V, E, rho, bc, 0.25, "f32")
+
+
 # The tensor-core z pass (PS_MATH_TF32X3, L3 = 512): n3 = 256 (free z) and
 # n3 = 512 (periodic z); ragged kx tiles (c not a multiple of 8), odd L2, c = 1.
 TC_CASES = [
