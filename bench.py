@@ -54,8 +54,8 @@ PASS_NAMES = ["p1_fwd_x_r2c", "p2_fwd_y", "p3_z_fwd_mul_inv", "p4_inv_y", "p5_in
 Z_KERNEL_FILES = ("fast_zsoa.cu", "fft_soa.cuh", "fft_regs.cuh", "fft_fast.cuh", "reduce.cuh", "common.cuh",
                   "../../include/psolver.h")
 TRAFFIC = {
-    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 363434496 + 218561792, "files": Z_KERNEL_FILES,
-                                          "src": "80e594d84a82c2b8"},
+    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 365298944 + 218791424, "files": Z_KERNEL_FILES,
+                                          "src": "6af54e17c4a2f259"},
 }
 
 

@@ -187,18 +187,6 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 
 // ---------------------------------------------------------------- pipelined y
 
-__device__ __forceinline__ void cpa16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-// 16 bytes of zeros into shared memory through the same async path (no global read)
-__device__ __forceinline__ void cpa16_zero(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // Persistent y pass (KIND 0 forward, 1 inverse), 16 lines per tile, tiles =
 // (kx tile, z plane) with kx fastest. The shared-memory tile serves twice: as
 // the landing area of the tile's input rows (copied with cp.async) and as the
@@ -231,22 +219,22 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
     for (int q = threadIdx.x; q < ROWS * (kTK / 2); q += blockDim.x) {
       const int row = q / (kTK / 2), part = q % (kTK / 2);
       if (KIND == 1 || row < a.nl)
-        cpa16(sh + row * kTK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
+        cp_async16(sh + row * kTK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
       else  // beyond the physical rows of the plane: zeros
-        cpa16_zero(sh + row * kTK + 2 * part, sp);
+        cp_async16_zero(sh + row * kTK + 2 * part, sp);
     }
   };
 
   int tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile);
-  cpa_commit();
+  cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
     const int kx = (a.kt0 + tile % ntk) * kTK + t;
     const bool valid = kx < a.c;
     const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
     float2* d = dst + (long long)zp * a.dst_plane + kx;
-    cpa_wait_all();
+    cp_async_wait_all();
     __syncthreads();  // the tile's rows have landed
     float2 X[NK][Q];
     if constexpr (KIND == 0) {
@@ -279,7 +267,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
       }
       __syncthreads();  // exchange read: the next tile's rows may land
       if (next < ntiles) prefetch(next);
-      cpa_commit();
+      cp_async_commit();
 #pragma unroll
       for (int v = 0; v < NK; ++v) {
         const int k1 = j + T * v;
@@ -317,7 +305,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
       }
       __syncthreads();  // exchange read: the next tile's rows may land
       if (next < ntiles) prefetch(next);
-      cpa_commit();
+      cp_async_commit();
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
         const int b = j + T * u;
@@ -330,7 +318,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
       }
     }
   }
-  cpa_wait_all();
+  cp_async_wait_all();
 }
 
 template <int P, int Q>

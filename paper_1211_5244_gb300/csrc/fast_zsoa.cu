@@ -167,17 +167,6 @@ const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
 
 // ---------------------------------------------------------------- pipelined
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async16_zero(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // Persistent version of k_zconv_soa with TK lines per tile (8 by default, 16
 // for comparisons): each CTA walks tiles (kx tile fastest, then the paired ky
 // rows) and copies the next tile's n3 input rows and its K^F octant slice into
