@@ -2,7 +2,8 @@
 //
 // A CTA owns 16 lines adjacent in kx (the contiguous axis of A and B), so a
 // warp reads or writes two runs of 16 consecutive complex numbers (2 x 128 B)
-// per instruction. Each line of length L = P * Q is transformed by T = min(P, Q)
+// per instruction; at L = 1024, 8 lines (64-byte runs), which keeps a CTA at
+// 256 threads and 64 KB of shared memory. Each line of length L = P * Q is transformed by T = min(P, Q)
 // threads with the four-step factorisation
 //     X[k1 + P k2] = sum_b W_Q^{b k2} W_L^{b k1} sum_a x[b + Q a] W_P^{a k1},
 // step 1 (P-point DFTs over a) and step 3 (Q-point DFTs over b) in registers,
@@ -32,9 +33,9 @@ constexpr int kTK = 16;  // lines per CTA
 // z pass: rows ky and L2 - ky read the same row of the K^F octant; launch
 // them from adjacent CTA rows (y = 0 -> ky = 0, y = 1 -> ky = L2/2, then
 // pairs p, L2 - p) so the second read hits L2.
-template <int P, int Q, int KIND, bool HALF>
-__global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
-                                  kTK * (P < Q ? P : Q) <= 256 ? (KIND == 2 ? 2 : 3) : 1)
+template <int P, int Q, int KIND, bool HALF, int TK>
+__global__ void __launch_bounds__(TK*(P < Q ? P : Q),
+                                  TK * (P < Q ? P : Q) <= 256 ? (KIND == 2 ? 2 : 3) : 1)
     k_strided(const void* src_v, void* dst_v, const float* __restrict__ K, const float2* __restrict__ tw,
               FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
   pdl_wait();
@@ -43,12 +44,12 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
   constexpr int NB = Q / T;            // step-1 transforms per thread
   constexpr int NK = P / T;            // step-3 transforms per thread
   constexpr int NA = HALF ? P / 2 : P; // a-range of the nonzero inputs / kept outputs
-  extern __shared__ float2 sh[];       // [L][kTK]: element e of line t at e * kTK + t
+  extern __shared__ float2 sh[];       // [L][TK]: element e of line t at e * TK + t
   const float2* src = static_cast<const float2*>(src_v);
   float2* dst = static_cast<float2*>(dst_v);
-  const int t = threadIdx.x % kTK;
-  const int j = threadIdx.x / kTK;
-  const int kx = blockIdx.x * kTK + t;
+  const int t = threadIdx.x % TK;
+  const int j = threadIdx.x / TK;
+  const int kx = blockIdx.x * TK + t;
   const bool valid = kx < a.c;
   const int yblk = KIND == 2 ? paired_ky(blockIdx.y, a.L2)
                              : (a.rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y);
@@ -74,14 +75,14 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
 #pragma unroll
       for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], __ldg(&tw[b * k1]));
 #pragma unroll
-      for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * kTK + t] = y[u][k1];
+      for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * TK + t] = y[u][k1];
     }
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < NK; ++v) {
       const int k1 = j + T * v;
 #pragma unroll
-      for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * kTK + t];
+      for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * TK + t];
       rdft<Q, -1, false>(X[v]);
     }
   } else {
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
     for (int v = 0; v < NK; ++v) {
       const int k1 = j + T * v;
 #pragma unroll
-      for (int b = 0; b < Q; ++b) sh[(b * P + k1) * kTK + t] = X[v][b];
+      for (int b = 0; b < Q; ++b) sh[(b * P + k1) * TK + t] = X[v][b];
     }
     __syncthreads();
 #pragma unroll
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
       const int b = j + T * u;
       float2 y[P];
 #pragma unroll
-      for (int k1 = 0; k1 < P; ++k1) y[k1] = sh[(b * P + k1) * kTK + t];
+      for (int k1 = 0; k1 < P; ++k1) y[k1] = sh[(b * P + k1) * TK + t];
       rdft<P, 1, false>(y);
       if (valid) {
 #pragma unroll
@@ -162,26 +163,219 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q),
   }
 }
 
-template <int P, int Q>
+template <int P, int Q, int TK = kTK>
 static const void* pick_strided(int kind, bool half) {
-  if (kind == 0) return half ? (const void*)k_strided<P, Q, 0, true> : (const void*)k_strided<P, Q, 0, false>;
-  if (kind == 1) return half ? (const void*)k_strided<P, Q, 1, true> : (const void*)k_strided<P, Q, 1, false>;
-  return half ? (const void*)k_strided<P, Q, 2, true> : (const void*)k_strided<P, Q, 2, false>;
+  if (kind == 0) return half ? (const void*)k_strided<P, Q, 0, true, TK> : (const void*)k_strided<P, Q, 0, false, TK>;
+  if (kind == 1) return half ? (const void*)k_strided<P, Q, 1, true, TK> : (const void*)k_strided<P, Q, 1, false, TK>;
+  return half ? (const void*)k_strided<P, Q, 2, true, TK> : (const void*)k_strided<P, Q, 2, false, TK>;
 }
 
-const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* smem) {
+// L = 1024 takes 8 lines per CTA (256 threads, 64 KB of shared memory); the
+// shorter lengths 16
+const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk) {
   const void* fn = nullptr;
-  int T = 0;
+  int T = 0, TK = kTK;
   switch (L) {
     case 64: fn = pick_strided<8, 8>(kind, half); T = 8; break;
     case 128: fn = pick_strided<16, 8>(kind, half); T = 8; break;
     case 256: fn = pick_strided<16, 16>(kind, half); T = 16; break;
     case 512: fn = pick_strided<16, 32>(kind, half); T = 16; break;
-    case 1024: fn = pick_strided<32, 32>(kind, half); T = 32; break;
+    case 1024: fn = pick_strided<32, 32, 8>(kind, half); T = 32; TK = 8; break;
     default: return nullptr;
   }
-  *threads = kTK * T;
-  *smem = (size_t)L * kTK * sizeof(float2);
+  *threads = TK * T;
+  *smem = (size_t)L * TK * sizeof(float2);
+  *tk = TK;
+  return fn;
+}
+
+// ---------------------------------------------------------------- pipelined z
+
+// Persistent z pass on unpacked lines (used at L3 = 1024, where a packed pair
+// of 32-point transforms would not fit in registers): TK lines per tile, tiles
+// = (kx tile, ky row in the paired order) with kx fastest. The tile's n3 input
+// rows land in the exchange (cp.async), the K^F octant slice in a stage of its
+// own; the next tile's K^F slice is copied once the current one has been
+// used, its input rows once the exchange has been read for the last time.
+template <int P, int Q, bool HALF, int TK>
+__global__ void __launch_bounds__(TK*(P < Q ? P : Q), 2)
+    k_zpipe_u(const void*, void* line_v, const float* __restrict__ K, const float2* __restrict__ tw, FastArgs a,
+              double* partials, unsigned* counter, double escale, double* E) {
+  constexpr int L = P * Q;
+  constexpr int T = P < Q ? P : Q;
+  constexpr int NB = Q / T;
+  constexpr int NK = P / T;
+  constexpr int NA = HALF ? P / 2 : P;
+  constexpr int ROWS = NA * Q;      // input rows of a line
+  constexpr int KROWS = L / 2 + 1;  // rows of the K^F octant
+  extern __shared__ float2 sh[];    // exchange [L][TK]; then the K^F slice [KROWS][TK] floats
+  float* const kstage = reinterpret_cast<float*>(sh + L * TK);
+  float2* const base = static_cast<float2*>(line_v);
+  const int t = threadIdx.x % TK;
+  const int j = threadIdx.x / TK;
+  const int ntk = a.ntk_loc;
+  const int ntiles = ntk * a.L2;
+  const long long es = a.src_elem;
+
+  constexpr int NT = TK * T;
+  constexpr int IPR = TK / 2;  // 16-byte pieces per input row
+  constexpr int ISTEP = NT / IPR;
+  static_assert(NT % IPR == 0 && ROWS % ISTEP == 0, "input copy shape");
+  const int irow0 = threadIdx.x / IPR;
+  const long long igoff = (long long)irow0 * es + 2 * (threadIdx.x % IPR);
+  const long long igstep = (long long)ISTEP * es;
+  float2* const is0 = sh + irow0 * TK + 2 * (threadIdx.x % IPR);
+  const int ivalid = a.nl - irow0;
+  constexpr int KPR = TK / 4;  // 16-byte pieces per K^F row
+  constexpr int KSTEP = NT / KPR;
+  constexpr int KIT = (KROWS + KSTEP - 1) / KSTEP;
+  const int krow0 = threadIdx.x / KPR;
+  const long long kgoff = (long long)krow0 * a.kz_stride + 4 * (threadIdx.x % KPR);
+  const long long kgstep = (long long)KSTEP * a.kz_stride;
+  float* const ks0 = kstage + krow0 * TK + 4 * (threadIdx.x % KPR);
+
+  const int dkt = gridDim.x % ntk, dyi = gridDim.x / ntk;
+  auto step_tile = [&](int& kt, int& yi) {
+    kt += dkt;
+    yi += dyi;
+    if (kt >= ntk) {
+      kt -= ntk;
+      ++yi;
+    }
+  };
+  auto issue_input = [&](int kt, int yi) {
+    const float2* src0 = base + paired_ky(yi, a.L2) * a.src_plane + (a.kt0 + kt) * TK;
+    const float2* src = src0 + igoff;
+#pragma unroll
+    for (int i = 0; i < ROWS / ISTEP; ++i) {
+      if (ISTEP * i < ivalid)
+        cp_async16(is0 + i * ISTEP * TK, src);
+      else  // beyond the physical z rows: zeros (nothing is read)
+        cp_async16_zero(is0 + i * ISTEP * TK, src0);
+      src += igstep;
+    }
+  };
+  auto issue_k = [&](int kt, int yi) {
+    const int ky = paired_ky(yi, a.L2);
+    const int kyo = min(ky, a.L2 - ky);
+    const float* src = K + (long long)kyo * a.ldk + (a.kt0 + kt) * TK + kgoff;
+#pragma unroll
+    for (int i = 0; i < KIT; ++i) {
+      if ((i + 1) * KSTEP <= KROWS || krow0 + i * KSTEP < KROWS) cp_async16(ks0 + i * KSTEP * TK, src);
+      src += kgstep;
+    }
+  };
+
+  float eacc = 0.f;
+  int tile = blockIdx.x;
+  int kt = tile % ntk, yi = tile / ntk;
+  int nkt = kt, nyi = yi;
+  step_tile(nkt, nyi);
+  if (tile < ntiles) issue_k(kt, yi);  // K^F is not written by any pass
+  pdl_wait();
+  if (tile < ntiles) issue_input(kt, yi);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    const int kx = (a.kt0 + kt) * TK + t;
+    const bool valid = kx < a.c;
+    const int ky = paired_ky(yi, a.L2);
+    float2* line = base + ky * a.src_plane + kx;
+    cp_async_wait_all();
+    __syncthreads();  // this tile's input rows and K^F slice have landed
+
+    float2 y[NB][P];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int b = j + T * u;
+#pragma unroll
+      for (int aa = 0; aa < P; ++aa) {
+        y[u][aa] = make_float2(0.f, 0.f);
+        if (aa < NA && valid) y[u][aa] = sh[(b + Q * aa) * TK + t];
+      }
+    }
+    __syncthreads();  // inputs read: the space becomes the exchange
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int b = j + T * u;
+      rdft<P, -1, HALF>(y[u]);
+#pragma unroll
+      for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], __ldg(&tw[b * k1]));
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * TK + t] = y[u][k1];
+    }
+    __syncthreads();
+    float2 X[NK][Q];
+    float e1 = 0.f;
+#pragma unroll
+    for (int v = 0; v < NK; ++v) {
+      const int k1 = j + T * v;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * TK + t];
+      rdft<Q, -1, false>(X[v]);
+      // V^F = K^F rho^F on the even octant of K^F; energy sum K |rho^F|^2
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) {
+        const int kz = k1 + P * k2;
+        const int kzo = kz <= L / 2 ? kz : L - kz;
+        const float kk = valid ? kstage[kzo * TK + t] : 0.f;
+        const float2 x = X[v][k2];
+        e1 = fmaf(kk, x.x * x.x + x.y * x.y, e1);
+        X[v][k2] = make_float2(kk * x.x, kk * x.y);
+      }
+      rdft<Q, 1, false>(X[v]);
+#pragma unroll
+      for (int b = 1; b < Q; ++b) X[v][b] = cmulcf(X[v][b], __ldg(&tw[b * k1]));
+    }
+    eacc += e1 * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
+    __syncthreads();  // the forward exchange and the K^F slice have been read
+    if (next < ntiles) issue_k(nkt, nyi);
+    cp_async_commit();
+#pragma unroll
+    for (int v = 0; v < NK; ++v) {
+      const int k1 = j + T * v;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) sh[(b * P + k1) * TK + t] = X[v][b];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int b = j + T * u;
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * P + k1) * TK + t];
+    }
+    __syncthreads();  // the exchange has been read: the next tile's rows may land in it
+    if (next < ntiles) issue_input(nkt, nyi);
+    cp_async_commit();
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int b = j + T * u;
+      rdft<P, 1, false>(y[u]);
+      if (valid) {
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa)
+          if (b + Q * aa < a.nl) line[(long long)(b + Q * aa) * es] = y[u][aa];
+      }
+    }
+    kt = nkt;
+    yi = nyi;
+    step_tile(nkt, nyi);
+  }
+  cp_async_wait_all();
+  if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
+}
+
+const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk) {
+  const void* fn = nullptr;
+  int T = 0, TK = 8;
+  switch (L) {
+    case 1024: fn = half ? (const void*)k_zpipe_u<32, 32, true, 8> : (const void*)k_zpipe_u<32, 32, false, 8>; T = 32;
+      break;
+    default: return nullptr;
+  }
+  *threads = TK * T;
+  *smem = (size_t)L * TK * sizeof(float2) + (size_t)(L / 2 + 1) * TK * sizeof(float);
+  *tk = TK;
   return fn;
 }
 
@@ -193,8 +387,8 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 // exchange of the four-step transform. Once a tile's exchange has been read,
 // the next tile's rows are copied in while the last transform step and the
 // stores of the current tile run.
-template <int P, int Q, int KIND, bool HALF>
-__global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
+template <int P, int Q, int KIND, bool HALF, int TK>
+__global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
     k_ypipe(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a, double*,
             unsigned*, double, double*) {
   pdl_wait();
@@ -204,36 +398,60 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
   constexpr int NK = P / T;
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = KIND == 0 ? NA * Q : L;  // input rows of a line
-  extern __shared__ float2 sh[];               // [L][kTK]
+  extern __shared__ float2 sh[];               // [L][TK]
   const float2* src = static_cast<const float2*>(src_v);
   float2* dst = static_cast<float2*>(dst_v);
-  const int t = threadIdx.x % kTK;
-  const int j = threadIdx.x / kTK;
+  const int t = threadIdx.x % TK;
+  const int j = threadIdx.x / TK;
   const int ntk = a.ntk_loc;  // kx tiles a.kt0 .. a.kt0 + ntk - 1
   const int ntiles = ntk * (int)a.nrows;  // nrows = number of z planes here
 
-  auto prefetch = [&](int tile) {
-    const int kx0 = (a.kt0 + tile % ntk) * kTK;
-    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
-    const float2* sp = src + (long long)zp * a.src_plane + kx0;
-    for (int q = threadIdx.x; q < ROWS * (kTK / 2); q += blockDim.x) {
-      const int row = q / (kTK / 2), part = q % (kTK / 2);
-      if (KIND == 1 || row < a.nl)
-        cp_async16(sh + row * kTK + 2 * part, sp + (long long)row * a.src_elem + 2 * part);
+  // the input copy: ROWS rows of TK float2 in 16-byte pieces, a fixed number
+  // of sweeps of the CTA, per-thread offsets computed once
+  constexpr int NT = TK * T;
+  constexpr int IPR = TK / 2;
+  constexpr int ISTEP = NT / IPR;
+  static_assert(NT % IPR == 0 && ROWS % ISTEP == 0, "input copy shape");
+  const int irow0 = threadIdx.x / IPR;
+  const long long igoff = (long long)irow0 * a.src_elem + 2 * (threadIdx.x % IPR);
+  const long long igstep = (long long)ISTEP * a.src_elem;
+  float2* const is0 = sh + irow0 * TK + 2 * (threadIdx.x % IPR);
+  const int ivalid = a.nl - irow0;  // sweep i copies a physical row iff ISTEP * i < ivalid
+  auto plane = [&](int zi) { return a.rev ? (int)a.nrows - 1 - zi : zi; };
+  auto prefetch = [&](int kt, int zi) {
+    const float2* sp0 = src + (long long)plane(zi) * a.src_plane + (a.kt0 + kt) * TK;
+    const float2* sp = sp0 + igoff;
+#pragma unroll
+    for (int i = 0; i < ROWS / ISTEP; ++i) {
+      if (KIND == 1 || ISTEP * i < ivalid)
+        cp_async16(is0 + i * ISTEP * TK, sp);
       else  // beyond the physical rows of the plane: zeros
-        cp_async16_zero(sh + row * kTK + 2 * part, sp);
+        cp_async16_zero(is0 + i * ISTEP * TK, sp0);
+      sp += igstep;
+    }
+  };
+  // tile = kt + ntk * zi (kx tile fastest); the CTA steps by gridDim.x tiles
+  const int dkt = gridDim.x % ntk, dzi = gridDim.x / ntk;
+  auto step_tile = [&](int& kt, int& zi) {
+    kt += dkt;
+    zi += dzi;
+    if (kt >= ntk) {
+      kt -= ntk;
+      ++zi;
     }
   };
 
   int tile = blockIdx.x;
-  if (tile < ntiles) prefetch(tile);
+  int kt = tile % ntk, zi = tile / ntk;
+  int nkt = kt, nzi = zi;
+  step_tile(nkt, nzi);
+  if (tile < ntiles) prefetch(kt, zi);
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
-    const int kx = (a.kt0 + tile % ntk) * kTK + t;
+    const int kx = (a.kt0 + kt) * TK + t;
     const bool valid = kx < a.c;
-    const int zp = a.rev ? (int)a.nrows - 1 - tile / ntk : tile / ntk;
-    float2* d = dst + (long long)zp * a.dst_plane + kx;
+    float2* d = dst + (long long)plane(zi) * a.dst_plane + kx;
     cp_async_wait_all();
     __syncthreads();  // the tile's rows have landed
     float2 X[NK][Q];
@@ -245,7 +463,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
 #pragma unroll
         for (int aa = 0; aa < P; ++aa) {
           y[u][aa] = make_float2(0.f, 0.f);
-          if (aa < NA && valid) y[u][aa] = sh[(b + Q * aa) * kTK + t];
+          if (aa < NA && valid) y[u][aa] = sh[(b + Q * aa) * TK + t];
         }
       }
       __syncthreads();  // inputs read: the tile becomes the exchange
@@ -256,17 +474,17 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
 #pragma unroll
         for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], __ldg(&tw[b * k1]));
 #pragma unroll
-        for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * kTK + t] = y[u][k1];
+        for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * TK + t] = y[u][k1];
       }
       __syncthreads();
 #pragma unroll
       for (int v = 0; v < NK; ++v) {
         const int k1 = j + T * v;
 #pragma unroll
-        for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * kTK + t];
+        for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * TK + t];
       }
       __syncthreads();  // exchange read: the next tile's rows may land
-      if (next < ntiles) prefetch(next);
+      if (next < ntiles) prefetch(nkt, nzi);
       cp_async_commit();
 #pragma unroll
       for (int v = 0; v < NK; ++v) {
@@ -283,7 +501,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
         const int k1 = j + T * v;
 #pragma unroll
         for (int k2 = 0; k2 < Q; ++k2)
-          X[v][k2] = valid ? sh[(k1 + P * k2) * kTK + t] : make_float2(0.f, 0.f);
+          X[v][k2] = valid ? sh[(k1 + P * k2) * TK + t] : make_float2(0.f, 0.f);
       }
       __syncthreads();  // inputs read: the tile becomes the exchange
 #pragma unroll
@@ -293,7 +511,7 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
 #pragma unroll
         for (int b = 1; b < Q; ++b) X[v][b] = cmulcf(X[v][b], __ldg(&tw[b * k1]));
 #pragma unroll
-        for (int b = 0; b < Q; ++b) sh[(b * P + k1) * kTK + t] = X[v][b];
+        for (int b = 0; b < Q; ++b) sh[(b * P + k1) * TK + t] = X[v][b];
       }
       __syncthreads();
       float2 y[NB][P];
@@ -301,10 +519,10 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
       for (int u = 0; u < NB; ++u) {
         const int b = j + T * u;
 #pragma unroll
-        for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * P + k1) * kTK + t];
+        for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * P + k1) * TK + t];
       }
       __syncthreads();  // exchange read: the next tile's rows may land
-      if (next < ntiles) prefetch(next);
+      if (next < ntiles) prefetch(nkt, nzi);
       cp_async_commit();
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
@@ -317,26 +535,31 @@ __global__ void __launch_bounds__(kTK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
         }
       }
     }
+    kt = nkt;
+    zi = nzi;
+    step_tile(nkt, nzi);
   }
   cp_async_wait_all();
 }
 
-template <int P, int Q>
+template <int P, int Q, int TK = kTK>
 static const void* pick_ypipe(int kind, bool half) {
-  if (kind == 0) return half ? (const void*)k_ypipe<P, Q, 0, true> : (const void*)k_ypipe<P, Q, 0, false>;
-  return half ? (const void*)k_ypipe<P, Q, 1, true> : (const void*)k_ypipe<P, Q, 1, false>;
+  if (kind == 0) return half ? (const void*)k_ypipe<P, Q, 0, true, TK> : (const void*)k_ypipe<P, Q, 0, false, TK>;
+  return half ? (const void*)k_ypipe<P, Q, 1, true, TK> : (const void*)k_ypipe<P, Q, 1, false, TK>;
 }
 
-const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem) {
+const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk) {
   const void* fn = nullptr;
-  int T = 0;
+  int T = 0, TK = kTK;
   switch (L) {
     case 256: fn = pick_ypipe<16, 16>(kind, half); T = 16; break;
     case 512: fn = pick_ypipe<16, 32>(kind, half); T = 16; break;
+    case 1024: fn = pick_ypipe<32, 32, 8>(kind, half); T = 32; TK = 8; break;
     default: return nullptr;
   }
-  *threads = kTK * T;
-  *smem = (size_t)L * kTK * sizeof(float2);
+  *threads = TK * T;
+  *smem = (size_t)L * TK * sizeof(float2);
+  *tk = TK;
   return fn;
 }
 

@@ -297,7 +297,6 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   base.kt0 = 0;
   base.ntk_loc = (p->c + 15) / 16;
   base.ldk = (int)p->ldk;
-  const int ntk = (p->c + 15) / 16;
 
   // x passes: L1 = 2M, n1 = M (free) or 2M (periodic)
   // x passes: L1 = 2M; n1 <= M (zero padding: inputs beyond n1 are zero,
@@ -335,33 +334,36 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const bool exact = 2 * n2 == L2 || n2 == L2;
     const bool soa0 = !plain && exact && !(yp && strcmp(yp, "pipe") == 0);
     const bool soa1 = soa0;
+    int tk0 = 16, tk1 = 16;  // lines per tile (kx columns) of the chosen kernels
     const void* f0 = soa0 ? ysoa_kernel(L2, 0, half, &threads0, &smem0) : nullptr;
     const void* f1 = soa1 ? ysoa_kernel(L2, 1, half, &threads1, &smem1) : nullptr;
     p->ysoa = (f0 ? 1 : 0) | (f1 ? 2 : 0);
-    if (!f0 && !plain) f0 = ypipe_kernel(L2, 0, half, &threads0, &smem0);
-    if (!f1 && !plain) f1 = ypipe_kernel(L2, 1, half, &threads1, &smem1);
+    if (!f0 && !plain) f0 = ypipe_kernel(L2, 0, half, &threads0, &smem0, &tk0);
+    if (!f1 && !plain) f1 = ypipe_kernel(L2, 1, half, &threads1, &smem1, &tk1);
     const bool ypersist = f0 && f1;
     if (!ypersist) {
       p->ysoa = 0;
-      f0 = strided_kernel(L2, 0, half, &threads0, &smem0);
-      f1 = strided_kernel(L2, 1, half, &threads1, &smem1);
+      f0 = strided_kernel(L2, 0, half, &threads0, &smem0, &tk0);
+      f1 = strided_kernel(L2, 1, half, &threads1, &smem1, &tk1);
     }
     if (f0 && f1) {
       FastArgs fwd = base, inv = base;
+      fwd.ntk_loc = (p->c + tk0 - 1) / tk0;
+      inv.ntk_loc = (p->c + tk1 - 1) / tk1;
       fwd.nl = inv.nl = n2;
       fwd.rev = l2order;  // the x pass wrote the last z planes last
       fwd.src_plane = (long long)n2 * ldc; fwd.src_elem = ldc;   // A[z][y][kx]
       fwd.dst_plane = (long long)L2 * ldc; fwd.dst_elem = ldc;   // B[z][ky][kx]
       inv.src_plane = (long long)L2 * ldc; inv.src_elem = ldc;
       inv.dst_plane = (long long)n2 * ldc; inv.dst_elem = ldc;
-      dim3 grid0(ntk, n3), grid1(ntk, n3);
+      dim3 grid0(fwd.ntk_loc, n3), grid1(inv.ntk_loc, n3);
       if (ypersist) {
         fwd.nrows = inv.nrows = n3;  // z planes walked by the persistent CTAs
         int dev = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        const long long tiles = (long long)ntk * n3;
-        auto persistent_grid = [&](const void* f, int threads, size_t smem, dim3* grid) -> cudaError_t {
+        auto persistent_grid = [&](const void* f, int threads, size_t smem, int ntk_f, dim3* grid) -> cudaError_t {
+          const long long tiles = (long long)ntk_f * n3;
           cudaError_t err = cudaSuccess;
           if (smem > 48 * 1024 &&
               (err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -373,8 +375,8 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
           *grid = dim3((unsigned)(g < tiles ? g : tiles), 1);
           return cudaSuccess;
         };
-        if ((e = persistent_grid(f0, threads0, smem0, &grid0)) != cudaSuccess) return e;
-        if ((e = persistent_grid(f1, threads1, smem1, &grid1)) != cudaSuccess) return e;
+        if ((e = persistent_grid(f0, threads0, smem0, fwd.ntk_loc, &grid0)) != cudaSuccess) return e;
+        if ((e = persistent_grid(f1, threads1, smem1, inv.ntk_loc, &grid1)) != cudaSuccess) return e;
       }
       if ((e = set(P2, f0, grid0, threads0, smem0, fwd)) != cudaSuccess) return e;
       if ((e = set(P4, f1, grid1, threads1, smem1, inv)) != cudaSuccess) return e;
@@ -435,11 +437,13 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const int zsoa_tk = ztk_env == 8 ? 8 : 16;
     const bool pipe = allow_soa && !(zp && strcmp(zp, "soa") == 0);
     const void* f = pipe ? zpipe_kernel(L3, half, pipe_tk, &threads, &smem) : nullptr;
-    const bool persistent = f != nullptr;
+    bool persistent = f != nullptr;
     if (!f && allow_soa) f = zsoa_kernel(L3, half, zsoa_tk, &threads, &smem);
     p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;
-    const int ztile = persistent ? pipe_tk : (f ? zsoa_tk : 16);
-    if (!f) f = strided_kernel(L3, 2, half, &threads, &smem);
+    int ztile = persistent ? pipe_tk : zsoa_tk;
+    // L3 = 1024: the persistent unpacked kernel (8 lines per tile)
+    if (!f && pipe && (f = zpipe_u_kernel(L3, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
+    if (!f) f = strided_kernel(L3, 2, half, &threads, &smem, &ztile);
     if (f) {
       FastArgs z = base;
       z.nl = n3;

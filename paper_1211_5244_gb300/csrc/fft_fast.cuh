@@ -54,7 +54,7 @@ using FastKernel = void (*)(const void*, void*, const float*, const float2*, Fas
 // Returns the kernel for a y/z pass of length L, or nullptr.
 //   kind 0: forward (n nonzero inputs, L outputs), 1: inverse (L inputs,
 //   n outputs), 2: forward, K^F multiply, inverse; half: n = L/2 (else n = L)
-const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* smem);
+const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk);
 // Returns the kernel for an x pass (real length 2M): kind 0 R2C, 1 C2R.
 const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, size_t* smem);
 
@@ -66,7 +66,9 @@ const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem);
 const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem);
 
 // The persistent, prefetching y-pass kernels (L2 = 256, 512), or nullptr.
-const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem);
+const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk);
+// persistent unpacked z kernel (L = 1024) and its lines per tile
+const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk);
 
 // The persistent, prefetching packed z-pass kernel (L3 = 512), or nullptr.
 // tk lines per tile (8 or 16).
