@@ -44,10 +44,18 @@ template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) 
 constexpr int kMaxStages = 16;
 constexpr int kMaxLen = 4096;
 
+// x / d for an invariant divisor d >= 1 as one multiply-high by m = ceil(2^32 / d)
+// (m = 0 stands for d = 1). With m d = 2^32 + e, 0 <= e < d, the quotient
+// x m / 2^32 = x / d + x e / (d 2^32) is exact whenever x d < 2^32, which the
+// tile and stage indices (x < 2^20, d <= 4097) satisfy.
+inline unsigned div_magic(unsigned d) { return d <= 1 ? 0u : (unsigned)(((1ull << 32) + d - 1) / d); }
+__device__ __forceinline__ int div_by(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
+
 // Factorisation of a transform length into Stockham stages (radix per stage).
 struct Stages {
   int n;                 // number of stages (0 for length 1)
   int R[kMaxStages];
+  unsigned mg[kMaxStages];  // div_magic of the sub-length Ns entering each stage
 };
 
 // ---------------------------------------------------------------- plan

@@ -101,18 +101,22 @@ template <int DIR, typename T>
 __device__ cpx<T>* stockham(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const Stages& st,
                             const cpx<T>* __restrict__ tw, int tws) {
   using C = cpx<T>;
+  // tk is a power of two dividing blockDim.x: each thread keeps one line t and
+  // takes every (blockDim.x / tk)-th butterfly of it
+  const int ltk = __ffs(tk) - 1;
+  const int t = threadIdx.x & (tk - 1);
+  const int bstep = blockDim.x >> ltk;
   int Ns = 1;
   for (int s = 0; s < st.n; ++s) {
     const int R = st.R[s];
     const int NR = N / R;
     const int estep = N / (Ns * R);
-    const int work = tk * NR;
-    for (int w = threadIdx.x; w < work; w += blockDim.x) {
-      const int t = w % tk;
-      const int bf = w / tk;
-      const int k = bf % Ns;
+    const unsigned mg = st.mg[s];
+    for (int bf = threadIdx.x >> ltk; bf < NR; bf += bstep) {
+      const int q = div_by(bf, mg);  // bf / Ns
+      const int k = bf - q * Ns;
       const int e = k * estep;  // r * e < N for every r < R
-      const int ob = (bf / Ns) * Ns * R + k;
+      const int ob = q * Ns * R + k;
       const C* in = a + bf * ldt + t;
       C* out = b + ob * ldt + t;
       if (R == 2) {
@@ -204,8 +208,10 @@ __device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, 
   const int M = bl.M;
   const C* __restrict__ ch = static_cast<const C*>(bl.chirp);
   const C* __restrict__ Bf = static_cast<const C*>(bl.Bf);
-  for (int w = threadIdx.x; w < tk * M; w += blockDim.x) {
-    const int t = w % tk, m = w / tk;
+  const int ltk = __ffs(tk) - 1;
+  const int t = threadIdx.x & (tk - 1);  // blockDim.x is a multiple of tk
+  const int mstep = blockDim.x >> ltk;
+  for (int m = threadIdx.x >> ltk; m < M; m += mstep) {
     C v = mk(T(0), T(0));
     if (m < N) v = DIR < 0 ? cmul(a[m * ldt + t], ch[m]) : cmulc(a[m * ldt + t], ch[m]);
     a[m * ldt + t] = v;
@@ -213,16 +219,12 @@ __device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, 
   __syncthreads();
   C* r = stockham<-1, T>(a, b, M, tk, ldt, bl.st, static_cast<const C*>(bl.twM), 1);
   C* o = (r == a) ? b : a;
-  for (int w = threadIdx.x; w < tk * M; w += blockDim.x) {
-    const int t = w % tk, m = w / tk;
+  for (int m = threadIdx.x >> ltk; m < M; m += mstep)
     r[m * ldt + t] = DIR < 0 ? cmul(r[m * ldt + t], Bf[m]) : cmulc(r[m * ldt + t], Bf[m]);
-  }
   __syncthreads();
   r = stockham<1, T>(r, o, M, tk, ldt, bl.st, static_cast<const C*>(bl.twM), 1);
-  for (int w = threadIdx.x; w < tk * N; w += blockDim.x) {
-    const int t = w % tk, k = w / tk;
+  for (int k = threadIdx.x >> ltk; k < N; k += mstep)
     r[k * ldt + t] = DIR < 0 ? cmul(r[k * ldt + t], ch[k]) : cmulc(r[k * ldt + t], ch[k]);
-  }
   __syncthreads();
   return r;
 }

@@ -40,6 +40,8 @@ struct GenArgs {
   int N;    // transform length of this pass
   int tws;  // twiddle-table stride (table length / N)
   int rows; // rows of each shared-memory buffer (>= N, and >= M in Bluestein form)
+  int ltk;  // log2 tk (tk is a power of two)
+  unsigned mn1, mc, mN1;  // div_magic of n1, c and N + 1
   Stages st;
   BlueArgs bl;
 };
@@ -59,7 +61,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
   for (int w = threadIdx.x; w < a.N * a.ldt; w += blockDim.x) buf0[w] = mk(T(0), T(0));
   __syncthreads();
   for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
-    const int t = w / a.n1, i = w - t * a.n1;
+    const int t = div_by(w, a.mn1), i = w - t * a.n1;
     const int row = row0 + t;
     if (row < nrows) {
       const T v = rho[(size_t)row * a.n1 + i];
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
     // X[k] = E[k] + W_L^k O[k],  E = (Z[k] + conj Z[N-k]) / 2,  O = -i (Z[k] - conj Z[N-k]) / 2
     const int N = a.N;
     for (int w = threadIdx.x; w < a.tk * (N + 1); w += blockDim.x) {
-      const int t = w / (N + 1), k = w - t * (N + 1);
+      const int t = div_by(w, a.mN1), k = w - t * (N + 1);
       const int row = row0 + t;
       if (row >= nrows) continue;
       const C zk = out[(k == N ? 0 : k) * a.ldt + t];
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
     }
   } else {
     for (int w = threadIdx.x; w < a.tk * a.c; w += blockDim.x) {
-      const int t = w / a.c, k = w - t * a.c;
+      const int t = div_by(w, a.mc), k = w - t * a.c;
       const int row = row0 + t;
       if (row < nrows) A[(size_t)row * a.ldc + k] = out[k * a.ldt + t];
     }
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
   const C* s = src + (size_t)z * rows_in * a.ldc + kx0;
   C* d = dst + (size_t)z * rows_out * a.ldc + kx0;
   for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
-    const int t = w % a.tk, y = w / a.tk;
+    const int t = w & (a.tk - 1), y = w >> a.ltk;
     C v = mk(T(0), T(0));
     if (y < nin && kx0 + t < a.c) v = s[(size_t)y * a.ldc + t];
     buf0[y * a.ldt + t] = v;
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
   __syncthreads();
   C* out = line_transform<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   for (int w = threadIdx.x; w < a.tk * nout; w += blockDim.x) {
-    const int t = w % a.tk, y = w / a.tk;
+    const int t = w & (a.tk - 1), y = w >> a.ltk;
     if (kx0 + t < a.c) d[(size_t)y * a.ldc + t] = out[y * a.ldt + t];
   }
 }
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   const size_t zstride = (size_t)a.L2 * a.ldc;
   C* line = Bw + (size_t)ky * a.ldc + kx0;
   for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
-    const int t = w % a.tk, z = w / a.tk;
+    const int t = w & (a.tk - 1), z = w >> a.ltk;
     C v = mk(T(0), T(0));
     if (z < a.n3 && kx0 + t < a.c) v = line[z * zstride + t];
     buf0[z * a.ldt + t] = v;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   const size_t kzstride = (size_t)(a.H2 + 1) * a.ldk;
   T eacc = T(0);
   for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
-    const int t = w % a.tk, kz = w / a.tk;
+    const int t = w & (a.tk - 1), kz = w >> a.ltk;
     const int kx = kx0 + t;
     C v = spec[kz * a.ldt + t];
     if (kx < a.c) {
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   __syncthreads();
   C* res = line_transform<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   for (int w = threadIdx.x; w < a.tk * a.n3; w += blockDim.x) {
-    const int t = w % a.tk, z = w / a.tk;
+    const int t = w & (a.tk - 1), z = w >> a.ltk;
     if (kx0 + t < a.c) line[z * zstride + t] = res[z * a.ldt + t];
   }
   if (E != nullptr) energy_finish((double)eacc, partials, counter, escale, E);
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
   for (int w = threadIdx.x; w < a.tk * a.c; w += blockDim.x) {
-    const int t = w / a.c, k = w - t * a.c;
+    const int t = div_by(w, a.mc), k = w - t * a.c;
     const int row = row0 + t;
     C v = mk(T(0), T(0));
     if (row < nrows) v = A[(size_t)row * a.ldc + k];
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   if (even) {
     // Z[k] = E' + i O',  E' = X[k] + conj X[N-k],  O' = (X[k] - conj X[N-k]) conj(W_L^k)
     for (int w = threadIdx.x; w < a.tk * N; w += blockDim.x) {
-      const int t = w % a.tk, k = w / a.tk;
+      const int t = w & (a.tk - 1), k = w >> a.ltk;
       const C xk = buf0[k * a.ldt + t];
       const C xm = buf0[(N - k) * a.ldt + t];
       const C e = mk(xk.x + xm.x, xk.y - xm.y);
@@ -215,14 +217,14 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
     }
   } else {
     for (int w = threadIdx.x; w < a.tk * N; w += blockDim.x) {
-      const int t = w % a.tk, k = w / a.tk;
+      const int t = w & (a.tk - 1), k = w >> a.ltk;
       buf1[k * a.ldt + t] = k < a.c ? buf0[k * a.ldt + t] : cconj(buf0[(N - k) * a.ldt + t]);
     }
   }
   __syncthreads();
   C* out = line_transform<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
   for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
-    const int t = w / a.n1, i = w - t * a.n1;
+    const int t = div_by(w, a.mn1), i = w - t * a.n1;
     const int row = row0 + t;
     if (row >= nrows) continue;
     T v;
@@ -282,6 +284,11 @@ Stages factorize(int N) {
     while (m % p == 0) { s.R[s.n++] = p; m /= p; }
     if (p * p > m && m > 1) { s.R[s.n++] = m; m = 1; }
   }
+  int Ns = 1;
+  for (int i = 0; i < s.n; ++i) {
+    s.mg[i] = div_magic((unsigned)Ns);
+    Ns *= s.R[i];
+  }
   return s;
 }
 
@@ -320,6 +327,11 @@ static GenArgs gen_args(const ps_plan_s* p, int pass) {
   a.st = p->st[axis];
   a.bl = p->blue[axis];
   a.rows = gen_rows(p, pass);
+  a.ltk = 0;
+  while ((1 << a.ltk) < a.tk) ++a.ltk;
+  a.mn1 = div_magic((unsigned)a.n1);
+  a.mc = div_magic((unsigned)a.c);
+  a.mN1 = div_magic((unsigned)(a.N + 1));
   return a;
 }
 
