@@ -93,7 +93,10 @@ struct PassCfg {
   int tk;       // lines (tile width) per CTA
   int ldt;      // shared-memory row stride in complex elements
   int threads;  // threads per CTA
-  size_t smem;  // dynamic shared memory bytes
+  size_t smem;  // dynamic shared memory bytes (of the specialised kernel when `fast`)
+  size_t gsmem; // dynamic shared memory bytes of the generic kernel of the pass (the x passes
+                // fall back to it when rho or V is not 8-byte aligned)
+  int twn;      // generic passes: twiddle entries kept in shared memory (0: read from global memory)
   int fast;     // 1 if a compile-time specialised kernel runs this pass
   const void* fn;  // the specialised kernel
   dim3 grid, block;

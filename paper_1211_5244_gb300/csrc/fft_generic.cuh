@@ -194,17 +194,42 @@ __device__ cpx<T>* stockham(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const 
   return a;
 }
 
+// Copies the twiddles a tile transform reads into shared memory: W_N^j for
+// j < N (from the length-L table, stride tws), or W_M^j for j < M in
+// Bluestein form. No barrier: the caller's next __syncthreads covers it.
+// Lengths whose table does not fit beside the tile read the global table.
+// Returns the table and stride the transform reads: tsm when `in_smem`, else
+// the global table itself.
+template <typename T>
+__device__ const cpx<T>* load_twiddles(cpx<T>* tsm, const cpx<T>* __restrict__ tw, int N, int tws,
+                                       const BlueArgs& bl, bool in_smem, int* tstr) {
+  if (!in_smem) {
+    *tstr = bl.M ? 1 : tws;
+    return bl.M ? static_cast<const cpx<T>*>(bl.twM) : tw;
+  }
+  *tstr = 1;
+  if (bl.M) {
+    const cpx<T>* __restrict__ tm = static_cast<const cpx<T>*>(bl.twM);
+    for (int j = threadIdx.x; j < bl.M; j += blockDim.x) tsm[j] = tm[j];
+  } else {
+    for (int j = threadIdx.x; j < N; j += blockDim.x) tsm[j] = tw[(size_t)j * tws];
+  }
+  return tsm;
+}
+
 // The transform of a tile (as stockham), in Bluestein form when bl.M > 0:
 // with the stored chirp c[m] = exp(-i pi m^2 / N) (its conjugate for the
 // inverse, DIR = +1), X[k] = c[k] sum_m (x[m] c[m]) conj(c[k - m]) since
 // m k = (m^2 + k^2 - (k - m)^2) / 2. The sum is a cyclic convolution of
 // length M >= 2N - 1, done with length-M Stockham transforms and bl.Bf, the
 // transform of the conjugate chirp divided by M. Both buffers hold M rows.
+// `ttab` with stride `tstr` holds W_N^j (W_M^j in Bluestein form): the
+// shared-memory table of load_twiddles (stride 1), or a global table.
 template <int DIR, typename T>
 __device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const Stages& st,
-                                  const cpx<T>* __restrict__ tw, int tws, const BlueArgs& bl) {
+                                  const cpx<T>* ttab, int tstr, const BlueArgs& bl) {
   using C = cpx<T>;
-  if (bl.M == 0) return stockham<DIR, T>(a, b, N, tk, ldt, st, tw, tws);
+  if (bl.M == 0) return stockham<DIR, T>(a, b, N, tk, ldt, st, ttab, tstr);
   const int M = bl.M;
   const C* __restrict__ ch = static_cast<const C*>(bl.chirp);
   const C* __restrict__ Bf = static_cast<const C*>(bl.Bf);
@@ -217,12 +242,12 @@ __device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, 
     a[m * ldt + t] = v;
   }
   __syncthreads();
-  C* r = stockham<-1, T>(a, b, M, tk, ldt, bl.st, static_cast<const C*>(bl.twM), 1);
+  C* r = stockham<-1, T>(a, b, M, tk, ldt, bl.st, ttab, tstr);
   C* o = (r == a) ? b : a;
   for (int m = threadIdx.x >> ltk; m < M; m += mstep)
     r[m * ldt + t] = DIR < 0 ? cmul(r[m * ldt + t], Bf[m]) : cmulc(r[m * ldt + t], Bf[m]);
   __syncthreads();
-  r = stockham<1, T>(r, o, M, tk, ldt, bl.st, static_cast<const C*>(bl.twM), 1);
+  r = stockham<1, T>(r, o, M, tk, ldt, bl.st, ttab, tstr);
   for (int k = threadIdx.x >> ltk; k < N; k += mstep)
     r[k * ldt + t] = DIR < 0 ? cmul(r[k * ldt + t], ch[k]) : cmulc(r[k * ldt + t], ch[k]);
   __syncthreads();

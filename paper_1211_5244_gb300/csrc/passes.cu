@@ -41,6 +41,7 @@ struct GenArgs {
   int tws;  // twiddle-table stride (table length / N)
   int rows; // rows of each shared-memory buffer (>= N, and >= M in Bluestein form)
   int ltk;  // log2 tk (tk is a power of two)
+  int twn;  // entries of the shared-memory twiddle table (N, or M in Bluestein form); 0: global
   unsigned mn1, mc, mN1;  // div_magic of n1, c and N + 1
   Stages st;
   BlueArgs bl;
@@ -55,6 +56,8 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + a.rows * a.ldt;
+  int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
+  const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
   const int nrows = a.n2 * a.n3;
   const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
     }
   }
   __syncthreads();
-  C* out = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
+  C* out = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   if (even) {
     // X[k] = E[k] + W_L^k O[k],  E = (Z[k] + conj Z[N-k]) / 2,  O = -i (Z[k] - conj Z[N-k]) / 2
     const int N = a.N;
@@ -109,6 +112,8 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + a.rows * a.ldt;
+  int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
+  const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
   const int kx0 = blockIdx.x * a.tk;
   const int z = blockIdx.y;
   const int nin = DIR < 0 ? a.n2 : a.L2;
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
     buf0[y * a.ldt + t] = v;
   }
   __syncthreads();
-  C* out = line_transform<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
+  C* out = line_transform<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   for (int w = threadIdx.x; w < a.tk * nout; w += blockDim.x) {
     const int t = w & (a.tk - 1), y = w >> a.ltk;
     if (kx0 + t < a.c) d[(size_t)y * a.ldc + t] = out[y * a.ldt + t];
@@ -142,6 +147,8 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + a.rows * a.ldt;
+  int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
+  const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
   const int kx0 = blockIdx.x * a.tk;
   const int ky = blockIdx.y;
   const size_t zstride = (size_t)a.L2 * a.ldc;
@@ -153,7 +160,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     buf0[z * a.ldt + t] = v;
   }
   __syncthreads();
-  C* spec = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
+  C* spec = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   C* other = (spec == buf0) ? buf1 : buf0;
   // multiply by the octant of K^F; accumulate w(kx) K |rho^F|^2 for the energy
   const int kyo = min(ky, a.L2 - ky);
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     spec[kz * a.ldt + t] = v;
   }
   __syncthreads();
-  C* res = line_transform<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
+  C* res = line_transform<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   for (int w = threadIdx.x; w < a.tk * a.n3; w += blockDim.x) {
     const int t = w & (a.tk - 1), z = w >> a.ltk;
     if (kx0 + t < a.c) line[z * zstride + t] = res[z * a.ldt + t];
@@ -193,6 +200,8 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + a.rows * a.ldt;
+  int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
+  const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
   const int nrows = a.n2 * a.n3;
   const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
     }
   }
   __syncthreads();
-  C* out = line_transform<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, tw, a.tws, a.bl);
+  C* out = line_transform<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
     const int t = div_by(w, a.mn1), i = w - t * a.n1;
     const int row = row0 + t;
@@ -292,11 +301,26 @@ Stages factorize(int N) {
   return s;
 }
 
-static int pick_tk(int rows, int nbuf, size_t csz, int tk0, size_t budget, int* ldt, size_t* smem) {
-  for (int tk = tk0; tk >= 1; tk /= 2) {
-    const int l = tk + 1;
-    const size_t b = (size_t)nbuf * rows * l * csz;
-    if (b <= budget) { *ldt = l; *smem = b; return tk; }
+// Tile width (lines per CTA, a power of two <= tk0) of a generic pass and
+// whether its twiddle table sits in shared memory: the widest tile whose two
+// buffers and table leave room for three CTAs per SM (72 KB each), else the
+// widest within the 200 KB a CTA may take, else without the table. Narrow
+// tiles of long lines keep the SM busy: with two resident CTAs and global
+// twiddles the generic kernels waited on their loads most of the time.
+static int pick_tk(int rows, int twn, size_t csz, int tk0, int* ldt, size_t* smem, int* twn_out) {
+  const size_t budgets[3] = {(size_t)72 * 1024, (size_t)200 * 1024, (size_t)200 * 1024};
+  for (int pass = 0; pass < 3; ++pass) {
+    const int tw = pass < 2 ? twn : 0;
+    for (int tk = tk0; tk >= 1; tk /= 2) {
+      const int l = tk + 1;
+      const size_t b = (size_t)2 * rows * l * csz + (size_t)tw * csz;
+      if (b <= budgets[pass]) {
+        *ldt = l;
+        *smem = b;
+        *twn_out = tw;
+        return tk;
+      }
+    }
   }
   return 0;
 }
@@ -329,6 +353,7 @@ static GenArgs gen_args(const ps_plan_s* p, int pass) {
   a.rows = gen_rows(p, pass);
   a.ltk = 0;
   while ((1 << a.ltk) < a.tk) ++a.ltk;
+  a.twn = p->cfg[pass].twn;
   a.mn1 = div_magic((unsigned)a.n1);
   a.mc = div_magic((unsigned)a.c);
   a.mN1 = div_magic((unsigned)(a.N + 1));
@@ -348,7 +373,11 @@ cudaError_t configure_passes(ps_plan_s* p) {
     PassCfg& cf = p->cfg[k];
     cf.threads = 256;
     cf.fast = 0;
-    cf.tk = pick_tk(rows[k], 2, sizeof(C), tk0, budget, &cf.ldt, &cf.smem);
+    const int axis = (k == P1 || k == P5) ? 0 : (k == P3 ? 2 : 1);
+    const int Nk = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
+    const int twn = p->blue[axis].M ? p->blue[axis].M : Nk;
+    cf.tk = pick_tk(rows[k], twn, sizeof(C), tk0, &cf.ldt, &cf.gsmem, &cf.twn);
+    cf.smem = cf.gsmem;
     if (cf.tk == 0) {
       set_error("transform length %d needs more shared memory than a CTA has", rows[k]);
       return cudaErrorInvalidConfiguration;
@@ -391,7 +420,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
     if ((e = launch_fast(p, P1, rho, A, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P1);
-    p1_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P1].threads, p->cfg[P1].smem, s>>>(rho, A, tw0, a);
+    p1_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(rho, A, tw0, a);
   }
   if (ev) cudaEventRecord(ev[1], s);
   // P2
@@ -400,7 +429,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   } else {
     GenArgs a = gen_args<T>(p, P2);
     dim3 g((p->c + a.tk - 1) / a.tk, p->n[2]);
-    py_generic<-1, T><<<g, p->cfg[P2].threads, p->cfg[P2].smem, s>>>(A, B, tw1, a);
+    py_generic<-1, T><<<g, p->cfg[P2].threads, p->cfg[P2].gsmem, s>>>(A, B, tw1, a);
   }
   if (ev) cudaEventRecord(ev[2], s);
   // P3
@@ -409,7 +438,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   } else {
     GenArgs a = gen_args<T>(p, P3);
     dim3 g((p->c + a.tk - 1) / a.tk, p->L[1]);
-    pz_generic<T><<<g, p->cfg[P3].threads, p->cfg[P3].smem, s>>>(
+    pz_generic<T><<<g, p->cfg[P3].threads, p->cfg[P3].gsmem, s>>>(
         B, static_cast<const T*>(p->K), tw2, a, p->partials, p->counter, escale, E);
   }
   if (ev) cudaEventRecord(ev[3], s);
@@ -419,7 +448,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   } else {
     GenArgs a = gen_args<T>(p, P4);
     dim3 g((p->c + a.tk - 1) / a.tk, p->n[2]);
-    py_generic<1, T><<<g, p->cfg[P4].threads, p->cfg[P4].smem, s>>>(B, A, tw1, a);
+    py_generic<1, T><<<g, p->cfg[P4].threads, p->cfg[P4].gsmem, s>>>(B, A, tw1, a);
   }
   if (ev) cudaEventRecord(ev[4], s);
   // P5
@@ -427,7 +456,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
     if ((e = launch_fast(p, P5, A, V, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P5);
-    p5_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P5].threads, p->cfg[P5].smem, s>>>(A, V, tw0, a);
+    p5_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(A, V, tw0, a);
   }
   if (ev) cudaEventRecord(ev[5], s);
   return cudaGetLastError();

@@ -236,6 +236,29 @@ def test_parity_odd_y_length_fast_z(torch_cuda, n, bc):
     _check(V, E, rho, bc, 0.25, "f32")
 
 
+@pytest.mark.parametrize("n,bc", [((64, 48, 40), "fff"), ((128, 20, 18), "pff"), ((512, 6, 5), "fff")])
+def test_parity_rho_v_not_8_byte_aligned(torch_cuda, n, bc):
+    """rho and V starting 4 bytes past an 8-byte boundary (valid FP32
+    pointers): the x passes, whose specialised kernels move pairs of reals,
+    run the generic kernels with their own launch configuration."""
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=31 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    rho32 = rho.astype(np.float32)
+    size = rho32.size
+    rbuf = torch.zeros(size + 1, dtype=torch.float32, device="cuda")
+    vbuf = torch.zeros(size + 1, dtype=torch.float32, device="cuda")
+    r = rbuf[1:].view(rho32.shape)
+    V = vbuf[1:].view(rho32.shape)
+    r.copy_(torch.from_numpy(rho32))
+    assert r.data_ptr() % 8 == 4 and V.data_ptr() % 8 == 4
+    plan = psolver.Plan(n, bc, 0.25, "f32")
+    assert plan.info().blocks[0] > 0  # the plan has the specialised x kernels
+    _, E = plan.solve(r, V)
+    torch.cuda.synchronize()
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.25, "f32")
+
+
 # c - 1 a multiple of the kx tile width: the last kx column (kx = L1/2) is the
 # only valid line of its tile in the persistent packed y and z kernels; odd
 # plane and ky-row counts.
