@@ -31,6 +31,8 @@
 
 namespace ps {
 
+constexpr int kU = 4;  // global loads each thread keeps in flight in the tile loops
+
 struct GenArgs {
   int n1, n2, n3;
   int L1, L2, L3;
@@ -63,16 +65,27 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
   const bool even = (a.L1 % 2) == 0;
   for (int w = threadIdx.x; w < a.N * a.ldt; w += blockDim.x) buf0[w] = mk(T(0), T(0));
   __syncthreads();
-  for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
-    const int t = div_by(w, a.mn1), i = w - t * a.n1;
-    const int row = row0 + t;
-    if (row < nrows) {
-      const T v = rho[(size_t)row * a.n1 + i];
-      if (even) {
-        T* f = reinterpret_cast<T*>(&buf0[(i >> 1) * a.ldt + t]);
-        f[i & 1] = v;
-      } else {
-        buf0[i * a.ldt + t] = mk(v, T(0));
+  // the tile's rows are consecutive rows of rho: kU loads in flight per thread
+  const int nin = a.tk * a.n1;
+  const long long base = (long long)row0 * a.n1, lim = (long long)nrows * a.n1;
+  for (int w0 = threadIdx.x; w0 < nin; w0 += kU * blockDim.x) {
+    T v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      v[u] = (w < nin && base + w < lim) ? rho[base + w] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      const int t = div_by(w, a.mn1), i = w - t * a.n1;
+      if (w < nin && row0 + t < nrows) {
+        if (even) {
+          T* f = reinterpret_cast<T*>(&buf0[(i >> 1) * a.ldt + t]);
+          f[i & 1] = v[u];
+        } else {
+          buf0[i * a.ldt + t] = mk(v[u], T(0));
+        }
       }
     }
   }
@@ -122,11 +135,21 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
   const int rows_out = DIR < 0 ? a.L2 : a.n2;
   const C* s = src + (size_t)z * rows_in * a.ldc + kx0;
   C* d = dst + (size_t)z * rows_out * a.ldc + kx0;
-  for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
-    const int t = w & (a.tk - 1), y = w >> a.ltk;
-    C v = mk(T(0), T(0));
-    if (y < nin && kx0 + t < a.c) v = s[(size_t)y * a.ldc + t];
-    buf0[y * a.ldt + t] = v;
+  const int ntot = a.tk * a.N;
+  for (int w0 = threadIdx.x; w0 < ntot; w0 += kU * blockDim.x) {  // kU loads in flight per thread
+    C v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      const int t = w & (a.tk - 1), y = w >> a.ltk;
+      v[u] = mk(T(0), T(0));
+      if (w < ntot && y < nin && kx0 + t < a.c) v[u] = s[(size_t)y * a.ldc + t];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      if (w < ntot) buf0[(w >> a.ltk) * a.ldt + (w & (a.tk - 1))] = v[u];
+    }
   }
   __syncthreads();
   C* out = line_transform<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
@@ -153,11 +176,21 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   const int ky = blockIdx.y;
   const size_t zstride = (size_t)a.L2 * a.ldc;
   C* line = Bw + (size_t)ky * a.ldc + kx0;
-  for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
-    const int t = w & (a.tk - 1), z = w >> a.ltk;
-    C v = mk(T(0), T(0));
-    if (z < a.n3 && kx0 + t < a.c) v = line[z * zstride + t];
-    buf0[z * a.ldt + t] = v;
+  const int ntot = a.tk * a.N;
+  for (int w0 = threadIdx.x; w0 < ntot; w0 += kU * blockDim.x) {  // kU loads in flight per thread
+    C v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      const int t = w & (a.tk - 1), z = w >> a.ltk;
+      v[u] = mk(T(0), T(0));
+      if (w < ntot && z < a.n3 && kx0 + t < a.c) v[u] = line[z * zstride + t];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      if (w < ntot) buf0[(w >> a.ltk) * a.ldt + (w & (a.tk - 1))] = v[u];
+    }
   }
   __syncthreads();
   C* spec = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
@@ -167,20 +200,26 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   const T* Krow = K + (size_t)kyo * a.ldk + kx0;
   const size_t kzstride = (size_t)(a.H2 + 1) * a.ldk;
   T eacc = T(0);
-  for (int w = threadIdx.x; w < a.tk * a.N; w += blockDim.x) {
-    const int t = w & (a.tk - 1), kz = w >> a.ltk;
-    const int kx = kx0 + t;
-    C v = spec[kz * a.ldt + t];
-    if (kx < a.c) {
-      const int kzo = min(kz, a.L3 - kz);
-      const T kk = Krow[kzo * kzstride + t];
-      const T wgt = (kx == 0 || 2 * kx == a.L1) ? T(1) : T(2);
-      eacc += wgt * kk * (v.x * v.x + v.y * v.y);
-      v = cscale(v, kk);
-    } else {
-      v = mk(T(0), T(0));
+  for (int w0 = threadIdx.x; w0 < ntot; w0 += kU * blockDim.x) {  // kU K^F loads in flight per thread
+    T kk[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      const int t = w & (a.tk - 1), kz = w >> a.ltk;
+      kk[u] = T(0);
+      if (w < ntot && kx0 + t < a.c) kk[u] = Krow[min(kz, a.L3 - kz) * kzstride + t];
     }
-    spec[kz * a.ldt + t] = v;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      if (w >= ntot) continue;
+      const int t = w & (a.tk - 1), kz = w >> a.ltk;
+      const int kx = kx0 + t;
+      C v = spec[kz * a.ldt + t];
+      const T wgt = (kx == 0 || 2 * kx == a.L1) ? T(1) : T(2);  // kk = 0 past the last column
+      eacc += wgt * kk[u] * (v.x * v.x + v.y * v.y);
+      spec[kz * a.ldt + t] = cscale(v, kk[u]);
+    }
   }
   __syncthreads();
   C* res = line_transform<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
@@ -205,12 +244,22 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   const int nrows = a.n2 * a.n3;
   const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
-  for (int w = threadIdx.x; w < a.tk * a.c; w += blockDim.x) {
-    const int t = div_by(w, a.mc), k = w - t * a.c;
-    const int row = row0 + t;
-    C v = mk(T(0), T(0));
-    if (row < nrows) v = A[(size_t)row * a.ldc + k];
-    buf0[k * a.ldt + t] = v;
+  const int ntot = a.tk * a.c;
+  for (int w0 = threadIdx.x; w0 < ntot; w0 += kU * blockDim.x) {  // kU loads in flight per thread
+    C v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      const int t = div_by(w, a.mc), k = w - t * a.c;
+      v[u] = mk(T(0), T(0));
+      if (w < ntot && row0 + t < nrows) v[u] = A[(size_t)(row0 + t) * a.ldc + k];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int w = w0 + u * blockDim.x;
+      const int t = div_by(w, a.mc), k = w - t * a.c;
+      if (w < ntot) buf0[k * a.ldt + t] = v[u];
+    }
   }
   __syncthreads();
   const int N = a.N;
@@ -307,12 +356,12 @@ Stages factorize(int N) {
 // widest within the 200 KB a CTA may take, else without the table. Narrow
 // tiles of long lines keep the SM busy: with two resident CTAs and global
 // twiddles the generic kernels waited on their loads most of the time.
-static int pick_tk(int rows, int twn, size_t csz, int tk0, int* ldt, size_t* smem, int* twn_out) {
+static int pick_tk(int rows, int twn, size_t csz, int tk0, int pad, int* ldt, size_t* smem, int* twn_out) {
   const size_t budgets[3] = {(size_t)72 * 1024, (size_t)200 * 1024, (size_t)200 * 1024};
   for (int pass = 0; pass < 3; ++pass) {
     const int tw = pass < 2 ? twn : 0;
     for (int tk = tk0; tk >= 1; tk /= 2) {
-      const int l = tk + 1;
+      const int l = tk + pad;
       const size_t b = (size_t)2 * rows * l * csz + (size_t)tw * csz;
       if (b <= budgets[pass]) {
         *ldt = l;
@@ -376,7 +425,10 @@ cudaError_t configure_passes(ps_plan_s* p) {
     const int axis = (k == P1 || k == P5) ? 0 : (k == P3 ? 2 : 1);
     const int Nk = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
     const int twn = p->blue[axis].M ? p->blue[axis].M : Nk;
-    cf.tk = pick_tk(rows[k], twn, sizeof(C), tk0, &cf.ldt, &cf.gsmem, &cf.twn);
+    // row pitch: tk + 1 for the x passes, whose tile loops transpose rows (a
+    // pitch of tk would put a row's consecutive elements on one bank); tk
+    // for the y and z passes, whose tile rows are contiguous runs
+    cf.tk = pick_tk(rows[k], twn, sizeof(C), tk0, axis == 0 ? 1 : 0, &cf.ldt, &cf.gsmem, &cf.twn);
     cf.smem = cf.gsmem;
     if (cf.tk == 0) {
       set_error("transform length %d needs more shared memory than a CTA has", rows[k]);
