@@ -191,14 +191,14 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 
 // ---------------------------------------------------------------- pipelined z
 
-// Persistent z pass on unpacked lines (used at L3 = 1024, where a packed pair
+// Persistent z pass on unpacked lines (L3 = 256, and 1024, where a packed pair
 // of 32-point transforms would not fit in registers): TK lines per tile, tiles
 // = (kx tile, ky row in the paired order) with kx fastest. The tile's n3 input
 // rows land in the exchange (cp.async), the K^F octant slice in a stage of its
 // own; the next tile's K^F slice is copied once the current one has been
 // used, its input rows once the exchange has been read for the last time.
 template <int P, int Q, bool HALF, int TK>
-__global__ void __launch_bounds__(TK*(P < Q ? P : Q), 2)
+__global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
     k_zpipe_u(const void*, void* line_v, const float* __restrict__ K, const float2* __restrict__ tw, FastArgs a,
               double* partials, unsigned* counter, double escale, double* E) {
   constexpr int L = P * Q;
@@ -369,6 +369,10 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
   const void* fn = nullptr;
   int T = 0, TK = 8;
   switch (L) {
+    case 256: fn = half ? (const void*)k_zpipe_u<16, 16, true, 16> : (const void*)k_zpipe_u<16, 16, false, 16>;
+      T = 16;
+      TK = 16;
+      break;
     case 1024: fn = half ? (const void*)k_zpipe_u<32, 32, true, 8> : (const void*)k_zpipe_u<32, 32, false, 8>; T = 32;
       break;
     default: return nullptr;

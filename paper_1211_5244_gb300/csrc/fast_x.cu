@@ -441,7 +441,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     if (!f && allow_soa) f = zsoa_kernel(L3, half, zsoa_tk, &threads, &smem);
     p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;
     int ztile = persistent ? pipe_tk : zsoa_tk;
-    // L3 = 1024: the persistent unpacked kernel (8 lines per tile)
+    // L3 = 256 and 1024: the persistent unpacked kernel
     if (!f && pipe && (f = zpipe_u_kernel(L3, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
     if (!f) f = strided_kernel(L3, 2, half, &threads, &smem, &ztile);
     if (f) {
