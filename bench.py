@@ -54,8 +54,8 @@ PASS_NAMES = ["p1_fwd_x_r2c", "p2_fwd_y", "p3_z_fwd_mul_inv", "p4_inv_y", "p5_in
 Z_KERNEL_FILES = ("fast_zsoa.cu", "fft_soa.cuh", "fft_regs.cuh", "fft_fast.cuh", "reduce.cuh", "common.cuh",
                   "../../include/psolver.h")
 TRAFFIC = {
-    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 365298944 + 218791424, "files": Z_KERNEL_FILES,
-                                          "src": "6af54e17c4a2f259"},
+    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 364813824 + 218522880, "files": Z_KERNEL_FILES,
+                                          "src": "f3ee192ce622c1ac"},
 }
 
 
