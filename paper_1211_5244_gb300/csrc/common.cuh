@@ -114,6 +114,7 @@ struct ps_plan_s {
   double h;
   int dtype;
   int math;
+  int gen_tk_max;  // most lines per tile of the generic passes (0: 16 for FP32, 8 for FP64)
   bool built;
   int device;
   size_t esz;    // bytes per real element

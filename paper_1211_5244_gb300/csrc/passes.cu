@@ -23,6 +23,7 @@
 // numbers. K^F is stored once, scaled by 1/(L1 L2 L3), as its even octant in
 // the [kz][ky][kx] layout the z pass reads (§3: the transposed kernel).
 #include <cstdio>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "fft_fast.cuh"
@@ -413,7 +414,15 @@ template <typename T>
 cudaError_t configure_passes(ps_plan_s* p) {
   using C = cpx<T>;
   const size_t budget = 200 * 1024;
-  const int tk0 = sizeof(T) == 4 ? 16 : 8;
+  // most lines per generic tile: the plan's (set by the autotuner), else
+  // PS_GEN_TK (a power of two <= 16; comparisons and tests), else 16 / 8
+  int tk0 = sizeof(T) == 4 ? 16 : 8;
+  if (p->gen_tk_max > 0) {
+    tk0 = p->gen_tk_max;
+  } else if (const char* g = getenv("PS_GEN_TK")) {
+    const int v = atoi(g);
+    if (v >= 1 && v <= 16 && (v & (v - 1)) == 0) tk0 = v;
+  }
   const bool even1 = (p->L[0] % 2) == 0;
   const int N0 = even1 ? p->L[0] / 2 : p->L[0];
   (void)N0;

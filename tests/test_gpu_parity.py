@@ -435,6 +435,8 @@ SWITCHES = [
     {"PS_ZPASS": "strided"},                 # unpacked z kernel
     {"PS_XC2R": "smem"},                     # C2R untangling through shared memory
     {"PS_L2ORDER": "0"},                     # every pass in forward plane order
+    {"PS_GEN_TK": "4"},                      # generic passes: at most 4 lines per tile
+    {"PS_GEN_TK": "1"},                      # generic passes: one line per tile
 ]
 
 
