@@ -55,7 +55,7 @@ Z_KERNEL_FILES = ("fast_zsoa.cu", "fft_soa.cuh", "fft_regs.cuh", "fft_fast.cuh",
                   "../../include/psolver.h")
 TRAFFIC = {
     ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 364813824 + 218522880, "files": Z_KERNEL_FILES,
-                                          "src": "f3ee192ce622c1ac"},
+                                          "src": "361db238d7561c98"},
 }
 
 
@@ -85,6 +85,27 @@ def _workload_desc(w, bc="fff", dtype="f32", L=None):
     return (f"{BC_NAMES.get(bc, bc)}-BC ({bc}) Poisson solve {n[0]}x{n[1]}x{n[2]} {'FP32' if dtype == 'f32' else 'FP64'} "
             f"(padded FFT {L[0]}x{L[1]}x{L[2]}), {w['n_gauss']}-Gaussian density + {w['noise']:g} noise"
             f"{neutral}, h={w['h']}, seed {w['seed']}")
+
+
+def _paper_unfused_bytes(info, esz):
+    """HBM bytes of the paper's separate GPU kernels (§3 step list), each reading
+    its input and writing its output once: spread_X, R2C 1DFFT_X, transpose
+    (+spread) and 1DFFT_Y, transpose(+spread) and 1DFFT_Z, the kernel
+    multiplication (K^F at the full half-spectrum size), and the mirror steps
+    of the inverse with compactions. Context for the five fused passes."""
+    n1, n2, n3 = info.n
+    S1, S2, S3 = info.L
+    free = [b == 1 for b in info.bc]
+    c = info.c
+    N = n1 * n2 * n3
+    r, cx = esz, 2 * esz
+    xrows = S1 * n2 * n3 * r            # padded real rows
+    A = c * n2 * n3 * cx                # after the x transform
+    B = c * S2 * n3 * cx                # after the y transform
+    Z = c * S2 * S3 * cx                # full half spectrum
+    one_way = ((N * r + xrows) if free[0] else 0) + (xrows + A) + (A + B) + 2 * B + (B + Z) + 2 * Z
+    multiply = 2 * Z + c * S2 * S3 * r
+    return 2 * one_way + multiply
 
 
 def _pass_flops(info):
@@ -634,6 +655,16 @@ def main():
     pass_ms, nrec = plan.pass_times()
     pass_ms = [t / max(nrec, 1) for t in pass_ms]
 
+    # ---- the same steps without the L2 flush (context: at 128^3 and below the
+    # working set of a solve fits in the 129 MB L2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(K):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    unflushed_ms = ev0.elapsed_time(ev1) / K
+
     # ---- end-to-end through the host-buffer entry point (pinned memory): K
     # densities, each uploaded, solved and downloaded (with its energy), the
     # transfers of one density overlapped with the solves of its neighbours
@@ -676,7 +707,10 @@ def main():
         "solve_roofline": {"alg_bytes": info.alg_bytes, "achieved": solve_gbs, "peak": peak,
                            "unit": "GB/s", "frac": solve_gbs / peak,
                            "compulsory_bytes": compulsory,
-                           "compulsory_frac": compulsory / (ms_per_step / 1e3) / 1e9 / peak},
+                           "compulsory_frac": compulsory / (ms_per_step / 1e3) / 1e9 / peak,
+                           "paper_unfused_bytes": _paper_unfused_bytes(info, esz)},
+        "l2_unflushed": {"ms_per_step": unflushed_ms, "value": npts / (unflushed_ms / 1e3),
+                         "note": "the same K steps back to back without the L2 flush (not the headline)"},
         "passes": passes,
         "e2e": e2e,
         "gpu_launches": info.launches * K,
