@@ -433,10 +433,10 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     // the non-persistent packed kernel; PS_ZTK=8/16 overrides (comparisons)
     const char* ztk = getenv("PS_ZTK");
     const int ztk_env = ztk ? atoi(ztk) : 0;
-    const int pipe_tk = ztk_env == 16 ? 16 : 8;
+    int pipe_tk = ztk_env == 16 ? 16 : 8;
     const int zsoa_tk = ztk_env == 8 ? 8 : 16;
     const bool pipe = allow_soa && !(zp && strcmp(zp, "soa") == 0);
-    const void* f = pipe ? zpipe_kernel(L3, half, pipe_tk, &threads, &smem) : nullptr;
+    const void* f = pipe ? zpipe_kernel(L3, half, &pipe_tk, &threads, &smem) : nullptr;
     bool persistent = f != nullptr;
     if (!f && allow_soa) f = zsoa_kernel(L3, half, zsoa_tk, &threads, &smem);
     p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;

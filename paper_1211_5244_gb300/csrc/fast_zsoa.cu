@@ -375,11 +375,17 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
   if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
 }
 
-const void* zpipe_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
+const void* zpipe_kernel(int L, bool half, int* tk_io, int* threads, size_t* smem) {
   const void* fn = nullptr;
   int T = 0;
+  int tk = *tk_io;
   if (tk != 8 && tk != 16) return nullptr;
   switch (L) {
+    case 128:  // 16 lines per tile (8 would leave a CTA at two warps)
+      fn = half ? (const void*)k_zconv_pipe<8, true, 16> : (const void*)k_zconv_pipe<8, false, 16>;
+      T = 8;
+      tk = 16;
+      break;
     case 512:
       if (tk == 16)
         fn = half ? (const void*)k_zconv_pipe<16, true, 16> : (const void*)k_zconv_pipe<16, false, 16>;
@@ -390,6 +396,7 @@ const void* zpipe_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
     default: return nullptr;
   }
   const int NA = half ? T / 2 : T;
+  *tk_io = tk;
   *threads = tk * T;
   // exchange, input stage (16 lines only; 8 lines reuse the exchange), K^F
   // slice, twiddle table (8 lines only)

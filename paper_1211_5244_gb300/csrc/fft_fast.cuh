@@ -72,7 +72,7 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
 
 // The persistent, prefetching packed z-pass kernel (L3 = 512), or nullptr.
 // tk lines per tile (8 or 16).
-const void* zpipe_kernel(int L, bool half, int tk, int* threads, size_t* smem);
+const void* zpipe_kernel(int L, bool half, int* tk, int* threads, size_t* smem);  // *tk: requested in, used out
 
 // The tensor-core z-pass kernel (L3 = 512; half: n3 = 256, else n3 = 512),
 // its table size in floats and the host fill of that table.
