@@ -42,6 +42,7 @@ METRIC = "grid points/s per Poisson solve (free BCs, 256³) and % of HBM rooflin
 UNIT = "grid points/s"
 WORKLOAD = "free256_f32"
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (context beside the measured peak)
 # FP64 arithmetic roof of the GB300: 1.25 TFLOP/s dense FP64 (nominal; the
 # FP64 pipe is a small fraction of the FP32 one on this part)
 FP64_PEAK_TFLOPS = 1.25
@@ -696,7 +697,8 @@ def main():
         "metric": METRIC if (args.workload in (WORKLOAD, "localpot256") and dt == "f32")
         else f"grid points/s per Poisson solve ({BC_NAMES.get(bc, bc)} BCs, {n[0]}x{n[1]}x{n[2]}, {dt.upper()})",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_median": statistics.median(step_ms),
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
         "config": {"workload": desc, "n": list(n), "bc": bc, "h": w["h"], "L": list(info.L),
                    "math": args.math, "tensor_passes": info.tensor_passes, "blocks": list(info.blocks),
@@ -708,6 +710,7 @@ def main():
                            "unit": "GB/s", "frac": solve_gbs / peak,
                            "compulsory_bytes": compulsory,
                            "compulsory_frac": compulsory / (ms_per_step / 1e3) / 1e9 / peak,
+                           "frac_of_nominal": solve_gbs / NOMINAL_HBM_GBS,
                            "paper_unfused_bytes": _paper_unfused_bytes(info, esz)},
         "l2_unflushed": {"ms_per_step": unflushed_ms, "value": npts / (unflushed_ms / 1e3),
                          "note": "the same K steps back to back without the L2 flush (not the headline)"},
