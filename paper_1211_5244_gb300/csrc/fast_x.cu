@@ -59,7 +59,9 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
   const bool valid = row < a.nrows;
   float2* ex = sh + r * S::ROW;
   float2* zr = ex;  // reused for the row spectrum once the exchange has been read
-  const float2* z = reinterpret_cast<const float2*>(static_cast<const float*>(src_v) + (long long)row * a.n1);
+  const float* xrow = static_cast<const float*>(src_v) + (long long)row * a.n1;
+  const float2* z = reinterpret_cast<const float2*>(xrow);  // pairs of reals (n1 even: 8-byte aligned rows)
+  const bool odd = a.n1 & 1;  // odd rows: reals one at a time, the last pair half zero
   float2* X = static_cast<float2*>(dst_v) + (long long)row * a.ldc;
 
 #pragma unroll
@@ -69,7 +71,9 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), 4)
 #pragma unroll
     for (int aa = 0; aa < P; ++aa) {
       y[aa] = make_float2(0.f, 0.f);
-      if (aa < NA && valid && 2 * (b + Q * aa) < a.n1) y[aa] = z[b + Q * aa];
+      const int m = b + Q * aa;
+      if (aa < NA && valid && 2 * m < a.n1)
+        y[aa] = odd ? make_float2(xrow[2 * m], 2 * m + 1 < a.n1 ? xrow[2 * m + 1] : 0.f) : z[m];
     }
     rdft<P, -1, HALF>(y);
 #pragma unroll
@@ -154,7 +158,9 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), SH ? 3 : 4)
   float2* ex = sh + r * S::ROW;
   float2* xr = ex;  // the row spectrum first, the exchange tile after a barrier
   const float2* X = static_cast<const float2*>(src_v) + (long long)row * a.ldc;
-  float2* z = reinterpret_cast<float2*>(static_cast<float*>(dst_v) + (long long)row * a.n1);
+  float* vrow = static_cast<float*>(dst_v) + (long long)row * a.n1;
+  float2* z = reinterpret_cast<float2*>(vrow);  // pairs of reals (n1 even: 8-byte aligned rows)
+  const bool odd = a.n1 & 1;  // odd rows: reals one at a time, the last one alone
 
   float2 x[NK][Q];
   if constexpr (SH && P == Q) {
@@ -225,8 +231,17 @@ __global__ void __launch_bounds__(TR*(P < Q ? P : Q), SH ? 3 : 4)
     rdft<P, 1, false>(y);
     if (valid) {
 #pragma unroll
-      for (int aa = 0; aa < NA; ++aa)
-        if (2 * (b + Q * aa) < a.n1) z[b + Q * aa] = y[aa];
+      for (int aa = 0; aa < NA; ++aa) {
+        const int m = b + Q * aa;
+        if (2 * m < a.n1) {
+          if (!odd) {
+            z[m] = y[aa];
+          } else {
+            vrow[2 * m] = y[aa].x;
+            if (2 * m + 1 < a.n1) vrow[2 * m + 1] = y[aa].y;
+          }
+        }
+      }
     }
   }
 }
@@ -300,9 +315,10 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
 
   // x passes: L1 = 2M, n1 = M (free) or 2M (periodic)
   // x passes: L1 = 2M; n1 <= M (zero padding: inputs beyond n1 are zero,
-  // outputs beyond n1 are not stored) or n1 = L1 (periodic); n1 even, so the
-  // rows of rho and V stay aligned for the 8-byte pair loads
-  if (L1 % 2 == 0 && pow2(L1 / 2) && (n1 <= L1 / 2 || n1 == L1) && n1 % 2 == 0) {
+  // outputs beyond n1 are not stored) or n1 = L1 (periodic). Even n1 moves
+  // rho and V as 8-byte pairs of reals; odd n1 (rows off the 8-byte grid)
+  // one real at a time
+  if (L1 % 2 == 0 && pow2(L1 / 2) && (n1 <= L1 / 2 || n1 == L1)) {
     const int M = L1 / 2;
     const bool half = n1 <= M;
     int threads, rows;

@@ -236,6 +236,25 @@ def test_parity_odd_y_length_fast_z(torch_cuda, n, bc):
     _check(V, E, rho, bc, 0.25, "f32")
 
 
+# odd n1 on the specialised x kernels (rows off the 8-byte grid: reals moved
+# one at a time), each x shape (M = 32, 64, 128, 256, 512)
+ODD_N1_CASES = [
+    ((31, 6, 10), "fff", (64, 12, 20)),
+    ((63, 20, 18), "fff", (128, 40, 36)),
+    ((127, 9, 7), "fpf", (256, 9, 14)),
+    ((255, 6, 5), "fff", (512, 12, 10)),
+    ((511, 3, 4), "ffp", (1024, 6, 4)),
+]
+
+
+@pytest.mark.parametrize("n,bc,L", ODD_N1_CASES)
+def test_parity_odd_n1_fast_x(torch_cuda, n, bc, L):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=37 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L)
+    assert plan.info().blocks[0] > 0 and plan.info().blocks[4] > 0  # the specialised x kernels ran
+    _check(V, E, rho, bc, 0.25, "f32", L=L)
+
+
 @pytest.mark.parametrize("n,bc", [((64, 48, 40), "fff"), ((128, 20, 18), "pff"), ((512, 6, 5), "fff")])
 def test_parity_rho_v_not_8_byte_aligned(torch_cuda, n, bc):
     """rho and V starting 4 bytes past an 8-byte boundary (valid FP32
