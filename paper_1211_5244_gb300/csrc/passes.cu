@@ -62,12 +62,15 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
   const int nrows = a.n2 * a.n3;
-  const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
+  // even L1: row t is the complex line z[m] = x[2m] + i x[2m+1] of length N;
+  // odd L1: rows 2t and 2t+1 are the real and imaginary parts of line t
+  const int rpc = even ? a.tk : 2 * a.tk;  // rows per CTA
+  const int row0 = blockIdx.x * rpc;
   for (int w = threadIdx.x; w < a.N * a.ldt; w += blockDim.x) buf0[w] = mk(T(0), T(0));
   __syncthreads();
   // the tile's rows are consecutive rows of rho: kU loads in flight per thread
-  const int nin = a.tk * a.n1;
+  const int nin = rpc * a.n1;
   const long long base = (long long)row0 * a.n1, lim = (long long)nrows * a.n1;
   for (int w0 = threadIdx.x; w0 < nin; w0 += kU * blockDim.x) {
     T v[kU];
@@ -85,7 +88,8 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
           T* f = reinterpret_cast<T*>(&buf0[(i >> 1) * a.ldt + t]);
           f[i & 1] = v[u];
         } else {
-          buf0[i * a.ldt + t] = mk(v[u], T(0));
+          T* f = reinterpret_cast<T*>(&buf0[i * a.ldt + (t >> 1)]);
+          f[t & 1] = v[u];
         }
       }
     }
@@ -106,10 +110,17 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
       A[(size_t)row * a.ldc + k] = cadd(e, cmul(o, tw[k]));
     }
   } else {
-    for (int w = threadIdx.x; w < a.tk * a.c; w += blockDim.x) {
-      const int t = div_by(w, a.mc), k = w - t * a.c;
-      const int row = row0 + t;
-      if (row < nrows) A[(size_t)row * a.ldc + k] = out[k * a.ldt + t];
+    // two real rows from one complex line: Xa[k] = (Z[k] + conj Z[N-k]) / 2,
+    // Xb[k] = (Z[k] - conj Z[N-k]) / (2i)
+    const int N = a.N;
+    for (int w = threadIdx.x; w < rpc * a.c; w += blockDim.x) {
+      const int r = div_by(w, a.mc), k = w - r * a.c;
+      const int row = row0 + r;
+      if (row >= nrows) continue;
+      const C zk = out[k * a.ldt + (r >> 1)];
+      const C zm = out[(k == 0 ? 0 : N - k) * a.ldt + (r >> 1)];
+      A[(size_t)row * a.ldc + k] = (r & 1) ? mk(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x))
+                                           : mk(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
     }
   }
 }
@@ -243,9 +254,14 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
   const int nrows = a.n2 * a.n3;
-  const int row0 = blockIdx.x * a.tk;
   const bool even = (a.L1 % 2) == 0;
-  const int ntot = a.tk * a.c;
+  // even L1: row t's spectrum gives the complex line of length N; odd L1:
+  // rows 2t and 2t+1 become the real and imaginary parts of line t (their
+  // half spectra sit at buffer rows [0, c) and [c, 2c); the buffers hold
+  // N + 1 = 2c rows)
+  const int rpc = even ? a.tk : 2 * a.tk;  // rows per CTA
+  const int row0 = blockIdx.x * rpc;
+  const int ntot = rpc * a.c;
   for (int w0 = threadIdx.x; w0 < ntot; w0 += kU * blockDim.x) {  // kU loads in flight per thread
     C v[kU];
 #pragma unroll
@@ -259,7 +275,12 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
     for (int u = 0; u < kU; ++u) {
       const int w = w0 + u * blockDim.x;
       const int t = div_by(w, a.mc), k = w - t * a.c;
-      if (w < ntot) buf0[k * a.ldt + t] = v[u];
+      if (w < ntot) {
+        if (even)
+          buf0[k * a.ldt + t] = v[u];
+        else
+          buf0[(k + (t & 1) * a.c) * a.ldt + (t >> 1)] = v[u];
+      }
     }
   }
   __syncthreads();
@@ -275,14 +296,23 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
       buf1[k * a.ldt + t] = mk(e.x - o.y, e.y + o.x);
     }
   } else {
+    // Z[k] = A[k] + i B[k] over the Hermitian extensions of the two half
+    // spectra; X[0] of a real row is real, so its (rounding-level) imaginary
+    // part is dropped instead of leaking into the other row
     for (int w = threadIdx.x; w < a.tk * N; w += blockDim.x) {
       const int t = w & (a.tk - 1), k = w >> a.ltk;
-      buf1[k * a.ldt + t] = k < a.c ? buf0[k * a.ldt + t] : cconj(buf0[(N - k) * a.ldt + t]);
+      C xa = k < a.c ? buf0[k * a.ldt + t] : cconj(buf0[(N - k) * a.ldt + t]);
+      C xb = k < a.c ? buf0[(a.c + k) * a.ldt + t] : cconj(buf0[(a.c + N - k) * a.ldt + t]);
+      if (k == 0) {
+        xa.y = T(0);
+        xb.y = T(0);
+      }
+      buf1[k * a.ldt + t] = mk(xa.x - xb.y, xa.y + xb.x);
     }
   }
   __syncthreads();
   C* out = line_transform<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
-  for (int w = threadIdx.x; w < a.tk * a.n1; w += blockDim.x) {
+  for (int w = threadIdx.x; w < rpc * a.n1; w += blockDim.x) {
     const int t = div_by(w, a.mn1), i = w - t * a.n1;
     const int row = row0 + t;
     if (row >= nrows) continue;
@@ -291,7 +321,8 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
       const C zz = out[(i >> 1) * a.ldt + t];
       v = (i & 1) ? zz.y : zz.x;
     } else {
-      v = out[i * a.ldt + t].x;
+      const C zz = out[i * a.ldt + (t >> 1)];
+      v = (t & 1) ? zz.y : zz.x;
     }
     V[(size_t)row * a.n1 + i] = v;
   }
@@ -481,7 +512,8 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
     if ((e = launch_fast(p, P1, rho, A, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P1);
-    p1_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(rho, A, tw0, a);
+    const int rpc = (p->L[0] % 2 == 0) ? a.tk : 2 * a.tk;  // odd L1: two real rows per line
+    p1_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(rho, A, tw0, a);
   }
   if (ev) cudaEventRecord(ev[1], s);
   // P2
@@ -517,7 +549,8 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
     if ((e = launch_fast(p, P5, A, V, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P5);
-    p5_generic<T><<<(nrows + a.tk - 1) / a.tk, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(A, V, tw0, a);
+    const int rpc = (p->L[0] % 2 == 0) ? a.tk : 2 * a.tk;  // odd L1: two real rows per line
+    p5_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(A, V, tw0, a);
   }
   if (ev) cudaEventRecord(ev[5], s);
   return cudaGetLastError();
