@@ -208,8 +208,10 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = NA * Q;      // input rows of a line
   constexpr int KROWS = L / 2 + 1;  // rows of the K^F octant
-  extern __shared__ float2 sh[];    // exchange [L][TK]; then the K^F slice [KROWS][TK] floats
+  extern __shared__ float2 sh[];    // exchange [L][TK]; the K^F slice [KROWS][TK] floats; W_L^i, i < L
   float* const kstage = reinterpret_cast<float*>(sh + L * TK);
+  float2* const tws = reinterpret_cast<float2*>(kstage + ((KROWS * TK + 1) & ~1));
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);  // before the first barrier
   float2* const base = static_cast<float2*>(line_v);
   const int t = threadIdx.x % TK;
   const int j = threadIdx.x / TK;
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
       const int b = j + T * u;
       rdft<P, -1, HALF>(y[u]);
 #pragma unroll
-      for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], __ldg(&tw[b * k1]));
+      for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], tws[b * k1]);
 #pragma unroll
       for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * TK + t] = y[u][k1];
     }
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
       }
       rdft<Q, 1, false>(X[v]);
 #pragma unroll
-      for (int b = 1; b < Q; ++b) X[v][b] = cmulcf(X[v][b], __ldg(&tw[b * k1]));
+      for (int b = 1; b < Q; ++b) X[v][b] = cmulcf(X[v][b], tws[b * k1]);
     }
     eacc += e1 * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
     __syncthreads();  // the forward exchange and the K^F slice have been read
@@ -378,7 +380,8 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
     default: return nullptr;
   }
   *threads = TK * T;
-  *smem = (size_t)L * TK * sizeof(float2) + (size_t)(L / 2 + 1) * TK * sizeof(float);
+  *smem = (size_t)L * TK * sizeof(float2) + (size_t)(((L / 2 + 1) * TK + 1) & ~1) * sizeof(float) +
+          (size_t)L * sizeof(float2);
   *tk = TK;
   return fn;
 }
