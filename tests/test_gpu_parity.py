@@ -445,6 +445,19 @@ def test_parity_long_prime_axes(torch_cuda, n, bc, dtype):
     _check(V, E, rho, bc, 0.2, dtype)
 
 
+# Maximum sizes: the longest transform (L = 4096 along y, the generic
+# kernels at two lines per tile), and an FP64 x axis whose tile buffers fill
+# the shared memory so the twiddles are read from global memory (odd
+# L1 = 2625 = 3 * 5^3 * 7: 2626 rows of 16 bytes, two real rows per line).
+@pytest.mark.parametrize("n,bc,dtype", [((4, 2048, 3), "ffp", "f32"), ((3, 2048, 2), "ffp", "f64"),
+                                        ((2625, 2, 3), "ppp", "f64"), ((2625, 3, 2), "pff", "f32")])
+def test_parity_maximum_lengths(torch_cuda, n, bc, dtype):
+    rho = synth.gaussian_mixture(n, 0.2, 3, seed=41 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.2, dtype)
+    assert max(plan.info().L) >= 2625
+    _check(V, E, rho, bc, 0.2, dtype)
+
+
 # The kernel alternatives behind the environment switches (each measured
 # slower at 256^3 than the default, kept for comparisons) against the oracle.
 SWITCHES = [
