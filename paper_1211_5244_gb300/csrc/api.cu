@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 
 #include "common.cuh"
@@ -84,6 +86,64 @@ bool overlap(const void* a, const void* b, size_t bytes) {
   const char* x = static_cast<const char*>(a);
   const char* y = static_cast<const char*>(b);
   return x < y + bytes && y < x + bytes;
+}
+
+// Estimated instructions of one length-M Stockham transform in the generic
+// kernels: per stage of radix R and per point, the shared-memory load and
+// store, the twiddle products of the R - 1 non-trivial inputs (5 each), the
+// R-point butterfly's own operations, about 15 index and loop operations per
+// butterfly, and 4 for the stage's barrier. The generic kernels are bound by
+// instruction issue, so fewer stages can beat a shorter length.
+double stockham_cost(int M) {
+  const Stages s = factorize(M);
+  double c = 0.0;
+  for (int i = 0; i < s.n; ++i) {
+    const int R = s.R[i];
+    double f;
+    switch (R) {
+      case 2: f = 4; break;
+      case 3: f = 12; break;
+      case 4: f = 16; break;
+      case 5: f = 34; break;
+      case 7: f = 66; break;
+      case 8: f = 52; break;
+      default: f = 8.0 * R * R; break;  // direct sum with table twiddles
+    }
+    c += (2.0 * R + 5.0 * (R - 1) + f + 15.0) / R + 4.0;
+  }
+  return c * M;
+}
+
+bool smooth(int m, std::initializer_list<int> primes) {
+  for (int q : primes)
+    while (m % q == 0) m /= q;
+  return m == 1;
+}
+
+// Convolution length M >= 2N - 1 of the Bluestein form of a length-N
+// transform: the 2,3,5,7-smooth length up to the next power of two with the
+// least stockham_cost (PS_BLUE_M=min: the smallest 5-smooth length).
+int bluestein_length(int N) {
+  const int lo = 2 * N - 1;
+  const char* v = getenv("PS_BLUE_M");
+  if (v && strcmp(v, "min") == 0) {
+    int M = lo;
+    while (!smooth(M, {2, 3, 5})) ++M;
+    return M;
+  }
+  int hi = 1;
+  while (hi < lo) hi *= 2;
+  int best = hi;
+  double best_cost = stockham_cost(hi);
+  for (int M = lo; M < hi; ++M) {
+    if (!smooth(M, {2, 3, 5, 7})) continue;
+    const double c = stockham_cost(M);
+    if (c < best_cost) {
+      best = M;
+      best_cost = c;
+    }
+  }
+  return best;
 }
 
 int check_solve_args(ps_plan p, const void* in, const void* out) {
@@ -185,16 +245,10 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
     for (int r = 0; r < p->st[j].n; ++r) big = p->st[j].R[r] > big ? p->st[j].R[r] : big;
     p->blue[j] = BlueArgs{};
     if (big >= 11) {
-      int M = 2 * N - 1;
-      for (;; ++M) {
-        int m = M;
-        for (int q : {2, 3, 5})
-          while (m % q == 0) m /= q;
-        if (m == 1) break;
-      }
       // two buffers of M rows for a one-line tile (ldt = 2) must fit the
       // 200 KiB shared-memory budget of the generic kernels
       const size_t csz = 2 * (p->dtype == PS_F32 ? 4 : 8);
+      const int M = bluestein_length(N);
       if (M <= kMaxLen && (size_t)2 * M * 2 * csz <= 200 * 1024) {
         p->blue[j].M = M;
         p->blue[j].st = factorize(M);

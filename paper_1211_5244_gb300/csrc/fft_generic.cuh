@@ -6,9 +6,9 @@
 // inputs b + r * N / R, multiplies input r by W_N^{r * (b mod Ns) * N/(Ns R)},
 // does an R-point DFT and writes output q to ((b / Ns) * Ns * R + b mod Ns +
 // q * Ns): after the last stage the result is in natural order. Radices 2, 3,
-// 4, 5 and 8 have closed-form butterflies; any other factor (7 or a prime up
-// to 4096) uses the direct R-point sum. Lanes of a warp take consecutive
-// lines t, so every shared-memory access of a warp is contiguous.
+// 4, 5, 7 and 8 have closed-form butterflies; any other factor (a prime from
+// 11 up to 4096) uses the direct R-point sum. Lanes of a warp take
+// consecutive lines t, so every shared-memory access of a warp is contiguous.
 #pragma once
 
 #include "common.cuh"
@@ -74,6 +74,34 @@ __device__ __forceinline__ void dft5(C* v) {
   v[4] = csub(t1, u1);
   v[2] = cadd(t2, u2);
   v[3] = csub(t2, u2);
+}
+
+// 7-point DFT, the same symmetric form as dft5 with c_k = cos(2 pi k / 7),
+// s_k = sin(2 pi k / 7), a_k, b_k = x_k +- x_{7-k} (k = 1, 2, 3):
+// y_m, y_{7-m} = t_m +- DIR i u_m, t_m = x0 + sum_k cos(2 pi m k / 7) a_k,
+// u_m = sum_k sin(2 pi m k / 7) b_k, the angles reduced to k = 1, 2, 3.
+template <int DIR, typename C>
+__device__ __forceinline__ void dft7(C* v) {
+  using R = decltype(v[0].x);
+  const R c1 = R(0.62348980185873353053), c2 = R(-0.22252093395631440429), c3 = R(-0.90096886790241912624);
+  const R s1 = R(0.78183148246802980871), s2 = R(0.97492791218182360702), s3 = R(0.43388373911755812048);
+  const C a1 = cadd(v[1], v[6]), b1 = csub(v[1], v[6]);
+  const C a2 = cadd(v[2], v[5]), b2 = csub(v[2], v[5]);
+  const C a3 = cadd(v[3], v[4]), b3 = csub(v[3], v[4]);
+  const C x0 = v[0];
+  const C t1 = mk(x0.x + c1 * a1.x + c2 * a2.x + c3 * a3.x, x0.y + c1 * a1.y + c2 * a2.y + c3 * a3.y);
+  const C t2 = mk(x0.x + c2 * a1.x + c3 * a2.x + c1 * a3.x, x0.y + c2 * a1.y + c3 * a2.y + c1 * a3.y);
+  const C t3 = mk(x0.x + c3 * a1.x + c1 * a2.x + c2 * a3.x, x0.y + c3 * a1.y + c1 * a2.y + c2 * a3.y);
+  const C u1 = cmul_i<DIR>(mk(s1 * b1.x + s2 * b2.x + s3 * b3.x, s1 * b1.y + s2 * b2.y + s3 * b3.y));
+  const C u2 = cmul_i<DIR>(mk(s2 * b1.x - s3 * b2.x - s1 * b3.x, s2 * b1.y - s3 * b2.y - s1 * b3.y));
+  const C u3 = cmul_i<DIR>(mk(s3 * b1.x - s1 * b2.x + s2 * b3.x, s3 * b1.y - s1 * b2.y + s2 * b3.y));
+  v[0] = cadd(x0, cadd(a1, cadd(a2, a3)));
+  v[1] = cadd(t1, u1);
+  v[6] = csub(t1, u1);
+  v[2] = cadd(t2, u2);
+  v[5] = csub(t2, u2);
+  v[3] = cadd(t3, u3);
+  v[4] = csub(t3, u3);
 }
 
 // 8-point DFT: two 4-point DFTs (even / odd inputs) joined by W_8^k.
@@ -158,6 +186,17 @@ __device__ cpx<T>* stockham(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const 
         dft5<DIR>(v);
 #pragma unroll
         for (int r = 0; r < 5; ++r) out[r * Ns * ldt] = v[r];
+      } else if (R == 7) {
+        C v[7];
+#pragma unroll
+        for (int r = 0; r < 7; ++r) v[r] = in[r * NR * ldt];
+        if (e) {
+#pragma unroll
+          for (int r = 1; r < 7; ++r) v[r] = twid<DIR>(v[r], tw, r * e, tws);
+        }
+        dft7<DIR>(v);
+#pragma unroll
+        for (int r = 0; r < 7; ++r) out[r * Ns * ldt] = v[r];
       } else if (R == 8) {
         C v[8];
 #pragma unroll

@@ -73,6 +73,30 @@ def test_parity_prime_lengths(torch_cuda, n, bc, dtype):
     _check(V, E, rho, bc, 0.3, dtype)
 
 
+# Lengths with radix-7 stages (closed-form 7-point butterflies) and prime
+# lengths whose Bluestein convolution length has a factor 7: 49 = 7 * 7,
+# 343 = 7^3, L1 = 98 (the R2C runs as a 49-point complex transform),
+# 11 -> M = 21 (3 * 7), 17 -> 35 (5 * 7), 23 -> 49, 137 -> 280 (8 * 5 * 7),
+# 109 -> 224 (8 * 4 * 7); free axes padded to 7-smooth lengths.
+RADIX7_CASES = [
+    ((49, 21, 343), "ppp", None),
+    ((98, 35, 56), "ppp", None),
+    ((22, 17, 23), "ppp", None),
+    ((137, 12, 10), "pff", None),
+    ((8, 109, 6), "fpf", None),
+    ((28, 45, 49), "fff", (56, 98, 98)),
+    ((30, 7, 31), "fpf", (63, 7, 126)),
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,bc,L", RADIX7_CASES)
+def test_parity_radix7_and_bluestein_lengths(torch_cuda, n, bc, L, dtype):
+    rho = synth.gaussian_mixture(n, 0.3, 4, seed=13 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.3, dtype, L=L)
+    _check(V, E, rho, bc, 0.3, dtype, L=L)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc,L", [("fff", (19, 25, 27)), ("pff", (10, 27, 45)), ("ppf", (10, 12, 27))])
 def test_parity_other_padded_lengths(torch_cuda, bc, L, dtype):
@@ -469,11 +493,13 @@ SWITCHES = [
     {"PS_L2ORDER": "0"},                     # every pass in forward plane order
     {"PS_GEN_TK": "4"},                      # generic passes: at most 4 lines per tile
     {"PS_GEN_TK": "1"},                      # generic passes: one line per tile
+    {"PS_BLUE_M": "min"},                    # smallest 5-smooth Bluestein length (137: 288, not 280)
 ]
 
 
 @pytest.mark.parametrize("env", SWITCHES, ids=lambda e: ",".join(f"{k}={v}" for k, v in e.items()))
-@pytest.mark.parametrize("n,bc", [((64, 48, 256), "fff"), ((20, 17, 256), "pff"), ((30, 256, 40), "fff")])
+@pytest.mark.parametrize("n,bc", [((64, 48, 256), "fff"), ((20, 17, 256), "pff"), ((30, 256, 40), "fff"),
+                                  ((137, 12, 10), "pff")])
 def test_parity_kernel_switches(torch_cuda, monkeypatch, env, n, bc):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
