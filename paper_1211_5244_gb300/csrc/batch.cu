@@ -6,8 +6,17 @@
 // (small, uneven problems cannot fill the GPU one at a time), and replayed
 // with a single cudaGraphLaunch. Instantiated graphs are cached by the exact
 // set of plans and pointers; destroying a plan drops every graph that uses it.
+//
+// Problems go to the side streams longest first, each to the stream with the
+// least estimated work so far (the LPT rule), so that no chain is left
+// running alone at the end of the batch (PS_BATCH_ORDER=rr: item i on
+// stream i mod 16).
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
+#include <numeric>
 #include <vector>
 
 #include "common.cuh"
@@ -61,15 +70,47 @@ cudaError_t launch_one(ps_plan_s* p, const void* rho, void* V, double* E, cudaSt
   return launch_solve<double>(p, static_cast<const double*>(rho), static_cast<double*>(V), E, s, nullptr);
 }
 
+// Estimated work of one solve: lines x N log2 N per transform (Bluestein:
+// two length-M transforms and the chirp products), forward and inverse.
+double solve_cost(const ps_plan_s* p) {
+  auto f = [&](int j, int N) -> double {
+    if (N < 2) return 0.0;
+    const int M = p->blue[j].M;
+    return M ? 2.0 * M * std::log2((double)M) + 3.0 * N : N * std::log2((double)N);
+  };
+  const double n2 = p->n[1], n3 = p->n[2];
+  const double x = p->L[0] % 2 == 0 ? n2 * n3 * f(0, p->L[0] / 2) : 0.5 * n2 * n3 * f(0, p->L[0]);
+  const double y = (double)p->c * n3 * f(1, p->L[1]);
+  const double z = (double)p->c * p->L[1] * f(2, p->L[2]);
+  return 2.0 * (x + y + z);
+}
+
 cudaError_t capture(int count, ps_plan_s* const* plans, const void* const* rho, void* const* V, double* E,
                     Side* sd, cudaGraphExec_t* exec) {
+  const int K = std::min(count, kSideStreams);
+  std::vector<int> order(count), stream(count);
+  std::iota(order.begin(), order.end(), 0);
+  const char* o = getenv("PS_BATCH_ORDER");
+  if (o && strcmp(o, "rr") == 0) {
+    for (int i = 0; i < count; ++i) stream[i] = i % K;
+  } else {
+    std::vector<double> cost(count), load(K, 0.0);
+    for (int i = 0; i < count; ++i) cost[i] = solve_cost(plans[i]);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int i : order) {
+      const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      stream[i] = k;
+      load[k] += cost[i];
+    }
+  }
   cudaError_t e = cudaStreamBeginCapture(sd->origin, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  const int K = std::min(count, kSideStreams);
   cudaError_t first = cudaEventRecord(sd->fork, sd->origin);
   for (int k = 0; first == cudaSuccess && k < K; ++k) first = cudaStreamWaitEvent(sd->s[k], sd->fork, 0);
-  for (int i = 0; first == cudaSuccess && i < count; ++i)
-    first = launch_one(plans[i], rho[i], V[i], E ? E + i : nullptr, sd->s[i % K]);
+  for (int j = 0; first == cudaSuccess && j < count; ++j) {
+    const int i = order[j];
+    first = launch_one(plans[i], rho[i], V[i], E ? E + i : nullptr, sd->s[stream[i]]);
+  }
   // join every side stream back, even after an error, so the capture can end
   for (int k = 0; k < K; ++k) {
     cudaError_t r = cudaEventRecord(sd->join[k], sd->s[k]);

@@ -164,10 +164,15 @@ def test_adjoint_is_the_symmetric_solve(torch_cuda, bc):
     assert torch.equal(Kv, KTv)
 
 
-def test_batched_matches_individual_solves(torch_cuda):
+@pytest.mark.parametrize("order", ["lpt", "rr"])
+def test_batched_matches_individual_solves(torch_cuda, monkeypatch, order):
+    """Each item of a batched solve equals its single solve, with the items
+    on the side streams longest first (the default) or round robin."""
     torch = torch_cuda
     from paper_1211_5244_gb300 import psolver
-    shapes = synth.batched_shapes(12, 8, 40, seed=3)
+    if order == "rr":
+        monkeypatch.setenv("PS_BATCH_ORDER", "rr")
+    shapes = synth.batched_shapes(36, 8, 40, seed=3)  # more items than side streams
     plans, rhos = [], []
     for i, (n, bc) in enumerate(shapes):
         dtype = "f32" if i % 3 else "f64"
