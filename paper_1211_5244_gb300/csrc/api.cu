@@ -1,6 +1,7 @@
 // C ABI of libpsolver: argument checking, plan bookkeeping, device memory, and
 // the sequence of launches of one solve. All arithmetic runs in the kernels of
 // passes.cu and kernel_build.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -121,29 +122,29 @@ bool smooth(int m, std::initializer_list<int> primes) {
 }
 
 // Convolution length M >= 2N - 1 of the Bluestein form of a length-N
-// transform: the 2,3,5,7-smooth length up to the next power of two with the
-// least stockham_cost (PS_BLUE_M=min: the smallest 5-smooth length).
-int bluestein_length(int N) {
+// transform: among the 2,3,5,7-smooth lengths up to the next power of two and
+// at most max_M, the one with the least stockham_cost (PS_BLUE_M=min, or no
+// candidate within max_M: the smallest 5-smooth length, which the caller
+// checks against max_M).
+int bluestein_length(int N, int max_M) {
   const int lo = 2 * N - 1;
+  int first = lo;
+  while (!smooth(first, {2, 3, 5})) ++first;
   const char* v = getenv("PS_BLUE_M");
-  if (v && strcmp(v, "min") == 0) {
-    int M = lo;
-    while (!smooth(M, {2, 3, 5})) ++M;
-    return M;
-  }
+  if (v && strcmp(v, "min") == 0) return first;
   int hi = 1;
   while (hi < lo) hi *= 2;
-  int best = hi;
-  double best_cost = stockham_cost(hi);
-  for (int M = lo; M < hi; ++M) {
+  int best = 0;
+  double best_cost = 0.0;
+  for (int M = lo; M <= hi && M <= max_M; ++M) {
     if (!smooth(M, {2, 3, 5, 7})) continue;
     const double c = stockham_cost(M);
-    if (c < best_cost) {
+    if (best == 0 || c < best_cost) {
       best = M;
       best_cost = c;
     }
   }
-  return best;
+  return best ? best : first;
 }
 
 int check_solve_args(ps_plan p, const void* in, const void* out) {
@@ -248,8 +249,9 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
       // two buffers of M rows for a one-line tile (ldt = 2) must fit the
       // 200 KiB shared-memory budget of the generic kernels
       const size_t csz = 2 * (p->dtype == PS_F32 ? 4 : 8);
-      const int M = bluestein_length(N);
-      if (M <= kMaxLen && (size_t)2 * M * 2 * csz <= 200 * 1024) {
+      const int max_M = (int)std::min<size_t>(kMaxLen, 200 * 1024 / (2 * 2 * csz));
+      const int M = bluestein_length(N, max_M);
+      if (M <= max_M) {
         p->blue[j].M = M;
         p->blue[j].st = factorize(M);
       }

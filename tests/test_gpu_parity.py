@@ -466,9 +466,12 @@ def test_host_stream_matches_device_solves(torch_cuda):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("n,bc", [((1031, 2, 3), "ppp"), ((3, 509, 2), "fpf"), ((2, 3, 257), "ffp")])
+@pytest.mark.parametrize("n,bc", [((1031, 2, 3), "ppp"), ((3, 509, 2), "fpf"), ((2, 3, 257), "ffp"),
+                                  ((1571, 2, 3), "ppp"), ((2, 1579, 3), "fpf")])
 def test_parity_long_prime_axes(torch_cuda, n, bc, dtype):
-    # long prime periodic axes: chirp-z (Bluestein) transforms of length up to 2048
+    # long prime periodic axes: chirp-z (Bluestein) transforms of length up to
+    # 3584; for 1571 and 1579 the cheapest convolution length (3584) does not
+    # fit the FP64 tiles' shared memory, and FP64 plans take one that does (3200)
     rho = synth.random_density(n, seed=sum(n), subtract_mean=True)
     V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.2, dtype)
     _check(V, E, rho, bc, 0.2, dtype)
