@@ -197,6 +197,10 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 // rows land in the exchange (cp.async), the K^F octant slice in a stage of its
 // own; the next tile's K^F slice is copied once the current one has been
 // used, its input rows once the exchange has been read for the last time.
+// With 8 lines per tile (64-byte exchange rows) the exchange has one padding
+// row after every 32: the four line positions j of a warp then write rows 33
+// apart, on alternate halves of the banks, instead of 32 apart on the same
+// 16 banks (a 4-way conflict in the forward write and the inverse read).
 template <int P, int Q, bool HALF, int TK>
 __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
     k_zpipe_u(const void*, void* line_v, const float* __restrict__ K, const float2* __restrict__ tw, FastArgs a,
@@ -208,8 +212,13 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = NA * Q;      // input rows of a line
   constexpr int KROWS = L / 2 + 1;  // rows of the K^F octant
-  extern __shared__ float2 sh[];    // exchange [L][TK]; the K^F slice [KROWS][TK] floats; W_L^i, i < L
-  float* const kstage = reinterpret_cast<float*>(sh + L * TK);
+  constexpr int RG = TK * 8 < 128 ? P : 0;  // exchange rows per padded group (0: no padding)
+  static_assert(RG == 0 || (P == RG && Q == RG), "padded exchange: P = Q = rows per group");
+  constexpr int PP = RG ? P + 1 : P;         // row pitch of b in the exchange (rows b * PP + k1)
+  constexpr int QQ = RG ? Q + 1 : Q;         // row pitch of aa for the input rows b + Q aa
+  constexpr int LP = RG ? L + L / RG : L;    // exchange rows including the padding
+  extern __shared__ float2 sh[];    // exchange [LP][TK]; the K^F slice [KROWS][TK] floats; W_L^i, i < L
+  float* const kstage = reinterpret_cast<float*>(sh + LP * TK);
   float2* const tws = reinterpret_cast<float2*>(kstage + ((KROWS * TK + 1) & ~1));
   for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);  // before the first barrier
   float2* const base = static_cast<float2*>(line_v);
@@ -223,10 +232,12 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
   constexpr int IPR = TK / 2;  // 16-byte pieces per input row
   constexpr int ISTEP = NT / IPR;
   static_assert(NT % IPR == 0 && ROWS % ISTEP == 0, "input copy shape");
+  static_assert(RG == 0 || ISTEP % RG == 0, "padded input copy shape");
+  constexpr int ISTEPP = RG ? ISTEP + ISTEP / RG : ISTEP;  // exchange rows per sweep, padding included
   const int irow0 = threadIdx.x / IPR;
   const long long igoff = (long long)irow0 * es + 2 * (threadIdx.x % IPR);
   const long long igstep = (long long)ISTEP * es;
-  float2* const is0 = sh + irow0 * TK + 2 * (threadIdx.x % IPR);
+  float2* const is0 = sh + (RG ? irow0 + irow0 / RG : irow0) * TK + 2 * (threadIdx.x % IPR);
   const int ivalid = a.nl - irow0;
   constexpr int KPR = TK / 4;  // 16-byte pieces per K^F row
   constexpr int KSTEP = NT / KPR;
@@ -251,9 +262,9 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
 #pragma unroll
     for (int i = 0; i < ROWS / ISTEP; ++i) {
       if (ISTEP * i < ivalid)
-        cp_async16(is0 + i * ISTEP * TK, src);
+        cp_async16(is0 + i * ISTEPP * TK, src);
       else  // beyond the physical z rows: zeros (nothing is read)
-        cp_async16_zero(is0 + i * ISTEP * TK, src0);
+        cp_async16_zero(is0 + i * ISTEPP * TK, src0);
       src += igstep;
     }
   };
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
 #pragma unroll
       for (int aa = 0; aa < P; ++aa) {
         y[u][aa] = make_float2(0.f, 0.f);
-        if (aa < NA && valid) y[u][aa] = sh[(b + Q * aa) * TK + t];
+        if (aa < NA && valid) y[u][aa] = sh[(b + QQ * aa) * TK + t];
       }
     }
     __syncthreads();  // inputs read: the space becomes the exchange
@@ -304,7 +315,7 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
 #pragma unroll
       for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], tws[b * k1]);
 #pragma unroll
-      for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * TK + t] = y[u][k1];
+      for (int k1 = 0; k1 < P; ++k1) sh[(b * PP + k1) * TK + t] = y[u][k1];
     }
     __syncthreads();
     float2 X[NK][Q];
@@ -313,7 +324,7 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
     for (int v = 0; v < NK; ++v) {
       const int k1 = j + T * v;
 #pragma unroll
-      for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * TK + t];
+      for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * PP + k1) * TK + t];
       rdft<Q, -1, false>(X[v]);
       // V^F = K^F rho^F on the even octant of K^F; energy sum K |rho^F|^2
 #pragma unroll
@@ -337,14 +348,14 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
     for (int v = 0; v < NK; ++v) {
       const int k1 = j + T * v;
 #pragma unroll
-      for (int b = 0; b < Q; ++b) sh[(b * P + k1) * TK + t] = X[v][b];
+      for (int b = 0; b < Q; ++b) sh[(b * PP + k1) * TK + t] = X[v][b];
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
       const int b = j + T * u;
 #pragma unroll
-      for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * P + k1) * TK + t];
+      for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * PP + k1) * TK + t];
     }
     __syncthreads();  // the exchange has been read: the next tile's rows may land in it
     if (next < ntiles) issue_input(nkt, nyi);
@@ -380,7 +391,8 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
     default: return nullptr;
   }
   *threads = TK * T;
-  *smem = (size_t)L * TK * sizeof(float2) + (size_t)(((L / 2 + 1) * TK + 1) & ~1) * sizeof(float) +
+  const int LP = TK * 8 < 128 ? L + L / T : L;  // exchange rows, with the kernel's padding rows
+  *smem = (size_t)LP * TK * sizeof(float2) + (size_t)(((L / 2 + 1) * TK + 1) & ~1) * sizeof(float) +
           (size_t)L * sizeof(float2);
   *tk = TK;
   return fn;

@@ -230,6 +230,7 @@ PADDED_CASES = [
     ((60, 33, 130), "fff", (128, 128, 512)),  # n3=130 with the persistent z kernel
     ((100, 64, 7), "fff", (256, 128, 14)),    # x M=128 (n1=100), z generic
     ((8, 300, 8), "ffp", (16, 1024, 8)),      # y L=1024 (n2=300)
+    ((33, 5, 300), "fff", (66, 64, 1024)),    # z L=1024 (n3=300: physical rows end mid-sweep)
     ((16, 100, 16), "fff", (32, 256, 32)),    # y persistent L=256 (n2=100)
     ((24, 20, 60), "fff", (64, 64, 128)),     # z packed L=128 (n3=60), x M=32 (n1=24)
     ((18, 9, 31), "fff", (64, 64, 64)),       # odd n2, n3; L=64 y and z
@@ -416,6 +417,7 @@ FAST_CASES = [
     ((8, 256, 16), "pff"),     # y L=512 half
     ((4, 4, 512), "ffp"),      # z L=512 full
     ((4, 4, 512), "fff"),      # z L=1024 half
+    ((4, 3, 1024), "ffp"),     # z L=1024 full
     ((6, 1024, 4), "ppf"),     # y L=1024 full
     ((1024, 4, 6), "pff"),     # x M=512 full
     ((512, 6, 4), "fff"),      # x M=512 half
