@@ -405,7 +405,11 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
 // the landing area of the tile's input rows (copied with cp.async) and as the
 // exchange of the four-step transform. Once a tile's exchange has been read,
 // the next tile's rows are copied in while the last transform step and the
-// stores of the current tile run.
+// stores of the current tile run. With 8 lines per tile (64-byte rows) the
+// exchange has one padding row after every 32, as in the L = 1024 z kernel:
+// the forward write and the inverse read of a warp then fall on alternate
+// bank halves instead of 4-way on the same 16 banks. The input rows keep the
+// unpadded layout (they are read before the exchange is written).
 template <int P, int Q, int KIND, bool HALF, int TK>
 __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
     k_ypipe(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a, double*,
@@ -417,7 +421,10 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
   constexpr int NK = P / T;
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = KIND == 0 ? NA * Q : L;  // input rows of a line
-  extern __shared__ float2 sh[];               // [L][TK]
+  constexpr int RG = TK * 8 < 128 ? P : 0;      // exchange rows per padded group (0: no padding)
+  static_assert(RG == 0 || (P == RG && Q == RG), "padded exchange: P = Q = rows per group");
+  constexpr int PP = RG ? P + 1 : P;             // row pitch of b in the exchange (rows b * PP + k1)
+  extern __shared__ float2 sh[];               // inputs [ROWS][TK]; later, in the same space, the exchange [L + L / RG][TK]
   const float2* src = static_cast<const float2*>(src_v);
   float2* dst = static_cast<float2*>(dst_v);
   const int t = threadIdx.x % TK;
@@ -493,14 +500,14 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
 #pragma unroll
         for (int k1 = 1; k1 < P; ++k1) y[u][k1] = cmulf(y[u][k1], __ldg(&tw[b * k1]));
 #pragma unroll
-        for (int k1 = 0; k1 < P; ++k1) sh[(b * P + k1) * TK + t] = y[u][k1];
+        for (int k1 = 0; k1 < P; ++k1) sh[(b * PP + k1) * TK + t] = y[u][k1];
       }
       __syncthreads();
 #pragma unroll
       for (int v = 0; v < NK; ++v) {
         const int k1 = j + T * v;
 #pragma unroll
-        for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * P + k1) * TK + t];
+        for (int b = 0; b < Q; ++b) X[v][b] = sh[(b * PP + k1) * TK + t];
       }
       __syncthreads();  // exchange read: the next tile's rows may land
       if (next < ntiles) prefetch(nkt, nzi);
@@ -530,7 +537,7 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
 #pragma unroll
         for (int b = 1; b < Q; ++b) X[v][b] = cmulcf(X[v][b], __ldg(&tw[b * k1]));
 #pragma unroll
-        for (int b = 0; b < Q; ++b) sh[(b * P + k1) * TK + t] = X[v][b];
+        for (int b = 0; b < Q; ++b) sh[(b * PP + k1) * TK + t] = X[v][b];
       }
       __syncthreads();
       float2 y[NB][P];
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
       for (int u = 0; u < NB; ++u) {
         const int b = j + T * u;
 #pragma unroll
-        for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * P + k1) * TK + t];
+        for (int k1 = 0; k1 < P; ++k1) y[u][k1] = sh[(b * PP + k1) * TK + t];
       }
       __syncthreads();  // exchange read: the next tile's rows may land
       if (next < ntiles) prefetch(nkt, nzi);
@@ -577,7 +584,8 @@ const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem,
     default: return nullptr;
   }
   *threads = TK * T;
-  *smem = (size_t)L * TK * sizeof(float2);
+  const int LP = TK * 8 < 128 ? L + L / T : L;  // exchange rows, with the kernel's padding rows
+  *smem = (size_t)LP * TK * sizeof(float2);
   *tk = TK;
   return fn;
 }
