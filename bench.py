@@ -216,6 +216,101 @@ def _errors(V_gpu, Vo, E_gpu=None, Eo=None, vs="FP64 oracle, full grid"):
     return err
 
 
+def _host_cpu():
+    """(nproc, CPU model) of the host the oracle runs on."""
+    import platform
+    nproc = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return nproc, model or platform.processor() or platform.machine()
+
+
+def _oracle_workers(n, bc, cap=64):
+    """Concurrent oracle processes the host holds: one per core, at most as
+    many as fit in 60% of the available memory (a solve keeps about four
+    copies of the padded complex grid and the padded K^F)."""
+    L = [2 * v if b == "f" else v for v, b in zip(n, bc)]
+    per_gb = 16.0 * L[0] * L[1] * L[2] * 4 / 1e9 + 1.0
+    k = min(os.cpu_count() or 1, cap)
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                k = min(k, max(1, int(0.6 * int(line.split()[1]) / 1e6 / per_gb)))
+                break
+    except Exception:
+        pass
+    return max(1, k)
+
+
+def _oracle_worker(task, barrier, out_q):
+    """One spawned oracle process: builds K^F and its densities (untimed), runs
+    its untimed warm-up solves, waits for the other processes, then times its
+    solves; puts (start, end, solves) on out_q (wall clock)."""
+    import numpy as np
+    from oracle import poisson as op
+    from paper_1211_5244_gb300 import synth
+    n, bc, h, n_gauss, noise, seeds, warm = task
+    KF = op.kernel_fourier(n, bc, h)
+    rhos = [synth.gaussian_mixture(n, h, n_gauss, sd, noise=noise, subtract_mean="p" in bc)
+            .astype(np.float32).astype(np.float64) for sd in seeds]
+    for i in range(warm):
+        op.solve(rhos[i % len(rhos)], bc, h, KF=KF)
+    barrier.wait()
+    t0 = time.time()
+    for r in rhos:
+        op.solve(r, bc, h, KF=KF)
+    out_q.put((t0, time.time(), len(rhos)))
+
+
+def _oracle_concurrent(w, bc, nsolves, workers, warmup=0):
+    """`nsolves` oracle solves of independently seeded densities of the
+    workload, spread over `workers` spawned processes (one per core) that
+    start together; returns (points/s over the whole run, wall seconds,
+    processes used)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    workers = max(1, min(workers, nsolves))
+    barrier = ctx.Barrier(workers)
+    q = ctx.Queue()
+    procs = []
+    for k in range(workers):
+        seeds = [w["seed"] + 1000 + i for i in range(k, nsolves, workers)]
+        warm = len(range(k, warmup, workers))
+        task = (tuple(w["n"]), bc, w["h"], w["n_gauss"], w["noise"], seeds, warm)
+        pr = ctx.Process(target=_oracle_worker, args=(task, barrier, q))
+        pr.start()
+        procs.append(pr)
+    res = [q.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    wall = max(r[1] for r in res) - min(r[0] for r in res)
+    done = sum(r[2] for r in res)
+    npts = int(w["n"][0]) * int(w["n"][1]) * int(w["n"][2])
+    return done * npts / wall, wall, workers
+
+
+def _oracle_item(args):
+    """One oracle solve (a pool task): (V, E) of a density in FP64."""
+    from oracle import poisson as op
+    rho, bc, h = args
+    return op.solve(rho, bc, h)
+
+
 def _oracle_baseline(w, bc, rho_in, V_gpu, E_gpu, kernel=None, max_full=256):
     """The FP64 oracle as it stands, timed on the host on one full solve of the
     workload (K^F built before the timed region, like the GPU's kernel build),
@@ -240,12 +335,27 @@ def _oracle_baseline(w, bc, rho_in, V_gpu, E_gpu, kernel=None, max_full=256):
     Vo, Eo = op.solve(rs, bc, w["h"], KF=KF)
     dt = time.perf_counter() - t0
     Ls = "x".join(str(2 * v if b == "f" else v) for v, b in zip(ns, bc))
-    base = {"value": rs.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full {ns[0]}x{ns[1]}x{ns[2]} {bc} oracle solve (numpy FFT of the padded "
-                      f"{Ls} grid, FP64, single thread), {dt:.1f} s; K^F built untimed"
-                      + ("" if full else f"; a bounded sample of the {w['n'][0]}^3 workload (same recipe)")}
+    nproc, model = _host_cpu()
+    one = {"value": rs.size / dt, "cores": 1,
+           "sample": f"one full {ns[0]}x{ns[1]}x{ns[2]} {bc} oracle solve (numpy FFT of the padded "
+                     f"{Ls} grid, FP64, single thread), {dt:.1f} s; K^F built untimed"
+                     + ("" if full else f"; a bounded sample of the {w['n'][0]}^3 workload (same recipe)")}
+    base = {"value": one["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": one["sample"],
+            "nproc": nproc, "cpu_model": model, "single_core": one}
+    if kernel is None:
+        # all cores: one oracle process per core (as many as the memory holds),
+        # each solving its own seeded density of the same recipe and size
+        try:
+            wk = _oracle_workers(ns, bc)
+            v_all, wall, wk = _oracle_concurrent(dict(w, n=ns), bc, wk, wk)
+            base["all_cores"] = {"value": v_all, "cores": wk,
+                                 "sample": f"{wk} concurrent oracle processes (spawned, one per core, as many "
+                                           f"as 60% of the host memory holds), one full {ns[0]}x{ns[1]}x{ns[2]} "
+                                           f"solve each, {wall:.1f} s wall; K^F built untimed"}
+        except Exception as exc:  # the single-core figure stands on its own
+            base["all_cores"] = {"value": None, "error": f"{type(exc).__name__}: {exc}"}
     if full:
-        return base, _errors(V_gpu, Vo, E_gpu, Eo)
+        return base, _errors(V_gpu, Vo, E_gpu, Eo), (Vo, Eo)
     assert bc == "fff" and kernel is None
     n1, n2, n3 = w["n"]
     rng = np.random.default_rng(7)
@@ -256,53 +366,119 @@ def _oracle_baseline(w, bc, rho_in, V_gpu, E_gpu, kernel=None, max_full=256):
     scale = np.abs(V_gpu).max()
     err = {"rel_max_sampled": float(np.abs(got - ref).max() / scale),
            "points": len(pts), "vs": "Eq. 2 summed directly in FP64 at sampled points (relative to max|V|)"}
-    return base, err
+    return base, err, None
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores. Each step is one oracle
-    solve of a free-BC density of the same recipe at a bounded size (a sample
-    of the 256^3 workload): 128^3 when K + W <= 60, 64^3 up to 600 steps,
-    32^3 beyond, so the whole run stays within about two minutes."""
-    import numpy as np
-    from oracle import poisson as op
+    """Reference arm: the FP64 oracle on the host cores, on this arm's own
+    workload (256^3 free BCs, the same recipe). Each step is one full oracle
+    solve of an independently seeded density; the W warm-up and K timed solves
+    are spread over one spawned process per core (as many as the host memory
+    holds), which start together. When the timed solves would take more than
+    about three minutes at that concurrency, fewer are timed and the line says
+    how many."""
     from paper_1211_5244_gb300 import synth
     from paper_1211_5244_gb300 import replicas
     rank, world, _ = replicas.dist_env()
     if rank != 0:
         return
     w = dict(synth.WORKLOADS[WORKLOAD])
-    m = 128 if args.steps + args.warmup <= 60 else (64 if args.steps + args.warmup <= 600 else 32)
-    ws = dict(w, n=(m, m, m))
-    rho = synth.gaussian_mixture(ws["n"], ws["h"], ws["n_gauss"], ws["seed"], noise=ws["noise"])
-    rho = rho.astype(np.float32).astype(np.float64)
-    KF = op.kernel_fourier(ws["n"], "fff", ws["h"])
-    for _ in range(args.warmup):
-        op.solve(rho, "fff", ws["h"], KF=KF)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        op.solve(rho, "fff", ws["h"], KF=KF)
-    dt = time.perf_counter() - t0
-    value = rho.size * args.steps / dt
-    sample = (f"each step one FP64 oracle solve of a {m}^3 free-BC density of the same recipe "
-              f"(numpy FFT, single thread)")
+    workers = _oracle_workers(w["n"], "fff")
+    # about 8 s per 256^3 solve and core on the GPU hosts measured so far
+    est_s = 8.0 * -(-(args.steps + args.warmup) // workers)
+    steps = args.steps if est_s <= 180 else max(1, int(180 / 8.0) * workers - args.warmup)
+    value, wall, workers = _oracle_concurrent(w, "fff", steps, workers, warmup=min(args.warmup, workers))
+    nproc, model = _host_cpu()
+    sample = (f"each step one full FP64 oracle solve of a 256^3 free-BC density of the workload's recipe "
+              f"(numpy FFT of the padded 512^3 grid, K^F built untimed), {steps} timed solves over {workers} "
+              f"concurrent spawned processes (one per core), {wall:.1f} s wall")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": _workload_desc(w), "bc": "fff"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": _workload_desc(w), "bc": "fff", "n": list(w["n"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
+                             "nproc": nproc, "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if steps != args.steps:
+        line["note"] = f"{steps} of the {args.steps} requested steps timed (each is a full 256^3 oracle solve)"
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args):
-    """64 uneven problems (n ~ U{24..160} per axis, BC uniform over free, wire,
-    surface, periodic; FP32), autotuned plans, one ps_solve_batched per step.
-    The metric is total physical points per second of the batch."""
+def _batched_measure(K, W, rank=0, dist=None, with_oracle=False):
+    """The uneven batch: 64 problems (n ~ U{24..160} per axis, BC uniform over
+    free, wire, surface, periodic; FP32), autotuned plans, one
+    ps_solve_batched per step, an L2 flush before every step. Returns the
+    measured object (and each item's error against the FP64 oracle when asked:
+    the oracle solves run on spawned processes, one per core)."""
     import numpy as np
     import torch
-    from paper_1211_5244_gb300 import build as _build
     from paper_1211_5244_gb300 import psolver, replicas, synth
+    w = synth.WORKLOADS["batched64"]
+    shapes = synth.batched_shapes(w["count"], w["nmin"], w["nmax"], w["seed"])
+    tune = not os.environ.get("PS_BENCH_NO_TUNE")
+    t_tune = time.perf_counter()
+    plans, rhos, rnp = [], [], []
+    for i, (n, bc) in enumerate(shapes):
+        plans.append(psolver.Plan(n, bc, w["h"], "f32", autotune=tune))
+        r = synth.gaussian_mixture(n, w["h"], w["n_gauss"], replicas.replica_seed(w["seed"] + 1000 * (rank + 1), i),
+                                   noise=w["noise"], subtract_mean="p" in bc).astype(np.float32)
+        rnp.append(r)
+        rhos.append(torch.from_numpy(r).cuda())
+    t_tune = time.perf_counter() - t_tune
+    Vs = [torch.empty_like(r) for r in rhos]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        flush.zero_()
+        psolver.solve_batched(plans, rhos, Vs, stream=stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    replicas.barrier(dist)
+    torch.cuda.synchronize()
+    E = None
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        _, E = psolver.solve_batched(plans, rhos, Vs, stream=stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    replicas.barrier(dist)
+    npts = sum(int(np.prod(n)) for n, _ in shapes)
+    value, total_s = replicas.aggregate(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)) / 1e3,
+                                        npts * K, dist, device="cuda")
+    ms = total_s * 1e3 / K
+    alg = sum(p.info().alg_bytes for p in plans)
+    peak, peak_src = _peak_hbm()
+    out = {"ms_per_batch": ms, "value": value, "unit": UNIT, "points": npts,
+           "workload": f"64 problems, n ~ U{{24..160}} per axis, BC uniform over fff/pff/ppf/ppp, FP32, "
+                       f"seed {w['seed']}, autotuned={tune}",
+           "lengths": [list(p.info().L) for p in plans], "autotune_s": t_tune,
+           "solve_roofline": {"alg_bytes": alg, "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
+           "gpu_launches": sum(p.info().launches for p in plans) * K}
+    if with_oracle:
+        import multiprocessing as mp
+        jobs = [(r.astype(np.float64), bc, w["h"]) for r, (_, bc) in zip(rnp, shapes)]
+        with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 16)) as pool:
+            ref = pool.map(_oracle_item, jobs, chunksize=1)
+        Eh = E.double().cpu().numpy()
+        worst = {"rel_l2": 0.0, "rel_max": 0.0, "energy_rel": 0.0}
+        for (Vo, Eo), V, e in zip(ref, Vs, Eh):
+            err = _errors(V.double().cpu().numpy(), Vo, float(e), Eo)
+            for k in worst:
+                worst[k] = max(worst[k], err[k])
+        worst["vs"] = "FP64 oracle, every item, full grids (worst over the 64 items)"
+        out["error_vs_oracle"] = worst
+    return out
+
+
+def run_batched(args):
+    """--workload batched64: the uneven batch as its own JSON line. The metric
+    is total physical points per second of the batch."""
+    import torch
+    from paper_1211_5244_gb300 import build as _build
+    from paper_1211_5244_gb300 import replicas
     rank, world, local = replicas.dist_env()
     torch.cuda.set_device(local)
     dist = None
@@ -310,55 +486,19 @@ def run_batched(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
-    w = synth.WORKLOADS["batched64"]
-    shapes = synth.batched_shapes(w["count"], w["nmin"], w["nmax"], w["seed"])
-    tune = not os.environ.get("PS_BENCH_NO_TUNE")
-    plans, rhos = [], []
-    for i, (n, bc) in enumerate(shapes):
-        plans.append(psolver.Plan(n, bc, w["h"], "f32", autotune=tune))
-        r = synth.gaussian_mixture(n, w["h"], w["n_gauss"], replicas.replica_seed(w["seed"] + 1000 * (rank + 1), i),
-                                   noise=w["noise"], subtract_mean="p" in bc)
-        rhos.append(torch.from_numpy(r.astype(np.float32)).cuda())
-    Vs = [torch.empty_like(r) for r in rhos]
-    E = torch.empty(len(plans), dtype=torch.float64, device="cuda")
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        flush.zero_()
-        psolver.solve_batched(plans, rhos, Vs, stream=stream)
-    torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(local)
-    replicas.barrier(dist)
-    torch.cuda.synchronize()
     sampler.start()
-    time.sleep(0.2)
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        psolver.solve_batched(plans, rhos, Vs, stream=stream)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    replicas.barrier(dist)
+    b = _batched_measure(args.steps, args.warmup, rank, dist,
+                         with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     clocks = sampler.stop()
-    npts = sum(int(np.prod(n)) for n, _ in shapes)
-    value, total_s = replicas.aggregate(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)) / 1e3,
-                                        npts * args.steps, dist, device="cuda")
-    total_ms = total_s * 1e3
-    alg = sum(p.info().alg_bytes for p in plans)
-    peak, peak_src = _peak_hbm()
-    ms = total_ms / args.steps
-    line = {"metric": "grid points/s of a batch of 64 uneven mixed-BC Poisson solves", "value":
-            value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": "grid points/s of a batch of 64 uneven mixed-BC Poisson solves", "value": b["value"],
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": b["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"64 problems, n ~ U{{24..160}} per axis, BC uniform over fff/pff/ppf/ppp, "
-                                   f"seed {w['seed']}, autotuned={tune}", "points": npts,
-                       "lengths": [list(p.info().L) for p in plans]},
-            "solve_roofline": {"alg_bytes": alg, "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
-                               "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
-            "gpu_launches": 5 * len(plans) * args.steps, "clocks": clocks}
+            "config": {"workload": b["workload"], "points": b["points"], "lengths": b["lengths"]},
+            "solve_roofline": b["solve_roofline"], "gpu_launches": b["gpu_launches"], "clocks": clocks}
+    if "error_vs_oracle" in b:
+        line["error_vs_oracle"] = b["error_vs_oracle"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -573,6 +713,59 @@ def run_hartree(args):
         dist.destroy_process_group()
 
 
+def _tf32x3_measure(w, bc, rho, K, W, flush, stream, dist, ref):
+    """One solve per step of the same density with PS_MATH_TF32X3 (the z pass's
+    32-point stages as tcgen05 TF32 MMAs on split operands): per-step CUDA
+    events after an L2 flush, the per-pass times of a second loop, and the
+    error against the FP64 oracle's solve of the same density."""
+    import torch
+    from paper_1211_5244_gb300 import psolver, replicas
+    plan = psolver.Plan(w["n"], bc, w["h"], "f32", math="tf32x3")
+    info = plan.info()
+    V = torch.empty_like(rho)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+
+    def step():
+        plan.solve(rho, V, stream=stream, E=E)
+
+    for _ in range(W):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    replicas.barrier(dist)
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    npts = int(w["n"][0]) * int(w["n"][1]) * int(w["n"][2])
+    value, total_s = replicas.aggregate(sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3, K * npts, dist,
+                                        device="cuda")
+    ms = total_s * 1e3 / K
+    plan.set_profiling(True)
+    plan.pass_times()
+    for _ in range(K):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    plan.set_profiling(False)
+    pass_ms, nrec = plan.pass_times()
+    pass_ms = [t / max(nrec, 1) for t in pass_ms]
+    plan.device_status()
+    peak, _ = _peak_hbm()
+    zb = _pass_bytes(info, 4)[2]
+    out = {"ms_per_step": ms, "value": value, "unit": UNIT, "tensor_passes": info.tensor_passes,
+           "z_pass_ms": pass_ms[2], "z_frac_hbm": zb / (pass_ms[2] / 1e3) / 1e9 / peak,
+           "solve_frac_hbm": info.alg_bytes / (ms / 1e3) / 1e9 / peak, "pass_ms": pass_ms,
+           "note": "z pass as tcgen05 TF32 MMAs with hi/lo operand splits (FP32 accumulation)"}
+    if ref is not None:
+        out["error_vs_oracle"] = _errors(V.double().cpu().numpy(), ref[0], float(E.item()), ref[1])
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -580,6 +773,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line without its tf32x3 and batched64 objects")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "free512", "bc128", "hartree192", "localpot256", "batched64"],
                     help="localpot256: the 256^3 free solve with a caller's even kernel (ps_kernel_set_real)")
@@ -720,10 +915,19 @@ def main():
         "clocks": clocks,
         "kernel_src": _src_hash(),
     }
+    ref = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base, err = _oracle_baseline(w, bc, rho_np, V.double().cpu().numpy(), float(E.item()), kernel)
+        base, err, ref = _oracle_baseline(w, bc, rho_np, V.double().cpu().numpy(), float(E.item()), kernel)
         line["cpu_baseline"] = base
         line["error_vs_oracle"] = err
+    headline = args.workload == WORKLOAD and dt == "f32" and args.math == "cudacore"
+    if headline and not args.no_extras:
+        # the same workload with the z pass on the tensor cores (TF32 split
+        # products), timed the same way, and its error against the same oracle
+        line["tf32x3"] = _tf32x3_measure(w, bc, rho, K, args.warmup, flush, stream, dist, ref)
+        # the uneven batched workload, timed the same way, every item against the oracle
+        line["batched64"] = _batched_measure(K, args.warmup, rank, dist,
+                                             with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

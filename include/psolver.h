@@ -57,8 +57,14 @@ enum ps_dtype { PS_F32 = 0, PS_F64 = 1 };
  *   each operand split into a TF32 part and a remainder and the product
  *   taken as hi*hi + hi*lo + lo*hi with FP32 accumulation (about FP32
  *   accuracy); the other passes stay on the CUDA cores. ps_plan_query's
- *   tensor_passes tells which passes use the tensor cores. */
-enum ps_math { PS_MATH_CUDACORE = 0, PS_MATH_TF32X3 = 1 };
+ *   tensor_passes tells which passes use the tensor cores.
+ * PS_MATH_BF16X3:   split-BF16 tensor-core stages. Not built: this build's
+ *   ps_plan_set_math returns PS_ERR_UNSUPPORTED for it. FP32-level accuracy
+ *   from BF16 needs every operand split into three BF16 terms and six of the
+ *   nine partial products, about 1.5 times the MMA columns of the TF32 form
+ *   and twice its operand splitting on the CUDA cores, and the TF32 form is
+ *   already slower than the CUDA-core stages on this GPU. */
+enum ps_math { PS_MATH_CUDACORE = 0, PS_MATH_TF32X3 = 1, PS_MATH_BF16X3 = 2 };
 
 enum ps_status {
   PS_OK = 0,
@@ -139,8 +145,8 @@ int ps_plan_set_lengths(ps_plan plan, int L1, int L2, int L3);
 int ps_plan_autotune(ps_plan plan, int reps, void* stream);
 
 /* ps_plan_set_math -- enum ps_math; must precede the build (PS_ERR_ARG
- * otherwise, and for an unknown mode). PS_MATH_TF32X3 on an FP64 plan:
- * PS_ERR_UNSUPPORTED. */
+ * otherwise, and for an unknown mode). PS_MATH_TF32X3 on an FP64 plan, and
+ * PS_MATH_BF16X3 on any plan: PS_ERR_UNSUPPORTED. */
 int ps_plan_set_math(ps_plan plan, int math_mode);
 
 /* ps_plan_query -- fill *info (host only; valid before and after the build). */
@@ -223,12 +229,11 @@ int ps_solve_vjp(ps_plan plan, const void* vbar, const void* V, const double* gE
 /*
  * ps_solve_batched -- count independent solves, each with its own built plan
  * (shapes, boundary conditions and dtypes may differ), enqueued on one stream.
- * Plans of the same dtype share one launch per pass.
  *   plans[i], rho[i], V[i]   as in ps_solve
  *   ehartree_dev             NULL or device array of count doubles
  * Each plan may appear at most once. Errors as ps_solve, with the index of
  * the failing item in ps_last_error().
- * The five launches of every problem are captured once into a CUDA graph in
+ * The launches of every problem are captured once into a CUDA graph in
  * which different problems' chains run concurrently (up to 16 at a time);
  * the instantiated graph is cached for the exact set of plans and pointers
  * and replayed by later calls with the same arguments (destroying a plan drops
@@ -317,12 +322,15 @@ int ps_plan_destroy(ps_plan plan);
  * a static device array inside the library, held by every GPU that loads the
  * library until the process exits. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current), so
- * make that first call before any stream capture. Every call shares the one
+ * make that first call before any stream capture. The address is kept for the
+ * life of the library: after a cudaDeviceReset of that device, unload and
+ * reload the library before calling again. Every call shares the one
  * array: calls whose work may overlap on the GPU (two streams, or two host
  * threads) race and give wrong energies; serialise them. The counter is
  * cleared at the start of every call; the partial sums are overwritten.
  * Errors: PS_ERR_ARG (dtype, npoints < 1, h, NULL or misaligned pointers),
- * PS_ERR_UNSUPPORTED (npoints too large), PS_ERR_CUDA.
+ * PS_ERR_UNSUPPORTED (npoints too large, or a device ordinal of 64 or more),
+ * PS_ERR_CUDA.
  */
 int ps_hartree_energy_noalloc(int dtype, long long npoints, double h, const void* rho,
                               const void* V, double* ehartree_dev, void* stream);

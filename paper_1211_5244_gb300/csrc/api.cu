@@ -265,8 +265,12 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
 int ps_plan_set_math(ps_plan p, int math_mode) {
   if (!p) return fail(PS_ERR_ARG, "plan is NULL");
   if (p->built) return fail(PS_ERR_ARG, "math mode must be set before ps_kernel_build");
-  if (math_mode != PS_MATH_CUDACORE && math_mode != PS_MATH_TF32X3)
+  if (math_mode != PS_MATH_CUDACORE && math_mode != PS_MATH_TF32X3 && math_mode != PS_MATH_BF16X3)
     return fail(PS_ERR_ARG, "unknown math mode %d", math_mode);
+  if (math_mode == PS_MATH_BF16X3)
+    return fail(PS_ERR_UNSUPPORTED,
+                "split-BF16 tensor-core stages are not built (three-term splits and six partial products "
+                "per stage cost more than the TF32x3 form, itself slower than the CUDA cores here)");
   if (math_mode == PS_MATH_TF32X3 && p->dtype != PS_F32)
     return fail(PS_ERR_UNSUPPORTED, "tensor-core math needs an FP32 plan");
   p->math = math_mode;

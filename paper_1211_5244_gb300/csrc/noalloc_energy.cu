@@ -94,9 +94,14 @@ extern "C" int ps_hartree_energy_noalloc(int dtype, long long npoints, double h,
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
+  if (e != cudaSuccess) {
     set_error("cudaGetDevice: %s", cudaGetErrorString(e));
     return PS_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kNaMaxDevices) {
+    set_error("device %d: ps_hartree_energy_noalloc keeps the scratch address of devices 0 .. %d only", dev,
+              kNaMaxDevices - 1);
+    return PS_ERR_UNSUPPORTED;
   }
   double* scratch = nullptr;
   if ((e = scratch_on_device(dev, &scratch)) != cudaSuccess) {

@@ -18,7 +18,7 @@ from . import build as _build
 
 PS_BC_PERIODIC, PS_BC_FREE = 0, 1
 PS_F32, PS_F64 = 0, 1
-PS_MATH_CUDACORE, PS_MATH_TF32X3 = 0, 1
+PS_MATH_CUDACORE, PS_MATH_TF32X3, PS_MATH_BF16X3 = 0, 1, 2
 STATUS = {0: "PS_OK", 1: "PS_ERR_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_ERR_NOT_BUILT",
           4: "PS_ERR_CUDA", 5: "PS_ERR_OOM", 6: "PS_ERR_TIMEOUT"}
 
@@ -128,7 +128,8 @@ class Plan:
         self._h = handle
         if L is not None:
             _check(lib.ps_plan_set_lengths(self._h, int(L[0]), int(L[1]), int(L[2])))
-        self.math = {"cudacore": PS_MATH_CUDACORE, "tf32x3": PS_MATH_TF32X3}[str(math).lower()]
+        self.math = {"cudacore": PS_MATH_CUDACORE, "tf32x3": PS_MATH_TF32X3,
+                     "bf16x3": PS_MATH_BF16X3}[str(math).lower()]
         _check(lib.ps_plan_set_math(self._h, self.math))
         if autotune:
             _check(lib.ps_plan_autotune(self._h, 5, _stream_handle(stream)))

@@ -75,6 +75,8 @@ def test_set_lengths_rules(lib):
     assert lib.ps_plan_set_math(p, 7) == 1
     assert lib.ps_plan_set_math(p, 0) == 0
     assert lib.ps_plan_set_math(p, 1) == 0  # tensor-core mode on an FP32 plan
+    assert lib.ps_plan_set_math(p, 2) == 2  # split-BF16 stages: declared, not built
+    assert b"BF16" in lib.ps_last_error()
     lib.ps_plan_destroy(p)
     rc, p = _create(lib, n=(10, 12, 7), bc=(0, 1, 1), dtype=1)
     assert rc == 0

@@ -165,35 +165,84 @@ def test_adjoint_is_the_symmetric_solve(torch_cuda, bc):
 
 
 @pytest.mark.parametrize("order", ["lpt", "rr"])
-def test_batched_matches_individual_solves(torch_cuda, monkeypatch, order):
-    """Each item of a batched solve equals its single solve, with the items
-    on the side streams longest first (the default) or round robin."""
+def test_batched_mixed_dtypes_match_oracle(torch_cuda, monkeypatch, order):
+    """Every item of a batched solve (FP32 and FP64 plans mixed, more items
+    than side streams) against the FP64 oracle, with the items on the side
+    streams longest first (the default) or round robin; each item also equals
+    its single solve bit for bit."""
     torch = torch_cuda
     from paper_1211_5244_gb300 import psolver
     if order == "rr":
         monkeypatch.setenv("PS_BATCH_ORDER", "rr")
-    shapes = synth.batched_shapes(36, 8, 40, seed=3)  # more items than side streams
-    plans, rhos = [], []
+    shapes = synth.batched_shapes(36, 8, 40, seed=3)
+    plans, rhos, dts = [], [], []
     for i, (n, bc) in enumerate(shapes):
         dtype = "f32" if i % 3 else "f64"
         plans.append(psolver.Plan(n, bc, 0.3, dtype))
         r = synth.gaussian_mixture(n, 0.3, 3, seed=i, noise=1e-3, subtract_mean="p" in bc)
-        rhos.append(torch.from_numpy(r.astype(np.float32 if dtype == "f32" else np.float64)).cuda())
+        rhos.append(torch.from_numpy(r.astype(_np_dtype(dtype))).cuda())
+        dts.append(dtype)
     Vs, Es = psolver.solve_batched(plans, rhos)
-    for p, r, V, E in zip(plans, rhos, Vs, Es):
+    torch.cuda.synchronize()
+    for (n, bc), dt, r, V, E, p in zip(shapes, dts, rhos, Vs, Es, plans):
+        _check(V.double().cpu().numpy(), float(E.item()), r.double().cpu().numpy(), bc, 0.3, dt)
         V1, E1 = p.solve(r)
         assert torch.equal(V, V1) and torch.equal(E, E1)
 
 
-def test_host_path_matches_device(torch_cuda):
+def test_batched_c4_workload_matches_oracle(torch_cuda):
+    """The uneven batch of the benchmark recipe: 64 FP32 problems, n ~ U{24..160}
+    per axis (primes such as 131, 137 and 157 among them), boundary conditions
+    drawn over free, wire, surface and periodic, autotuned plans, one batched
+    call; every item's V and E against the FP64 oracle."""
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    w = synth.WORKLOADS["batched64"]
+    shapes = synth.batched_shapes(w["count"], w["nmin"], w["nmax"], w["seed"])
+    assert {bc for _, bc in shapes} == {"fff", "pff", "ppf", "ppp"}
+    assert {131, 137, 157} <= {v for n, _ in shapes for v in n}
+    plans, rhos = [], []
+    for i, (n, bc) in enumerate(shapes):
+        plans.append(psolver.Plan(n, bc, w["h"], "f32", autotune=True))
+        r = synth.gaussian_mixture(n, w["h"], w["n_gauss"], w["seed"] + i, noise=w["noise"],
+                                   subtract_mean="p" in bc)
+        rhos.append(torch.from_numpy(r.astype(np.float32)).cuda())
+    Vs, Es = psolver.solve_batched(plans, rhos)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for (n, bc), r, V, E in zip(shapes, rhos, Vs, Es):
+        l2, mx, ee = _check(V.double().cpu().numpy(), float(E.item()), r.double().cpu().numpy(), bc, w["h"], "f32")
+        worst = max(worst, l2, mx, ee)
+    assert worst <= TOL["f32"]
+
+
+def test_host_path_matches_oracle(torch_cuda):
+    """ps_solve_host (pinned host buffers in and out) against the FP64 oracle,
+    and bit for bit against the device solve of the same plan."""
     torch = torch_cuda
     from paper_1211_5244_gb300 import psolver
     n = (40, 33, 27)
     plan = psolver.Plan(n, "fff", 0.3, "f32")
-    rho = torch.from_numpy(synth.gaussian_mixture(n, 0.3, 3, 4).astype(np.float32))
+    rho_np = synth.gaussian_mixture(n, 0.3, 3, 4).astype(np.float32)
+    rho = torch.from_numpy(rho_np)
     Vh, Eh = plan.solve_host(rho.pin_memory())
+    _check(Vh.double().numpy(), Eh, rho_np, "fff", 0.3, "f32")
     Vd, Ed = plan.solve(rho.cuda())
     assert torch.equal(Vh, Vd.cpu()) and Eh == float(Ed.item())
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_host_path_full_size_matches_oracle(torch_cuda, dtype):
+    """ps_solve_host on a 128^3 wire density (the specialised FP32 kernels, or
+    the FP64 generic ones) against the FP64 oracle."""
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    w = synth.WORKLOADS["bc128"]
+    rho_np = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"], noise=w["noise"],
+                                    subtract_mean=True).astype(_np_dtype(dtype))
+    plan = psolver.Plan(w["n"], "pff", w["h"], dtype)
+    Vh, Eh = plan.solve_host(torch.from_numpy(rho_np).pin_memory())
+    _check(Vh.double().numpy(), Eh, rho_np, "pff", w["h"], dtype)
 
 
 @pytest.mark.parametrize("name", ["free256_f32", "free512_f32"])
@@ -453,7 +502,10 @@ def test_autotuned_plan_matches_oracle(torch_cuda, n, bc, dtype):
     _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, dtype)
 
 
-def test_host_stream_matches_device_solves(torch_cuda):
+def test_host_stream_matches_oracle(torch_cuda):
+    """ps_solve_host_stream (uploads, solves and downloads of neighbouring
+    densities overlapped): every V and E against the FP64 oracle, and bit for
+    bit against the device solves of the same plan."""
     torch = torch_cuda
     from paper_1211_5244_gb300 import psolver
     n = (48, 40, 36)
@@ -462,9 +514,24 @@ def test_host_stream_matches_device_solves(torch_cuda):
             .pin_memory() for i in range(5)]
     Vh, Eh = plan.solve_host_stream(rhos)
     for r, v, e in zip(rhos, Vh, Eh):
+        _check(v.double().numpy(), e, r.numpy(), "pff", 0.3, "f32")
         Vd, Ed = plan.solve(r.cuda())
         assert torch.equal(v, Vd.cpu()) and e == float(Ed.item())
     assert plan.solve_host_stream([]) == ([], [])
+
+
+def test_full_grid_headline_matches_oracle(torch_cuda):
+    """The benchmark workload itself (256^3 free FP32, padded 512^3, the launch
+    configuration bench.py times): the whole V element by element and E
+    against the FP64 oracle's full solve."""
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    w = synth.WORKLOADS["free256_f32"]
+    rho32 = synth.gaussian_mixture(w["n"], w["h"], w["n_gauss"], w["seed"], noise=w["noise"]).astype(np.float32)
+    plan = psolver.Plan(w["n"], "fff", w["h"], "f32")
+    V, E = plan.solve(torch.from_numpy(rho32).cuda())
+    torch.cuda.synchronize()
+    _check(V.double().cpu().numpy(), float(E.item()), rho32, "fff", w["h"], "f32")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

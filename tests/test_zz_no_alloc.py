@@ -31,8 +31,9 @@ def _solve(torch, n, bc, dtype, seed):
     return rho_t, V, float(E.item())
 
 
-def _noalloc(lib, torch, rho, V, h):
-    E = torch.full((), float("nan"), dtype=torch.float64, device=rho.device)
+def _noalloc(lib, torch, rho, V, h, E=None):
+    if E is None:
+        E = torch.full((), float("nan"), dtype=torch.float64, device=rho.device)
     dtype = 0 if rho.dtype == torch.float32 else 1
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = lib.ps_hartree_energy_noalloc(dtype, rho.numel(), h, ctypes.c_void_p(rho.data_ptr()),
@@ -64,3 +65,21 @@ def test_noalloc_rejects_grids_beyond_its_scratch(gpu_lib):
     assert gpu_lib.ps_hartree_energy_noalloc(0, 0, 0.3, ctypes.c_void_p(x.data_ptr()),
                                              ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(E.data_ptr()),
                                              None) == 1
+
+
+def test_noalloc_call_leaves_device_memory_unchanged(gpu_lib):
+    """The defining property: once the first call on the device has looked up
+    the scratch address (and the kernel's module is loaded), a call takes no
+    device memory. Free memory is read before and after a second call on the
+    same, already allocated tensors."""
+    import torch
+    rho, V, E_solve = _solve(torch, (64, 48, 40), "fff", "f32", seed=5)
+    E = torch.empty((), dtype=torch.float64, device="cuda")
+    _noalloc(gpu_lib, torch, rho, V, 0.3, E)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    e2 = _noalloc(gpu_lib, torch, rho, V, 0.3, E)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert abs(e2 - E_solve) <= TOL["f32"] * abs(E_solve)
