@@ -128,7 +128,9 @@ def _pass_flops(info):
 
 
 def _pass_bytes(info, esz):
-    """Algorithmic HBM bytes of each pass (one launch each)."""
+    """Algorithmic HBM bytes of each pass (one launch each). Where the x and y
+    passes are fused (info.fused), the forward kernel moves rho in and B out
+    and the inverse B in and V out; the fused-away passes move nothing."""
     n1, n2, n3 = info.n
     L1, L2, L3 = info.L
     c = info.c
@@ -136,6 +138,8 @@ def _pass_bytes(info, esz):
     A = c * n2 * n3 * 2 * esz          # complex spectrum after the x pass
     B = c * L2 * n3 * 2 * esz          # after the y pass
     Koct = c * (L2 // 2 + 1) * (L3 // 2 + 1) * esz
+    if getattr(info, "fused", 0):
+        return [N * esz + B, 0, 2 * B + Koct, B + N * esz, 0]
     return [N * esz + A, A + B, 2 * B + Koct, B + A, A + N * esz]
 
 
@@ -552,12 +556,20 @@ def _rooflines(info, pass_ms, dtype, workload, math_mode):
     esz = 4 if dtype == "f32" else 8
     pbytes = _pass_bytes(info, esz)
     pflops = _pass_flops(info)
+    if getattr(info, "fused", 0):  # the fused kernels do the work of two passes each
+        pflops = [pflops[0] + pflops[1], 0.0, pflops[2], pflops[3] + pflops[4], 0.0]
     dom = max(range(5), key=lambda k: pass_ms[k])
-    passes = {PASS_NAMES[k]: {"ms": pass_ms[k], "alg_bytes": pbytes[k],
-                              "GB/s": pbytes[k] / (pass_ms[k] / 1e3) / 1e9,
-                              "frac_hbm": pbytes[k] / (pass_ms[k] / 1e3) / 1e9 / peak,
-                              "nominal_flops": pflops[k],
-                              "TFLOP/s": pflops[k] / (pass_ms[k] / 1e3) / 1e12} for k in range(5)}
+    fused = getattr(info, "fused", 0)
+    passes = {}
+    for k in range(5):
+        if fused & (1 << k):
+            passes[PASS_NAMES[k]] = {"fused_into": PASS_NAMES[k - 1 if k == 1 else 3], "ms": pass_ms[k]}
+            continue
+        passes[PASS_NAMES[k]] = {"ms": pass_ms[k], "alg_bytes": pbytes[k],
+                                 "GB/s": pbytes[k] / (pass_ms[k] / 1e3) / 1e9,
+                                 "frac_hbm": pbytes[k] / (pass_ms[k] / 1e3) / 1e9 / peak,
+                                 "nominal_flops": pflops[k],
+                                 "TFLOP/s": pflops[k] / (pass_ms[k] / 1e3) / 1e12}
     if dtype == "f32":
         achieved = pbytes[dom] / (pass_ms[dom] / 1e3) / 1e9
         tr = TRAFFIC.get((PASS_NAMES[dom], workload))

@@ -97,14 +97,26 @@ typedef struct {
                                3 S_x S_y S_z (paper_points / paper_full_points is
                                7/12 for free and wire, 2/3 for surface BCs)      */
   double alg_bytes;         /* HBM bytes one solve must move in this design:
-                               rho in, V out, four intermediate write+read pairs,
+                               rho in, V out, the intermediate write+read pairs
+                               (four; two where the x and y passes are fused),
                                and one read of the stored K^F octant            */
   size_t workspace_bytes;   /* device bytes the plan allocates at build          */
   int launches;             /* kernels one ps_solve launches (0 before build)    */
   int tensor_passes;        /* bit k set: pass k (0 fwd x .. 4 inv x) runs on the
                                tensor cores (0 before build)                     */
   int blocks[5];            /* CTAs launched per pass by its specialised kernel
-                               (0 before build and where the generic kernel runs) */
+                               (0 before build and where the generic kernel runs;
+                               a fused pass reports the CTAs of its kernel)      */
+  int fused;                /* bit 1: the forward y pass runs inside the forward x
+                               kernel, bit 4: the inverse x pass inside the
+                               inverse y kernel (thread-block clusters exchange
+                               each z plane through distributed shared memory;
+                               used when rho and V are 16-byte aligned)         */
+  int schedule[5];          /* kernel schedule requested (0 = default): generic
+                               lines per tile, generic radix split (1: radix 4
+                               only), lines per tile of the persistent packed z
+                               kernel, y kernel form (1 unpacked persistent, 2
+                               non-persistent), fused x/y passes (1)            */
 } ps_plan_info;
 
 /*
@@ -131,15 +143,21 @@ int ps_plan_create(int n1, int n2, int n3, double h, int bc_x, int bc_y, int bc_
 int ps_plan_set_lengths(ps_plan plan, int L1, int L2, int L3);
 
 /*
- * ps_plan_autotune -- choose the padded lengths of the free axes by timing.
- * Any L >= 2n - 1 gives the same physical result (§2); the candidates are the
- * paper's 2n and the smallest lengths >= 2n - 1 made of the factors {2},
- * {2, 3} and {2, 3, 5, 7} (a power of two selects the register-resident
- * kernels). One trial plan per candidate is built on the current device and
- * `reps` solves of it are timed on `stream` (reps < 1 means 5); the fastest
- * lengths are set on `plan` (not built). Results are cached per geometry and
- * device in memory and, when the environment variable PS_TUNE_CACHE names a
- * file, in that file. Must precede ps_kernel_build; synchronises `stream`.
+ * ps_plan_autotune -- choose the padded lengths of the free axes and the
+ * kernel schedule by timing. Any L >= 2n - 1 gives the same physical result
+ * (§2); the candidates are the paper's 2n and the smallest lengths >= 2n - 1
+ * made of the factors {2}, {2, 3} and {2, 3, 5, 7} (a power of two selects
+ * the register-resident kernels). Then, at the fastest lengths, each schedule
+ * choice that applies to the plan is timed in turn and kept if faster: the
+ * lines per tile of the generic passes, their radix split (radix 8 first or
+ * radix 4 only), the lines per tile of the persistent packed z kernel, the y
+ * kernel form (packed persistent, unpacked persistent, non-persistent) and
+ * the fused x/y passes (see ps_plan_info.fused). One trial plan per candidate
+ * is built on the current device and `reps` solves of it are timed on
+ * `stream` (reps < 1 means 5); the choice is set on `plan` (not built; see
+ * ps_plan_info.schedule). Results are cached per geometry and device in
+ * memory and, when the environment variable PS_TUNE_CACHE names a file, in
+ * that file. Must precede ps_kernel_build; synchronises `stream`.
  * Errors: PS_ERR_ARG (plan NULL or built), PS_ERR_OOM, PS_ERR_CUDA.
  */
 int ps_plan_autotune(ps_plan plan, int reps, void* stream);
@@ -148,6 +166,20 @@ int ps_plan_autotune(ps_plan plan, int reps, void* stream);
  * otherwise, and for an unknown mode). PS_MATH_TF32X3 on an FP64 plan, and
  * PS_MATH_BF16X3 on any plan: PS_ERR_UNSUPPORTED. */
 int ps_plan_set_math(ps_plan plan, int math_mode);
+
+/*
+ * ps_plan_set_schedule -- choose the kernel schedule by hand before the build
+ * (ps_plan_autotune chooses it by timing). Every choice gives the same result
+ * up to rounding; a choice that does not apply to the plan's shapes is
+ * ignored. 0 keeps a field's default.
+ *   tile    most lines per tile of the generic passes: 0, 1, 2, 4, 8 or 16
+ *   radix   generic Stockham stages: 0 radix 8 first, 1 radix 4 and 2 only
+ *   ztk     lines per tile of the persistent packed z kernel: 0, 8 or 16
+ *   ykind   y kernels: 0 default, 1 unpacked persistent, 2 non-persistent
+ *   xy      1: fused x/y passes where the shapes have them (ps_plan_info.fused)
+ * Errors: PS_ERR_ARG (plan NULL or built, a value out of range).
+ */
+int ps_plan_set_schedule(ps_plan plan, int tile, int radix, int ztk, int ykind, int xy);
 
 /* ps_plan_query -- fill *info (host only; valid before and after the build). */
 int ps_plan_query(ps_plan plan, ps_plan_info* info);

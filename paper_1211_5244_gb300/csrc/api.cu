@@ -277,6 +277,23 @@ int ps_plan_set_math(ps_plan p, int math_mode) {
   return PS_OK;
 }
 
+int ps_plan_set_schedule(ps_plan p, int tile, int radix, int ztk, int ykind, int xy) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (p->built) return fail(PS_ERR_ARG, "the schedule must be set before ps_kernel_build");
+  if (tile < 0 || tile > 16 || (tile & (tile - 1)) != 0)
+    return fail(PS_ERR_ARG, "tile = %d: 0 or a power of two up to 16", tile);
+  if (radix != 0 && radix != 1) return fail(PS_ERR_ARG, "radix = %d: 0 or 1", radix);
+  if (ztk != 0 && ztk != 8 && ztk != 16) return fail(PS_ERR_ARG, "ztk = %d: 0, 8 or 16", ztk);
+  if (ykind < 0 || ykind > 2) return fail(PS_ERR_ARG, "ykind = %d: 0, 1 or 2", ykind);
+  if (xy != 0 && xy != 1) return fail(PS_ERR_ARG, "xy = %d: 0 or 1", xy);
+  p->gen_tk_max = tile;
+  p->radix_pref = radix;
+  p->z_tk = ztk;
+  p->y_kind = ykind;
+  p->xy_sched = xy;
+  return PS_OK;
+}
+
 int ps_plan_query(ps_plan p, ps_plan_info* info) {
   if (!p || !info) return fail(PS_ERR_ARG, "plan or info is NULL");
   memset(info, 0, sizeof *info);
@@ -303,13 +320,26 @@ int ps_plan_query(ps_plan p, ps_plan_info* info) {
   info->paper_points = (double)(n2 * n3 * L1) + (double)(L1 * n3 * L2) + (double)(L1 * L2 * L3);
   info->paper_full_points = 3.0 * (double)(L1 * L2 * L3);
   const double b = (double)p->esz;
-  info->alg_bytes = 2.0 * (double)(n1 * n2 * n3) * b + 8.0 * b * (double)(c * n3 * (n2 + L2)) +
+  const bool xyf = p->built && p->xyfuse;
+  // the fused x/y kernels never write or read A: the intermediate pairs of
+  // the x-transformed array drop out
+  info->alg_bytes = 2.0 * (double)(n1 * n2 * n3) * b + 8.0 * b * (double)(c * n3 * ((xyf ? 0 : n2) + L2)) +
                     b * (double)c * (double)(p->H[1] + 1) * (double)(p->H[2] + 1);
   info->workspace_bytes = p->ws_bytes;
-  info->launches = p->built ? 5 : 0;
+  info->launches = p->built ? (xyf ? 3 : 5) : 0;
   info->tensor_passes = (p->built && p->tctab) ? (1 << 2) : 0;
+  info->fused = xyf ? ((1 << 1) | (1 << 4)) : 0;
+  info->schedule[0] = p->gen_tk_max;
+  info->schedule[1] = p->radix_pref;
+  info->schedule[2] = p->z_tk;
+  info->schedule[3] = p->y_kind;
+  info->schedule[4] = p->xy_sched;
   for (int k = 0; k < 5; ++k)
     info->blocks[k] = (p->built && p->cfg[k].fast) ? (int)(p->cfg[k].grid.x * p->cfg[k].grid.y) : 0;
+  if (xyf) {
+    info->blocks[0] = info->blocks[1] = (int)p->xyf[0].grid.x;
+    info->blocks[3] = info->blocks[4] = (int)p->xyf[1].grid.x;
+  }
   return PS_OK;
 }
 
@@ -321,6 +351,14 @@ int ps_kernel_build(ps_plan p, void* stream) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   p->device = dev;
+  if (p->radix_pref) {  // the schedule's radix split of the generic stages
+    const bool even1 = p->L[0] % 2 == 0;
+    p->st[0] = factorize(even1 ? p->L[0] / 2 : p->L[0], p->radix_pref);
+    p->st[1] = factorize(p->L[1], p->radix_pref);
+    p->st[2] = factorize(p->L[2], p->radix_pref);
+    for (int j = 0; j < 3; ++j)
+      if (p->blue[j].M) p->blue[j].st = factorize(p->blue[j].M, p->radix_pref);
+  }
   e = p->dtype == PS_F32 ? configure_passes<float>(p) : configure_passes<double>(p);
   if (e != cudaSuccess) return cuda_fail(e, "configure passes");
   const size_t csz = 2 * p->esz;

@@ -87,6 +87,7 @@ struct FastArgs {
                           // beyond nl are zero on input and not stored on output
   int rev;                // walk the z planes (y passes) or rows (x passes) from the last one:
                           // the previous pass wrote them last, so they are still in L2
+  const float2* tw1;      // fused x/y kernels: W_L1^k, k < L1 (set at launch)
 };
 
 struct PassCfg {
@@ -100,6 +101,7 @@ struct PassCfg {
   int fast;     // 1 if a compile-time specialised kernel runs this pass
   const void* fn;  // the specialised kernel
   dim3 grid, block;
+  int cluster;  // CTAs per thread-block cluster (0: launched without clusters)
   FastArgs fa;
 };
 
@@ -150,6 +152,15 @@ struct ps_plan_s {
   ps::Stages st[3];     // stages of the 1D transform per axis (x: length L1/2 if L1 even)
   ps::BlueArgs blue[3]; // Bluestein descriptors per axis (M = 0: off); device pointers owned
   ps::PassCfg cfg[5];
+  // fused x/y passes (thread-block clusters): xyf[0] runs passes 1 and 2,
+  // xyf[1] passes 4 and 5, when xyfuse is set and rho and V are 16-byte aligned
+  int xyfuse;
+  ps::PassCfg xyf[2];
+  // kernel schedule (chosen by ps_plan_autotune; 0 = the default choice):
+  int xy_sched;    // 1: fused x/y passes where they apply
+  int z_tk;        // lines per tile of the persistent packed z kernel (8 or 16)
+  int y_kind;      // y passes: 1 unpacked persistent kernels, 2 non-persistent ones
+  int radix_pref;  // generic Stockham stages: 0 radix 8 first, 1 radix 4 and 2 only
   // per-pass timing (ps_plan_set_profiling): 6 events per recorded solve
   bool profiling;
   std::vector<cudaEvent_t> events;
@@ -161,8 +172,8 @@ namespace ps {
 // Error reporting (thread-local message), defined in api.cu.
 void set_error(const char* fmt, ...);
 
-// Radix factorisation used by the generic kernels.
-Stages factorize(int N);
+// Radix factorisation used by the generic kernels (pref 1: no radix-8 stages).
+Stages factorize(int N, int pref = 0);
 
 // Launchers (defined in passes.cu / kernel_build.cu). They only enqueue.
 template <typename T>

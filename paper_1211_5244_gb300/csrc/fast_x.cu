@@ -11,6 +11,7 @@
 // positions. T lanes own one row (contiguous 8-byte elements), so loads and
 // stores are coalesced along the row. With zero padding (n1 = M), inputs
 // z[m] with m >= M/2 are zero and outputs there are never formed.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 
@@ -250,9 +251,8 @@ template <int P, int Q, int TR>
 static const void* pick_x(int kind, bool half) {
   if (kind == 0) return half ? (const void*)k_x_r2c<P, Q, TR, true> : (const void*)k_x_r2c<P, Q, TR, false>;
   // P = Q: the untangling by shuffles (three CTAs per SM; 44.4 against 45.7 us
-  // at 256^3); PS_XC2R=smem keeps the shared-memory form
-  const char* v = getenv("PS_XC2R");
-  if (P == Q && !(v && strcmp(v, "smem") == 0))
+  // at 256^3 for the shared-memory form)
+  if constexpr (P == Q)
     return half ? (const void*)k_x_c2r<P, Q, TR, true, true> : (const void*)k_x_c2r<P, Q, TR, false, true>;
   return half ? (const void*)k_x_c2r<P, Q, TR, true> : (const void*)k_x_c2r<P, Q, TR, false>;
 }
@@ -343,12 +343,12 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     // persistent prefetching kernels where they exist: the packed FP32x2 ones
     // at L2 = 512 (n2 = L2/2 or L2; at 256^3 forward 76.5 against 83 us for
     // the unpacked kernel, inverse 79.9 against 80.2 us), the unpacked ones at
-    // L2 = 256 and counts below L2/2. PS_YPASS=pipe: unpacked for both
-    // directions; PS_YPASS=plain: the non-persistent kernels
-    const char* yp = getenv("PS_YPASS");
-    const bool plain = yp && strcmp(yp, "plain") == 0;
+    // L2 = 256 and counts below L2/2. The plan's schedule y_kind = 1 takes the
+    // unpacked persistent kernels for both directions, y_kind = 2 the
+    // non-persistent ones.
+    const bool plain = p->y_kind == 2;
     const bool exact = 2 * n2 == L2 || n2 == L2;
-    const bool soa0 = !plain && exact && !(yp && strcmp(yp, "pipe") == 0);
+    const bool soa0 = !plain && exact && p->y_kind != 1;
     const bool soa1 = soa0;
     int tk0 = 16, tk1 = 16;  // lines per tile (kx columns) of the chosen kernels
     const void* f0 = soa0 ? ysoa_kernel(L2, 0, half, &threads0, &smem0) : nullptr;
@@ -398,6 +398,67 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       if ((e = set(P4, f1, grid1, threads1, smem1, inv)) != cudaSuccess) return e;
     }
   }
+  // fused x/y passes: thread-block clusters of 16 CTAs own one z plane and
+  // exchange its x-transformed rows through distributed shared memory, so
+  // array A is never written (L1 = 512 with n1 = 256 or 512, L2 = 512 with
+  // n2 = 256; they use the x twiddle matrix and the paired y twiddles of the
+  // kernels above). Measured slower than the separate passes at 256^3 (at most
+  // 14 clusters of 16 CTAs are resident, and each plane waits on a cluster
+  // barrier), so they run when the plan's schedule asks for them
+  // (ps_plan_set_schedule, or ps_plan_autotune where they win).
+  p->xyfuse = 0;
+  {
+    const bool allow = p->xy_sched == 1;
+    if (allow && L1 == 512 && (n1 == 256 || n1 == 512) && L2 == 512 && n2 == 256 && p->xP == 16 &&
+        (p->ysoa & 3) == 3 && p->cfg[P1].fast && p->cfg[P5].fast) {
+      bool ok = true;
+      for (int kind = 0; kind < 2 && ok; ++kind) {
+        int threads = 0, cl = 0;
+        size_t smem = 0;
+        const void* fn = xy_kernel(kind, n1 == 256, &threads, &smem, &cl);
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+          return e;
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+          return e;
+        PassCfg& cf = p->xyf[kind];
+        cf = PassCfg{};
+        cf.fast = 1;
+        cf.fn = fn;
+        cf.grid = dim3((unsigned)(n3 * cl));
+        cf.block = dim3(threads);
+        cf.smem = smem;
+        cf.cluster = cl;
+        cf.fa = base;
+        cf.fa.n1 = n1;
+        cf.fa.nrows = n2;  // rows per plane
+        if (kind == 0) {
+          cf.fa.dst_plane = (long long)L2 * ldc;
+          cf.fa.dst_elem = ldc;
+        } else {
+          cf.fa.src_plane = (long long)L2 * ldc;
+          cf.fa.src_elem = ldc;
+        }
+        // the GPU must be able to hold at least one such cluster
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = cf.grid;
+        lc.blockDim = cf.block;
+        lc.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &lc) != cudaSuccess || nclusters < 1) {
+          cudaGetLastError();  // clear a refusal: the separate passes run instead
+          ok = false;
+        }
+      }
+      p->xyfuse = ok ? 1 : 0;
+    }
+  }
   // z pass on the tensor cores (PS_MATH_TF32X3, L3 = 512): persistent, one
   // wave of resident CTAs over tiles of 8 kx lines
   p->tctab_floats = 0;
@@ -435,30 +496,23 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       return cudaSuccess;
     }
   }
-  // z pass: the persistent prefetching packed kernel where it exists (L3 = 512),
-  // else the packed kernel (L3 = 128), else the unpacked one. PS_ZPASS=soa or
-  // PS_ZPASS=strided selects a simpler kernel (diagnostics and comparisons).
+  // z pass: the persistent prefetching packed kernel where it exists (L3 = 128
+  // and 512), the persistent unpacked one at L3 = 256 and 1024, else the
+  // non-persistent unpacked one.
   if (pow2(L3) && (n3 <= L3 / 2 || n3 == L3)) {
     const bool half = n3 <= L3 / 2;
     int threads;
     size_t smem;
-    const char* zp = getenv("PS_ZPASS");
-    const bool allow_soa = !(zp && strcmp(zp, "strided") == 0);
-    // lines per tile: 8 for the persistent kernel (four CTAs of 42 KB per SM;
-    // at 256^3 228 us against 251 us for 16 lines and 280 us for 4), 16 for
-    // the non-persistent packed kernel; PS_ZTK=8/16 overrides (comparisons)
-    const char* ztk = getenv("PS_ZTK");
-    const int ztk_env = ztk ? atoi(ztk) : 0;
-    int pipe_tk = ztk_env == 16 ? 16 : 8;
-    const int zsoa_tk = ztk_env == 8 ? 8 : 16;
-    const bool pipe = allow_soa && !(zp && strcmp(zp, "soa") == 0);
-    const void* f = pipe ? zpipe_kernel(L3, half, &pipe_tk, &threads, &smem) : nullptr;
+    // lines per tile of the persistent packed kernel: 8 (four CTAs of 42 KB
+    // per SM; at 256^3 228 us against 251 us for 16 lines and 280 us for 4),
+    // or 16 where the plan's schedule z_tk asks for it
+    int pipe_tk = p->z_tk == 16 ? 16 : 8;
+    const void* f = zpipe_kernel(L3, half, &pipe_tk, &threads, &smem);
     bool persistent = f != nullptr;
-    if (!f && allow_soa) f = zsoa_kernel(L3, half, zsoa_tk, &threads, &smem);
     p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;
-    int ztile = persistent ? pipe_tk : zsoa_tk;
+    int ztile = pipe_tk;
     // L3 = 256 and 1024: the persistent unpacked kernel
-    if (!f && pipe && (f = zpipe_u_kernel(L3, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
+    if (!f && (f = zpipe_u_kernel(L3, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
     if (!f) f = strided_kernel(L3, 2, half, &threads, &smem, &ztile);
     if (f) {
       FastArgs z = base;
@@ -487,21 +541,17 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   return cudaSuccess;
 }
 
-cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, double* E, double escale,
-                        cudaStream_t s) {
-  PassCfg& cf = p->cfg[pass];
-  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
-  // x passes get the twiddle matrix in the K slot
-  const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
-  const void* tw = (pass == P3 && p->tctab) ? p->tctab
-                   : (pass == P3 && p->zsoa_T) ? p->tw4z
-                   : ((pass == P2 && (p->ysoa & 1)) || (pass == P4 && (p->ysoa & 2))) ? p->tw4y : p->tw[axis];
-  double* partials = p->partials;
-  unsigned* counter = p->counter;
-  void* args[] = {(void*)&src, (void*)&dst, (void*)&K, (void*)&tw, (void*)&cf.fa,
+namespace {
+
+// One launch of a specialised kernel: programmatic stream serialisation
+// (the kernel may start while the previous one drains; it waits for it before
+// touching memory; PS_PDL=0 off) and, for cluster kernels, the cluster shape.
+cudaError_t launch_cfg(const PassCfg& cf, const FastArgs& fa, const void* src, void* dst, const float* K,
+                       const void* tw, double* partials, unsigned* counter, double escale, double* E,
+                       cudaStream_t s) {
+  FastArgs a = fa;
+  void* args[] = {(void*)&src, (void*)&dst, (void*)&K, (void*)&tw, (void*)&a,
                   (void*)&partials, (void*)&counter, (void*)&escale, (void*)&E};
-  // programmatic dependent launch: the kernel may start while the previous one
-  // in the stream drains (it waits for it before touching memory); PS_PDL=0 off
   static const bool pdl = [] {
     const char* v = getenv("PS_PDL");
     return !(v && atoi(v) == 0);
@@ -511,12 +561,50 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
   lc.blockDim = cf.block;
   lc.dynamicSmemBytes = cf.smem;
   lc.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[3];
+  int na = 0;
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (cf.cluster > 0) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = (unsigned)cf.cluster;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+    // load-balancing placement of the clusters (fused forward 180 -> 171 us
+    // at 256^3 against the default spread policy)
+    attr[na].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    attr[na].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
+    ++na;
+  }
   lc.attrs = attr;
-  lc.numAttrs = pdl ? 1 : 0;
+  lc.numAttrs = na;
   return cudaLaunchKernelExC(&lc, cf.fn, args);
+}
+
+}  // namespace
+
+cudaError_t launch_xy(ps_plan_s* p, int kind, const void* src, void* dst, cudaStream_t s) {
+  const PassCfg& cf = p->xyf[kind];
+  FastArgs fa = cf.fa;
+  fa.tw1 = static_cast<const float2*>(p->tw[0]);
+  return launch_cfg(cf, fa, src, dst, static_cast<const float*>(p->twx), p->tw4y, nullptr, nullptr, 0.0, nullptr,
+                    s);
+}
+
+cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, double* E, double escale,
+                        cudaStream_t s) {
+  PassCfg& cf = p->cfg[pass];
+  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
+  // x passes get the twiddle matrix in the K slot
+  const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
+  const void* tw = (pass == P3 && p->tctab) ? p->tctab
+                   : (pass == P3 && p->zsoa_T) ? p->tw4z
+                   : ((pass == P2 && (p->ysoa & 1)) || (pass == P4 && (p->ysoa & 2))) ? p->tw4y : p->tw[axis];
+  return launch_cfg(cf, cf.fa, src, dst, K, tw, p->partials, p->counter, escale, E, s);
 }
 
 }  // namespace ps

@@ -61,114 +61,10 @@ __device__ __forceinline__ void dit_all(c2 (&z)[T], std::integer_sequence<int, B
 
 }  // namespace
 
-template <int T, bool HALF, int kTKs>
-__global__ void __launch_bounds__(kTKs * T, 512 / (kTKs * T))
-    k_zconv_soa(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
-                FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
-  pdl_wait();
-  constexpr int P = T, Q = 2 * T, L = P * Q;
-  constexpr int NA = HALF ? P / 2 : P;
-  extern __shared__ float4 sh4[];  // [T * P][kTKs]: slot (r, c) of line t at (r * P + c) * kTKs + t
-  const int t = threadIdx.x % kTKs;
-  const int j = threadIdx.x / kTKs;
-  const int kx = blockIdx.x * kTKs + t;
-  const bool valid = kx < a.c;
-  const int ky = paired_ky(blockIdx.y, a.L2);
-  float2* line = static_cast<float2*>(line_v) + ky * a.src_plane + kx;
-  const long long es = a.src_elem;
-
-  // step 1: P-point transforms of x[b + Q a] for the lanes b = j and b = j + T
-  c2 y[P];
-#pragma unroll
-  for (int aa = 0; aa < P; ++aa) {
-    y[aa] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    if (aa < NA && valid) {
-      const int r0 = j + Q * aa, r1 = r0 + T;
-      const float2 u0 = r0 < a.nl ? line[(long long)r0 * es] : make_float2(0.f, 0.f);
-      const float2 u1 = r1 < a.nl ? line[(long long)r1 * es] : make_float2(0.f, 0.f);
-      y[aa] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
-    }
-  }
-  soa::dft2<P, -1, HALF>(y);
-#pragma unroll
-  for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], __ldg(&tw4[j * P + k1]));
-#pragma unroll
-  for (int k1 = 0; k1 < P; ++k1) sh4[(j * P + k1) * kTKs + t] = pack(y[k1]);
-  __syncthreads();
-
-  // step 3 for k1 = j: lanes (Y_b, Y_{b+T}) -> radix-2 across lanes -> two T-point
-  // transforms: z[m] = (X[j + P 2m], X[j + P (2m+1)])
-  c2 z[T];
-#pragma unroll
-  for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * kTKs + t]);
-  dif_all<T>(z, std::make_integer_sequence<int, T>{});
-  soa::dft2<T, -1, false>(z);
-
-  // V^F = K^F rho^F on the even octant; energy sum w(kx) K |rho^F|^2
-  const int kyo = min(ky, a.L2 - ky);
-  const float* Kp = K + (long long)kyo * a.ldk + kx;
-  float2 e2 = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int m = 0; m < T; ++m) {
-    const int kz0 = j + P * 2 * m, kz1 = kz0 + P;
-    const int o0 = kz0 <= L / 2 ? kz0 : L - kz0, o1 = kz1 <= L / 2 ? kz1 : L - kz1;
-    const float2 kk = valid ? make_float2(__ldg(&Kp[(long long)o0 * a.kz_stride]), __ldg(&Kp[(long long)o1 * a.kz_stride]))
-                            : make_float2(0.f, 0.f);
-    const float2 p2 = soa::fma2(z[m].re, z[m].re, soa::mul2(z[m].im, z[m].im));
-    e2 = soa::fma2(kk, p2, e2);
-    z[m] = {soa::mul2(z[m].re, kk), soa::mul2(z[m].im, kk)};
-  }
-  float eacc = (e2.x + e2.y) * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
-
-  // inverse step A for k1 = j: two T-point inverses (even / odd k2), radix-2
-  // across lanes -> (Z_b, Z_{b+T}); step B: conjugate twiddles
-  soa::dft2<T, 1, false>(z);
-  dit_all<T>(z, std::make_integer_sequence<int, T>{});
-#pragma unroll
-  for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], __ldg(&tw4[b * P + j]));
-  __syncthreads();  // every thread has read the forward exchange
-#pragma unroll
-  for (int b = 0; b < T; ++b) sh4[(b * P + j) * kTKs + t] = pack(z[b]);
-  __syncthreads();
-
-  // step C for the lanes b = j and b = j + T: P-point inverses over k1
-#pragma unroll
-  for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[(j * P + k1) * kTKs + t]);
-  soa::dft2<P, 1, false, HALF>(y);  // only the NA stored outputs when HALF
-  if (valid) {
-#pragma unroll
-    for (int aa = 0; aa < NA; ++aa) {
-      const int r0 = j + Q * aa, r1 = r0 + T;
-      if (r0 < a.nl) line[(long long)r0 * es] = make_float2(y[aa].re.x, y[aa].im.x);
-      if (r1 < a.nl) line[(long long)r1 * es] = make_float2(y[aa].re.y, y[aa].im.y);
-    }
-  }
-  if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
-}
-
-template <int T, int TK>
-static const void* pick_zsoa(bool half) {
-  return half ? (const void*)k_zconv_soa<T, true, TK> : (const void*)k_zconv_soa<T, false, TK>;
-}
-
-const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem) {
-  const void* fn = nullptr;
-  int T = 0;
-  if (tk != 8 && tk != 16) return nullptr;
-  switch (L) {
-    case 128: fn = tk == 8 ? pick_zsoa<8, 8>(half) : pick_zsoa<8, 16>(half); T = 8; break;
-    case 512: fn = tk == 8 ? pick_zsoa<16, 8>(half) : pick_zsoa<16, 16>(half); T = 16; break;
-    default: return nullptr;
-  }
-  *threads = tk * T;
-  *smem = (size_t)T * T * tk * sizeof(float4);
-  return fn;
-}
-
 // ---------------------------------------------------------------- pipelined
 
-// Persistent version of k_zconv_soa with TK lines per tile (8 by default, 16
-// for comparisons): each CTA walks tiles (kx tile fastest, then the paired ky
+// Persistent z pass with TK lines per tile (8 by default, 16 as a schedule
+// choice of the autotuner): each CTA walks tiles (kx tile fastest, then the paired ky
 // rows) and copies the next tile's n3 input rows and its K^F octant slice into
 // shared memory with cp.async while it computes the current tile, so the
 // global-load latency of one tile overlaps the arithmetic of the previous one.

@@ -58,10 +58,6 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 // Returns the kernel for an x pass (real length 2M): kind 0 R2C, 1 C2R.
 const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, size_t* smem);
 
-// The packed FP32x2 z-pass kernel for L3 = 2 T^2 (T = 8, 16) with tk lines
-// per CTA (8 or 16), or nullptr.
-const void* zsoa_kernel(int L, bool half, int tk, int* threads, size_t* smem);
-
 // The persistent packed y-pass kernels (L2 = 512), or nullptr.
 const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem);
 
@@ -80,11 +76,17 @@ const void* ztc_kernel(int L, bool half, int* threads, size_t* smem);
 size_t ztc_table_floats(bool half);
 void ztc_fill_table(bool half, float* out);
 
+// The fused x/y kernels (fast_xy.cu; kind 0 forward, 1 inverse) for L1 = 512
+// (half: n1 = 256, else 512) and L2 = 512 with n2 = 256, and their launch shape.
+const void* xy_kernel(int kind, bool half, int* threads, size_t* smem, int* cluster);
+
 // Fills p->cfg[k].fast / fn / grid / block / smem / fa for the passes covered.
 cudaError_t configure_fast_f32(ps_plan_s* p);
 
 // Launches pass `pass` with its specialised kernel.
 cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, double* E, double escale,
                         cudaStream_t s);
+// Launches the fused forward (kind 0: rho -> B) or inverse (kind 1: B -> V) x/y kernel.
+cudaError_t launch_xy(ps_plan_s* p, int kind, const void* src, void* dst, cudaStream_t s);
 
 }  // namespace ps

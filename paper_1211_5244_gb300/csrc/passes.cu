@@ -358,18 +358,24 @@ template cudaError_t launch_vjp_axpy<double>(ps_plan_s*, double*, const double*,
 
 // ---------------------------------------------------------------- host side
 
-Stages factorize(int N) {
+Stages factorize(int N, int pref) {
   Stages s;
   s.n = 0;
   int m = N;
   int twos = 0;
   while (m % 2 == 0) { m /= 2; ++twos; }
-  // powers of two: as many radix-8 stages as possible, the rest as 4 or 2
-  int eights = twos / 3, rest = twos % 3;
-  if (rest == 1 && eights > 0) { --eights; s.R[s.n++] = 4; s.R[s.n++] = 4; rest = 0; }
-  for (int i = 0; i < eights; ++i) s.R[s.n++] = 8;
-  if (rest == 1) s.R[s.n++] = 2;
-  if (rest == 2) s.R[s.n++] = 4;
+  if (pref == 1) {
+    // radix 4 (and one radix 2 for an odd power): more, cheaper stages
+    for (int i = 0; i < twos / 2; ++i) s.R[s.n++] = 4;
+    if (twos % 2) s.R[s.n++] = 2;
+  } else {
+    // powers of two: as many radix-8 stages as possible, the rest as 4 or 2
+    int eights = twos / 3, rest = twos % 3;
+    if (rest == 1 && eights > 0) { --eights; s.R[s.n++] = 4; s.R[s.n++] = 4; rest = 0; }
+    for (int i = 0; i < eights; ++i) s.R[s.n++] = 8;
+    if (rest == 1) s.R[s.n++] = 2;
+    if (rest == 2) s.R[s.n++] = 4;
+  }
   for (int p = 3; m > 1; p += 2) {
     while (m % p == 0) { s.R[s.n++] = p; m /= p; }
     if (p * p > m && m > 1) { s.R[s.n++] = m; m = 1; }
@@ -445,15 +451,10 @@ template <typename T>
 cudaError_t configure_passes(ps_plan_s* p) {
   using C = cpx<T>;
   const size_t budget = 200 * 1024;
-  // most lines per generic tile: the plan's (set by the autotuner), else
-  // PS_GEN_TK (a power of two <= 16; comparisons and tests), else 16 / 8
+  // most lines per generic tile: the plan's schedule (ps_plan_set_schedule or
+  // the autotuner), else 16 (FP32) / 8 (FP64)
   int tk0 = sizeof(T) == 4 ? 16 : 8;
-  if (p->gen_tk_max > 0) {
-    tk0 = p->gen_tk_max;
-  } else if (const char* g = getenv("PS_GEN_TK")) {
-    const int v = atoi(g);
-    if (v >= 1 && v <= 16 && (v & (v - 1)) == 0) tk0 = v;
-  }
+  if (p->gen_tk_max > 0) tk0 = p->gen_tk_max;
   const bool even1 = (p->L[0] % 2) == 0;
   const int N0 = even1 ? p->L[0] / 2 : p->L[0];
   (void)N0;
@@ -505,10 +506,15 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
 
   // the x-pass kernels read and write 8-byte pairs of reals
   const bool a8 = ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(V)) & 7) == 0;
+  // fused x/y passes: one kernel for P1 + P2 and one for P4 + P5 (A unused);
+  // the forward one copies rows of rho in 16-byte pieces
+  const bool xyf = p->xyfuse && ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(V)) & 15) == 0;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
   // P1
-  if (p->cfg[P1].fast && a8) {
+  if (xyf) {
+    if ((e = launch_xy(p, 0, rho, B, s)) != cudaSuccess) return e;
+  } else if (p->cfg[P1].fast && a8) {
     if ((e = launch_fast(p, P1, rho, A, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P1);
@@ -517,7 +523,9 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   }
   if (ev) cudaEventRecord(ev[1], s);
   // P2
-  if (p->cfg[P2].fast) {
+  if (xyf) {
+    // done by the fused kernel above
+  } else if (p->cfg[P2].fast) {
     if ((e = launch_fast(p, P2, A, B, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P2);
@@ -536,7 +544,9 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   }
   if (ev) cudaEventRecord(ev[3], s);
   // P4
-  if (p->cfg[P4].fast) {
+  if (xyf) {
+    if ((e = launch_xy(p, 1, B, V, s)) != cudaSuccess) return e;
+  } else if (p->cfg[P4].fast) {
     if ((e = launch_fast(p, P4, B, A, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P4);
@@ -545,7 +555,9 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   }
   if (ev) cudaEventRecord(ev[4], s);
   // P5
-  if (p->cfg[P5].fast && a8) {
+  if (xyf) {
+    // done by the fused kernel above
+  } else if (p->cfg[P5].fast && a8) {
     if ((e = launch_fast(p, P5, A, V, nullptr, 0.0, s)) != cudaSuccess) return e;
   } else {
     GenArgs a = gen_args<T>(p, P5);

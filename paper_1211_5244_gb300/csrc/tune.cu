@@ -1,17 +1,23 @@
-// Autotuner for the padded lengths of the free axes and the tile width of the
-// generic passes.
+// Autotuner for the padded lengths of the free axes and the kernel schedule
+// of a plan.
 //
 // Any padded length L >= 2n - 1 of a free axis gives the same physical result
 // (§2), but the cost of the transforms depends on L: a power of two selects
 // the register-resident kernels, other smooth lengths use fewer or cheaper
 // radix stages than 2n when 2n has a large prime factor. The tuner times one
-// plan per candidate on the device and keeps the fastest; then, if the plan
-// runs any pass on the generic kernels, it times narrower generic tiles (at
-// most 8 and 4 lines instead of 16 for FP32, 4 and 2 instead of 8 for FP64:
-// more CTAs per line set, shorter per-CTA chains) at those lengths. Results
-// are kept in memory, and in a text file when PS_TUNE_CACHE names one (one
-// line per geometry: "n1 n2 n3 bc1 bc2 bc3 dtype sms L1 L2 L3 tile", tile 0
-// for the default).
+// trial plan per candidate on the device and keeps the fastest, then tunes
+// the schedule at those lengths one choice at a time (each kept only if it
+// is faster), among the choices that apply to the plan:
+//   tile    lines per tile of the generic passes (16 / 8 / 4 in FP32,
+//           8 / 4 / 2 in FP64: more CTAs per line set, shorter chains)
+//   radix   radix split of the generic Stockham stages (radix 8 first, or
+//           radix 4 and 2 only)
+//   ztk     lines per tile of the persistent packed z kernel (8 or 16)
+//   ykind   y kernels: packed persistent, unpacked persistent, non-persistent
+//   xy      the fused x/y passes (thread-block clusters) or the separate ones
+// Results are kept in memory, and in a text file when PS_TUNE_CACHE names one
+// (one line per geometry: "n1 n2 n3 bc1 bc2 bc3 mode sms L1 L2 L3 tile radix
+// ztk ykind xy", mode = dtype + 2 math, 0 for a default choice).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -25,6 +31,9 @@
 
 namespace ps {
 namespace {
+
+// a tuned choice: padded lengths and the schedule fields of the plan
+enum { kL1, kL2, kL3, kTile, kRadix, kZtk, kYkind, kXy, kFields };
 
 std::mutex g_tune_mu;
 std::map<std::string, std::vector<int>> g_tuned;
@@ -49,24 +58,49 @@ void load_file() {
   if (!path || !*path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  int n[3], bc[3], dt, sms, L[3], tile;
-  while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d", &n[0], &n[1], &n[2], &bc[0], &bc[1], &bc[2], &dt, &sms,
-                &L[0], &L[1], &L[2], &tile) == 12) {
+  char line[256];
+  while (fgets(line, sizeof line, f)) {
+    int n[3], bc[3], dt, sms, v[kFields] = {};
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &n[0], &n[1], &n[2], &bc[0],
+                           &bc[1], &bc[2], &dt, &sms, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7]);
+    if (got != 8 + kFields && got != 12) continue;  // 12: lengths and tile only
     char key[128];
     snprintf(key, sizeof key, "%d %d %d %d %d %d %d %d", n[0], n[1], n[2], bc[0], bc[1], bc[2], dt, sms);
-    g_tuned[key] = {L[0], L[1], L[2], tile};
+    g_tuned[key] = std::vector<int>(v, v + kFields);
   }
   fclose(f);
 }
 
-void append_file(const std::string& key, const int* L) {
+void append_file(const std::string& key, const std::vector<int>& v) {
   const char* path = getenv("PS_TUNE_CACHE");
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d\n", key.c_str(), L[0], L[1], L[2], L[3]);
+  fprintf(f, "%s", key.c_str());
+  for (int x : v) fprintf(f, " %d", x);
+  fprintf(f, "\n");
   fclose(f);
 }
+
+// applies a tuned choice to an unbuilt plan
+int apply_choice(ps_plan p, const std::vector<int>& v) {
+  const int rc = ps_plan_set_lengths(p, v[kL1], v[kL2], v[kL3]);
+  if (rc != PS_OK) return rc;
+  p->gen_tk_max = v[kTile];
+  p->radix_pref = v[kRadix];
+  p->z_tk = v[kZtk];
+  p->y_kind = v[kYkind];
+  p->xy_sched = v[kXy];
+  return PS_OK;
+}
+
+// What a built trial plan says about the choices that apply to it.
+struct Applies {
+  bool generic = false;  // some pass runs the generic kernels
+  bool zpipe = false;    // the z pass runs the persistent packed kernel
+  bool ypacked = false;  // the y passes run the packed persistent kernels
+  bool xy = false;       // the fused x/y kernels run
+};
 
 }  // namespace
 }  // namespace ps
@@ -92,40 +126,13 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
   }
   char keybuf[128];
   snprintf(keybuf, sizeof keybuf, "%d %d %d %d %d %d %d %d", p->n[0], p->n[1], p->n[2], p->bc[0], p->bc[1],
-           p->bc[2], p->dtype, sms);
+           p->bc[2], p->dtype + 2 * p->math, sms);
   const std::string key(keybuf);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     load_file();
     auto it = g_tuned.find(key);
-    if (it != g_tuned.end()) {
-      p->gen_tk_max = it->second[3];
-      return ps_plan_set_lengths(p, it->second[0], it->second[1], it->second[2]);
-    }
-  }
-
-  // candidate length triples: one rule applied to every free axis
-  static const int p2[] = {2}, p23[] = {2, 3}, p2357[] = {2, 3, 5, 7};
-  std::vector<std::vector<int>> cands;
-  for (int rule = 0; rule < 4; ++rule) {
-    std::vector<int> L(3);
-    bool ok = true;
-    for (int j = 0; j < 3; ++j) {
-      if (p->bc[j] == PS_BC_PERIODIC) {
-        L[j] = p->n[j];
-        continue;
-      }
-      const int lo = 2 * p->n[j] - 1;
-      switch (rule) {
-        case 0: L[j] = 2 * p->n[j]; break;
-        case 1: L[j] = next_smooth(lo, p2, 1); break;
-        case 2: L[j] = next_smooth(lo, p23, 2); break;
-        default: L[j] = next_smooth(lo, p2357, 4); break;
-      }
-      ok &= L[j] > 0 && L[j] <= kMaxLen;
-    }
-    L.push_back(0);  // default tile width
-    if (ok && std::find(cands.begin(), cands.end(), L) == cands.end()) cands.push_back(L);
+    if (it != g_tuned.end()) return apply_choice(p, it->second);
   }
 
   const size_t bytes = (size_t)p->n[0] * p->n[1] * p->n[2] * p->esz;
@@ -136,42 +143,109 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(rho, 0, bytes, s);
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
-  float best_ms = -1.f;
-  std::vector<int> best = {p->L[0], p->L[1], p->L[2], 0};
-  bool best_generic = false;  // the best plan runs a pass on the generic kernels
   int rc = PS_OK;
-  const size_t nlen = cands.size();
-  for (size_t c = 0; e == cudaSuccess && rc == PS_OK && c < cands.size(); ++c) {
-    if (c == nlen && best_generic) {
-      // second phase: narrower generic tiles at the best lengths
-      const int t0w = p->dtype == PS_F32 ? 16 : 8;
-      for (int tw = t0w / 2; tw >= t0w / 4; tw /= 2) cands.push_back({best[0], best[1], best[2], tw});
-      if (c == cands.size()) break;
-    } else if (c == nlen) {
-      break;
-    }
-    ps_plan trial = nullptr;
-    rc = ps_plan_create(p->n[0], p->n[1], p->n[2], p->h, p->bc[0], p->bc[1], p->bc[2], p->dtype, &trial);
-    if (rc == PS_OK) rc = ps_plan_set_lengths(trial, cands[c][0], cands[c][1], cands[c][2]);
-    if (rc == PS_OK) trial->gen_tk_max = cands[c][3];
-    if (rc == PS_OK) rc = ps_kernel_build(trial, stream);
-    for (int w = 0; rc == PS_OK && w < 2; ++w) rc = ps_solve(trial, rho, V, nullptr, stream);
-    if (rc == PS_OK) {
+
+  // builds a trial plan with choice v, times `reps` solves after two
+  // untimed ones; *ms < 0 if the choice is not valid for this plan
+  auto trial = [&](const std::vector<int>& v, float* ms, Applies* ap) {
+    *ms = -1.f;
+    ps_plan tp = nullptr;
+    int r = ps_plan_create(p->n[0], p->n[1], p->n[2], p->h, p->bc[0], p->bc[1], p->bc[2], p->dtype, &tp);
+    if (r == PS_OK) r = ps_plan_set_math(tp, p->math);
+    if (r == PS_OK) r = apply_choice(tp, v);
+    if (r == PS_OK) r = ps_kernel_build(tp, stream);
+    for (int w = 0; r == PS_OK && w < 2; ++w) r = ps_solve(tp, rho, V, nullptr, stream);
+    if (r == PS_OK) {
       e = cudaEventRecord(t0, s);
-      for (int r = 0; rc == PS_OK && r < reps; ++r) rc = ps_solve(trial, rho, V, nullptr, stream);
+      for (int k = 0; r == PS_OK && k < reps; ++k) r = ps_solve(tp, rho, V, nullptr, stream);
       if (e == cudaSuccess) e = cudaEventRecord(t1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-      float ms = 0.f;
-      if (e == cudaSuccess && rc == PS_OK) e = cudaEventElapsedTime(&ms, t0, t1);
-      if (e == cudaSuccess && rc == PS_OK && (best_ms < 0.f || ms < best_ms)) {
-        best_ms = ms;
-        best = cands[c];
-        best_generic = false;
-        for (int k = 0; k < 5; ++k) best_generic |= !trial->cfg[k].fast;
+      if (e == cudaSuccess && r == PS_OK) e = cudaEventElapsedTime(ms, t0, t1);
+      if (ap) {
+        for (int k = 0; k < 5; ++k) ap->generic |= !tp->cfg[k].fast;
+        ap->zpipe = tp->zsoa_T == 16 && tp->cfg[P3].fast && !tp->tctab;
+        ap->ypacked = tp->ysoa == 3;
+        ap->xy = tp->xyfuse != 0;
       }
     }
-    if (trial) ps_plan_destroy(trial);
+    if (tp) ps_plan_destroy(tp);
+    if (r == PS_ERR_UNSUPPORTED || r == PS_ERR_ARG) r = PS_OK;  // a choice that does not apply
+    return r;
+  };
+
+  // 1. padded lengths: one rule applied to every free axis
+  static const int p2[] = {2}, p23[] = {2, 3}, p2357[] = {2, 3, 5, 7};
+  std::vector<std::vector<int>> cands;
+  for (int rule = 0; rule < 4; ++rule) {
+    std::vector<int> v(kFields, 0);
+    bool ok = true;
+    for (int j = 0; j < 3; ++j) {
+      if (p->bc[j] == PS_BC_PERIODIC) {
+        v[j] = p->n[j];
+        continue;
+      }
+      const int lo = 2 * p->n[j] - 1;
+      switch (rule) {
+        case 0: v[j] = 2 * p->n[j]; break;
+        case 1: v[j] = next_smooth(lo, p2, 1); break;
+        case 2: v[j] = next_smooth(lo, p23, 2); break;
+        default: v[j] = next_smooth(lo, p2357, 4); break;
+      }
+      ok &= v[j] > 0 && v[j] <= kMaxLen;
+    }
+    if (ok && std::find(cands.begin(), cands.end(), v) == cands.end()) cands.push_back(v);
   }
+  float best_ms = -1.f;
+  std::vector<int> best = {p->L[0], p->L[1], p->L[2], 0, 0, 0, 0, 0};
+  Applies best_ap;
+  for (size_t c = 0; e == cudaSuccess && rc == PS_OK && c < cands.size(); ++c) {
+    float ms;
+    Applies ap;
+    rc = trial(cands[c], &ms, &ap);
+    if (rc == PS_OK && e == cudaSuccess && ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+      best_ms = ms;
+      best = cands[c];
+      best_ap = ap;
+    }
+  }
+  // 2. the schedule, one choice at a time at the best lengths
+  auto try_field = [&](int field, std::initializer_list<int> values) {
+    for (int val : values) {
+      if (e != cudaSuccess || rc != PS_OK || best_ms < 0.f) return;
+      std::vector<int> v = best;
+      v[field] = val;
+      float ms;
+      Applies ap;
+      rc = trial(v, &ms, &ap);
+      if (rc == PS_OK && e == cudaSuccess && ms >= 0.f && ms < best_ms) {
+        best_ms = ms;
+        best = v;
+        best_ap = ap;
+      }
+    }
+  };
+  const int t0w = p->dtype == PS_F32 ? 16 : 8;
+  if (best_ap.generic) {
+    try_field(kTile, {t0w / 2, t0w / 4});
+    try_field(kRadix, {1});
+  }
+  if (best_ap.zpipe) try_field(kZtk, {16});
+  if (best_ap.ypacked) try_field(kYkind, {1, 2});
+  {
+    // the fused x/y passes: only where the plan's shapes have them
+    std::vector<int> v = best;
+    v[kXy] = 1;
+    float ms;
+    Applies ap;
+    if (e == cudaSuccess && rc == PS_OK && best_ms >= 0.f) {
+      rc = trial(v, &ms, &ap);
+      if (rc == PS_OK && e == cudaSuccess && ap.xy && ms >= 0.f && ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+  }
+
   if (rho) cudaFree(rho);
   if (V) cudaFree(V);
   if (t0) cudaEventDestroy(t0);
@@ -184,8 +258,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned[key] = best;
-    append_file(key, best.data());
+    append_file(key, best);
   }
-  p->gen_tk_max = best[3];
-  return ps_plan_set_lengths(p, best[0], best[1], best[2]);
+  return apply_choice(p, best);
 }

@@ -39,7 +39,8 @@ class PlanInfo(ctypes.Structure):
         ("fft_points", ctypes.c_double), ("paper_points", ctypes.c_double),
         ("paper_full_points", ctypes.c_double), ("alg_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_int),
-        ("tensor_passes", ctypes.c_int), ("blocks", ctypes.c_int * 5),
+        ("tensor_passes", ctypes.c_int), ("blocks", ctypes.c_int * 5), ("fused", ctypes.c_int),
+        ("schedule", ctypes.c_int * 5),
     ]
 
 
@@ -61,6 +62,7 @@ def load_library():
         "ps_plan_create": [i, i, i, d, i, i, i, i, ctypes.POINTER(vp)],
         "ps_plan_set_lengths": [vp, i, i, i],
         "ps_plan_set_math": [vp, i],
+        "ps_plan_set_schedule": [vp, i, i, i, i, i],
         "ps_plan_autotune": [vp, i, vp],
         "ps_plan_query": [vp, ctypes.POINTER(PlanInfo)],
         "ps_kernel_build": [vp, vp],
@@ -115,7 +117,7 @@ class Plan:
     """One solve geometry: ps_plan_create (+ optional lengths) and ps_kernel_build."""
 
     def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None, autotune=False,
-                 math="cudacore"):
+                 math="cudacore", schedule=None):
         lib = load_library()
         self.n = tuple(int(v) for v in n)
         self.bc = str(bc).lower()
@@ -131,10 +133,17 @@ class Plan:
         self.math = {"cudacore": PS_MATH_CUDACORE, "tf32x3": PS_MATH_TF32X3,
                      "bf16x3": PS_MATH_BF16X3}[str(math).lower()]
         _check(lib.ps_plan_set_math(self._h, self.math))
+        if schedule is not None:
+            self.set_schedule(**schedule)
         if autotune:
             _check(lib.ps_plan_autotune(self._h, 5, _stream_handle(stream)))
         if build:
             self.build(stream)
+
+    def set_schedule(self, tile=0, radix=0, ztk=0, ykind=0, xy=0):
+        """ps_plan_set_schedule: the kernel schedule by hand (before the build)."""
+        _check(_lib.ps_plan_set_schedule(self._h, int(tile), int(radix), int(ztk), int(ykind), int(xy)))
+        return self
 
     # ------------------------------------------------------------ lifecycle
     def build(self, stream=None):

@@ -334,23 +334,60 @@ def test_parity_odd_n1_fast_x(torch_cuda, n, bc, L):
     _check(V, E, rho, bc, 0.25, "f32", L=L)
 
 
-@pytest.mark.parametrize("n,bc", [((64, 48, 40), "fff"), ((128, 20, 18), "pff"), ((512, 6, 5), "fff")])
-def test_parity_rho_v_not_8_byte_aligned(torch_cuda, n, bc):
+# The fused x/y kernels (thread-block clusters of 16 CTAs exchanging a z plane
+# through distributed shared memory): L1 = 512 with n1 = 256 (free x) or 512
+# (periodic x), L2 = 512 with n2 = 256 (free y); the z pass on every kind of
+# kernel (generic, register, packed, persistent, tensor-core).
+FUSED_CASES = [
+    ((256, 256, 5), "fff", "cudacore"),    # z generic (L3 = 10)
+    ((256, 256, 32), "fff", "cudacore"),   # z L3 = 64 register kernel
+    ((512, 256, 7), "pff", "cudacore"),    # periodic x (n1 = 512), z generic
+    ((256, 256, 24), "ffp", "cudacore"),   # periodic z
+    ((256, 256, 64), "fff", "cudacore"),   # z packed L3 = 128
+    ((256, 256, 256), "fff", "tf32x3"),    # the tensor-core z pass
+]
+
+
+@pytest.mark.parametrize("n,bc,math", FUSED_CASES)
+def test_parity_fused_xy(torch_cuda, n, bc, math):
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=43 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    # not the default schedule (the separate passes are faster)
+    plan = psolver.Plan(n, bc, 0.25, "f32", math=math, schedule={"xy": 1})
+    info = plan.info()
+    assert info.fused == (1 << 1) | (1 << 4) and info.launches == 3, (info.fused, info.launches)
+    r = torch.from_numpy(rho.astype(np.float32)).cuda()
+    V, E = plan.solve(r)
+    if math == "tf32x3":
+        plan.device_status()
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.25, "f32")
+    # repeatable: every CTA computes the same values on every call
+    V2 = torch.empty_like(V)
+    plan.solve(r, V2)
+    assert torch.equal(V, V2)
+
+
+@pytest.mark.parametrize("n,bc,off", [((64, 48, 40), "fff", 1), ((128, 20, 18), "pff", 1), ((512, 6, 5), "fff", 1),
+                                      ((256, 256, 6), "fff", 1), ((256, 256, 6), "fff", 2)])
+def test_parity_rho_v_not_8_byte_aligned(torch_cuda, n, bc, off):
     """rho and V starting 4 bytes past an 8-byte boundary (valid FP32
     pointers): the x passes, whose specialised kernels move pairs of reals,
-    run the generic kernels with their own launch configuration."""
+    run the generic kernels with their own launch configuration; 8 bytes past
+    a 16-byte boundary: the separate specialised x and y kernels run where the
+    fused ones (16-byte copies of rho) would."""
     from paper_1211_5244_gb300 import psolver
     torch = torch_cuda
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=31 + sum(n), noise=1e-3, subtract_mean="p" in bc)
     rho32 = rho.astype(np.float32)
     size = rho32.size
-    rbuf = torch.zeros(size + 1, dtype=torch.float32, device="cuda")
-    vbuf = torch.zeros(size + 1, dtype=torch.float32, device="cuda")
-    r = rbuf[1:].view(rho32.shape)
-    V = vbuf[1:].view(rho32.shape)
+    rbuf = torch.zeros(size + off, dtype=torch.float32, device="cuda")
+    vbuf = torch.zeros(size + off, dtype=torch.float32, device="cuda")
+    r = rbuf[off:].view(rho32.shape)
+    V = vbuf[off:].view(rho32.shape)
     r.copy_(torch.from_numpy(rho32))
-    assert r.data_ptr() % 8 == 4 and V.data_ptr() % 8 == 4
-    plan = psolver.Plan(n, bc, 0.25, "f32")
+    assert r.data_ptr() % 16 == 4 * off and V.data_ptr() % 16 == 4 * off
+    plan = psolver.Plan(n, bc, 0.25, "f32", schedule={"xy": 1})  # fused kernels where they apply must step aside
     assert plan.info().blocks[0] > 0  # the plan has the specialised x kernels
     _, E = plan.solve(r, V)
     torch.cuda.synchronize()
@@ -502,6 +539,37 @@ def test_autotuned_plan_matches_oracle(torch_cuda, n, bc, dtype):
     _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, dtype)
 
 
+@pytest.mark.parametrize("n,bc", [((256, 256, 16), "fff"), ((24, 40, 256), "pff"), ((50, 33, 20), "ppp")])
+def test_autotuned_schedule_matches_oracle(torch_cuda, n, bc):
+    """Plans whose autotuned schedule has choices to make: the fused x/y
+    passes (256 x 256 planes), the tile width of the persistent packed z kernel
+    and the y kernel form (L3 = 512), the generic tile width and radix split
+    (periodic lengths 50, 33, 20); the chosen plan against the FP64 oracle."""
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    plan = psolver.Plan(n, bc, 0.3, "f32", autotune=True)
+    sched = list(plan.info().schedule)
+    assert sched[1] in (0, 1) and sched[2] in (0, 16) and sched[3] in (0, 1, 2) and sched[4] in (0, 1), sched
+    rho = synth.gaussian_mixture(n, 0.3, 4, seed=5, noise=1e-3, subtract_mean="p" in bc)
+    V, E = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, "f32")
+
+
+@pytest.mark.parametrize("radix", [1])
+def test_radix4_schedule_matches_oracle(torch_cuda, monkeypatch, radix):
+    """The radix-4 split of the generic Stockham stages, forced on plans of
+    several generic lengths (powers of two with odd exponents, 2^k 3, a
+    Bluestein length), against the FP64 oracle."""
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    for n, bc, dtype in (((40, 24, 20), "ppp", "f32"), ((17, 12, 24), "fpf", "f64"), ((96, 6, 10), "pff", "f32")):
+        plan = psolver.Plan(n, bc, 0.3, dtype, schedule={"radix": radix})
+        assert plan.info().schedule[1] == radix
+        rho = synth.gaussian_mixture(n, 0.3, 3, seed=9, noise=1e-3, subtract_mean="p" in bc)
+        V, E = plan.solve(torch.from_numpy(rho.astype(_np_dtype(dtype))).cuda())
+        _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, dtype)
+
+
 def test_host_stream_matches_oracle(torch_cuda):
     """ps_solve_host_stream (uploads, solves and downloads of neighbouring
     densities overlapped): every V and E against the FP64 oracle, and bit for
@@ -559,27 +627,30 @@ def test_parity_maximum_lengths(torch_cuda, n, bc, dtype):
     _check(V, E, rho, bc, 0.2, dtype)
 
 
-# The kernel alternatives behind the environment switches (each measured
-# slower at 256^3 than the default, kept for comparisons) against the oracle.
-SWITCHES = [
-    {"PS_ZTK": "16"},                        # 16 lines per z tile, separate input stage
-    {"PS_YPASS": "pipe"},                    # unpacked persistent y kernels
-    {"PS_YPASS": "plain", "PS_ZPASS": "soa"},  # non-persistent y and z kernels
-    {"PS_ZPASS": "strided"},                 # unpacked z kernel
-    {"PS_XC2R": "smem"},                     # C2R untangling through shared memory
-    {"PS_L2ORDER": "0"},                     # every pass in forward plane order
-    {"PS_GEN_TK": "4"},                      # generic passes: at most 4 lines per tile
-    {"PS_GEN_TK": "1"},                      # generic passes: one line per tile
-    {"PS_BLUE_M": "min"},                    # smallest 5-smooth Bluestein length (137: 288, not 280)
+# The schedule choices of ps_plan_set_schedule (which the autotuner picks
+# among by timing) and the measurement switches, against the oracle.
+SCHEDULES = [
+    ({"ztk": 16}, {}),                   # 16 lines per z tile, separate input stage
+    ({"ykind": 1}, {}),                  # unpacked persistent y kernels
+    ({"ykind": 2}, {}),                  # non-persistent y kernels
+    ({"tile": 4}, {}),                   # generic passes: at most 4 lines per tile
+    ({"tile": 1, "radix": 1}, {}),       # one line per tile, radix-4 stages
+    ({"xy": 1}, {}),                     # fused x/y kernels where they apply (256 x 256 planes)
+    ({}, {"PS_L2ORDER": "0"}),           # every pass in forward plane order
+    ({}, {"PS_BLUE_M": "min"}),          # smallest 5-smooth Bluestein length (137: 288, not 280)
 ]
 
 
-@pytest.mark.parametrize("env", SWITCHES, ids=lambda e: ",".join(f"{k}={v}" for k, v in e.items()))
+@pytest.mark.parametrize("sched,env", SCHEDULES,
+                         ids=lambda e: ",".join(f"{k}={v}" for k, v in e.items()) or "-")
 @pytest.mark.parametrize("n,bc", [((64, 48, 256), "fff"), ((20, 17, 256), "pff"), ((30, 256, 40), "fff"),
-                                  ((137, 12, 10), "pff")])
-def test_parity_kernel_switches(torch_cuda, monkeypatch, env, n, bc):
+                                  ((137, 12, 10), "pff"), ((256, 256, 16), "fff")])
+def test_parity_schedules(torch_cuda, monkeypatch, sched, env, n, bc):
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=17 + sum(n), noise=1e-3, subtract_mean="p" in bc)
-    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
-    _check(V, E, rho, bc, 0.25, "f32")
+    plan = psolver.Plan(n, bc, 0.25, "f32", schedule=sched)
+    V, E = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.25, "f32")
