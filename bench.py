@@ -94,18 +94,18 @@ def _paper_unfused_bytes(info, esz):
     (+spread) and 1DFFT_Y, transpose(+spread) and 1DFFT_Z, the kernel
     multiplication (K^F at the full half-spectrum size), and the mirror steps
     of the inverse with compactions. Context for the five fused passes."""
-    n1, n2, n3 = info.n
-    S1, S2, S3 = info.L
-    free = [b == 1 for b in info.bc]
+    n, S = list(info.n), list(info.L)
+    a, b, c3 = list(info.order)         # the steps in processing order
+    free = [bc == 1 for bc in info.bc]
     c = info.c
-    N = n1 * n2 * n3
+    N = n[0] * n[1] * n[2]
     r, cx = esz, 2 * esz
-    xrows = S1 * n2 * n3 * r            # padded real rows
-    A = c * n2 * n3 * cx                # after the x transform
-    B = c * S2 * n3 * cx                # after the y transform
-    Z = c * S2 * S3 * cx                # full half spectrum
-    one_way = ((N * r + xrows) if free[0] else 0) + (xrows + A) + (A + B) + 2 * B + (B + Z) + 2 * Z
-    multiply = 2 * Z + c * S2 * S3 * r
+    xrows = S[a] * n[b] * n[c3] * r     # padded real rows of the first axis
+    A = c * n[b] * n[c3] * cx           # after the first transform
+    B = c * S[b] * n[c3] * cx           # after the second
+    Z = c * S[b] * S[c3] * cx           # full half spectrum
+    one_way = ((N * r + xrows) if free[a] else 0) + (xrows + A) + (A + B) + 2 * B + (B + Z) + 2 * Z
+    multiply = 2 * Z + c * S[b] * S[c3] * r
     return 2 * one_way + multiply
 
 
@@ -131,13 +131,13 @@ def _pass_bytes(info, esz):
     """Algorithmic HBM bytes of each pass (one launch each). Where the x and y
     passes are fused (info.fused), the forward kernel moves rho in and B out
     and the inverse B in and V out; the fused-away passes move nothing."""
-    n1, n2, n3 = info.n
-    L1, L2, L3 = info.L
+    n, L = list(info.n), list(info.L)
+    a, b, cx = list(info.order)        # processing order (x, y, z unless the axis rule permutes it)
     c = info.c
-    N = n1 * n2 * n3
-    A = c * n2 * n3 * 2 * esz          # complex spectrum after the x pass
-    B = c * L2 * n3 * 2 * esz          # after the y pass
-    Koct = c * (L2 // 2 + 1) * (L3 // 2 + 1) * esz
+    N = n[0] * n[1] * n[2]
+    A = c * n[b] * n[cx] * 2 * esz     # complex spectrum after the first pass
+    B = c * L[b] * n[cx] * 2 * esz     # after the second pass
+    Koct = (L[0] // 2 + 1) * (L[1] // 2 + 1) * (L[2] // 2 + 1) * esz
     if getattr(info, "fused", 0):
         return [N * esz + B, 0, 2 * B + Koct, B + N * esz, 0]
     return [N * esz + A, A + B, 2 * B + Koct, B + A, A + N * esz]

@@ -81,21 +81,26 @@ typedef struct {
   int n[3];                 /* physical grid n1, n2, n3                           */
   int bc[3];                /* enum ps_bc per axis x, y, z                        */
   int L[3];                 /* FFT length per axis (§3: S_j = N_j B_j by default) */
-  int c;                    /* L1/2 + 1: x-spectrum kept after the R2C (§3)       */
+  int c;                    /* L/2 + 1 of the first axis of the processing order:
+                               the spectrum kept after the R2C (§3)             */
   int dtype;                /* enum ps_dtype                                      */
   int math;                 /* enum ps_math                                       */
-  long long lines[5];       /* 1D transforms per pass: fwd x, fwd y, z (each of
-                               its lines is transformed forward and back), inv y,
-                               inv x                                             */
-  long long line_len[5];    /* their lengths (L1, L2, L3, L2, L1)                 */
-  double fft_points;        /* sum over the passes above of lines * length (the z
-                               lines counted twice: forward and inverse)          */
+  long long lines[5];       /* 1D transforms per pass, in processing order
+                               (order[] below; x, y, z by default): fwd first
+                               axis, fwd second axis, last axis (each of its
+                               lines is transformed forward and back), inv
+                               second axis, inv first axis                      */
+  long long line_len[5];    /* their lengths                                      */
+  double fft_points;        /* sum over the passes above of lines * length (the
+                               last axis's lines counted twice)                  */
   double paper_points;      /* §3 count for one forward 3D transform: rows times
-                               length per step with complex rows, N_y N_z S_x +
-                               S_x N_z S_y + S_x S_y S_z                          */
+                               length per step with complex rows, in processing
+                               order a, b, c: N_b N_c S_a + S_a N_c S_b +
+                               S_a S_b S_c                                       */
   double paper_full_points; /* the same count for an unpruned padded 3D FFT,
                                3 S_x S_y S_z (paper_points / paper_full_points is
-                               7/12 for free and wire, 2/3 for surface BCs)      */
+                               7/12 for free and wire, 2/3 for surface BCs, with
+                               the paper's axis order)                           */
   double alg_bytes;         /* HBM bytes one solve must move in this design:
                                rho in, V out, the intermediate write+read pairs
                                (four; two where the x and y passes are fused),
@@ -112,6 +117,8 @@ typedef struct {
                                inverse y kernel (thread-block clusters exchange
                                each z plane through distributed shared memory;
                                used when rho and V are 16-byte aligned)         */
+  int order[3];             /* physical axes (0 x, 1 y, 2 z) in forward
+                               processing order (ps_plan_set_order)             */
   int schedule[5];          /* kernel schedule requested (0 = default): generic
                                lines per tile, generic radix split (1: radix 4
                                only), lines per tile of the persistent packed z
@@ -141,6 +148,22 @@ int ps_plan_create(int n1, int n2, int n3, double h, int bc_x, int bc_y, int bc_
  * Errors: PS_ERR_ARG (plan NULL, L too small, periodic L != n, plan built).
  */
 int ps_plan_set_lengths(ps_plan plan, int L1, int L2, int L3);
+
+/*
+ * ps_plan_set_order -- the processing order of the axes (0 x, 1 y, 2 z):
+ * axis a0 takes the forward real-to-complex transform (keeping L/2 + 1
+ * outputs), a1 the second forward transform, a2 the last one with the K^F
+ * multiply; the inverse runs in the reverse order. ps_plan_create sets §3's
+ * rule: periodic axes first (their transforms run before any zero padding
+ * exists), free axes last, so that wire BCs do 7/12 and surface BCs 2/3 of a
+ * full padded 3D FFT's 1D transforms for any assignment of the axes. Orders
+ * other than x, y, z run the generic kernels along strided axes (the
+ * specialised FP32 kernels, the fused x/y passes and the tensor-core z pass
+ * need x first); every order gives the same result up to rounding. No
+ * transpose: the passes index the x-fastest arrays through strides.
+ * Errors: PS_ERR_ARG (plan NULL or built, not a permutation of 0, 1, 2).
+ */
+int ps_plan_set_order(ps_plan plan, int a0, int a1, int a2);
 
 /*
  * ps_plan_autotune -- choose the padded lengths of the free axes and the

@@ -202,6 +202,15 @@ int ps_plan_create(int n1, int n2, int n3, double h, int bc_x, int bc_y, int bc_
     p->bc[j] = bc[j];
     p->L[j] = bc[j] == PS_BC_FREE ? 2 * n[j] : n[j];  // §3: S_j = N_j B_j
   }
+  // §3's axis rule: periodic axes first on the forward transform (no zero
+  // padding to carry through the first steps), free axes last; in x, y, z
+  // order among axes of the same kind
+  {
+    int k = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < 3; ++j)
+        if ((bc[j] == PS_BC_PERIODIC) == (pass == 0)) p->ord[k++] = j;
+  }
   p->h = h;
   p->dtype = dtype;
   p->math = PS_MATH_CUDACORE;
@@ -233,15 +242,13 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
     p->L[j] = L[j];
     p->H[j] = L[j] / 2;
   }
-  p->c = p->L[0] / 2 + 1;
-  const bool even1 = p->L[0] % 2 == 0;
-  p->st[0] = factorize(even1 ? p->L[0] / 2 : p->L[0]);
-  p->st[1] = factorize(p->L[1]);
-  p->st[2] = factorize(p->L[2]);
+  const int a0 = p->ord[0], a1 = p->ord[1];
+  p->c = p->L[a0] / 2 + 1;  // outputs kept by the real-to-complex transform (§3)
+  for (int j = 0; j < 3; ++j) p->st[j] = factorize(xform_len(p, j));
   // Bluestein for transform lengths with a prime factor >= 11 (a direct sum
   // over that factor would cost N * p per line), if M fits the tile
   for (int j = 0; j < 3; ++j) {
-    const int N = (j == 0 && even1) ? p->L[0] / 2 : p->L[j];
+    const int N = xform_len(p, j);
     int big = 1;
     for (int r = 0; r < p->st[j].n; ++r) big = p->st[j].R[r] > big ? p->st[j].R[r] : big;
     p->blue[j] = BlueArgs{};
@@ -257,9 +264,39 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
       }
     }
   }
-  p->ldc = round_up((size_t)p->c, p->dtype == PS_F32 ? 16 : 8);
-  p->ldk = round_up((size_t)p->c, 16);
+  // the arrays after the first forward pass (extent c along the first axis)
+  // and after the second (the second axis at its padded length), x fastest
+  // with a pitch of 128 bytes
+  for (int j = 0; j < 3; ++j) p->ext1[j] = p->n[j];
+  p->ext1[a0] = p->c;
+  for (int j = 0; j < 3; ++j) p->ext2[j] = p->ext1[j];
+  p->ext2[a1] = p->L[a1];
+  const size_t pitch = p->dtype == PS_F32 ? 16 : 8;
+  p->ld1 = round_up((size_t)p->ext1[0], pitch);
+  p->ld2 = round_up((size_t)p->ext2[0], pitch);
+  p->ldc = p->ld1;  // x first: both arrays keep the c columns of the x spectrum
+  p->ldk = round_up((size_t)p->H[0] + 1, 16);  // the K^F octant: kx <= L1/2
   return PS_OK;
+}
+
+int ps_plan_set_order(ps_plan p, int a0, int a1, int a2) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (p->built) return fail(PS_ERR_ARG, "the order must be set before ps_kernel_build");
+  const int a[3] = {a0, a1, a2};
+  int seen = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (a[k] < 0 || a[k] > 2 || (seen & (1 << a[k]))) return fail(PS_ERR_ARG, "(%d, %d, %d) is not a permutation of the axes 0, 1, 2", a0, a1, a2);
+    seen |= 1 << a[k];
+  }
+  int old[3];
+  for (int k = 0; k < 3; ++k) {
+    old[k] = p->ord[k];
+    p->ord[k] = a[k];
+  }
+  const int rc = ps_plan_set_lengths(p, 0, 0, 0);  // c, stages and array shapes of the new order
+  if (rc != PS_OK)
+    for (int k = 0; k < 3; ++k) p->ord[k] = old[k];
+  return rc;
 }
 
 int ps_plan_set_math(ps_plan p, int math_mode) {
@@ -305,26 +342,30 @@ int ps_plan_query(ps_plan p, ps_plan_info* info) {
   info->c = p->c;
   info->dtype = p->dtype;
   info->math = p->math;
+  const int a0 = p->ord[0], a1 = p->ord[1], a2 = p->ord[2];
   const long long n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
   const long long L1 = p->L[0], L2 = p->L[1], L3 = p->L[2], c = p->c;
-  info->lines[0] = n2 * n3;  info->line_len[0] = L1;
-  info->lines[1] = c * n3;   info->line_len[1] = L2;
-  info->lines[2] = c * L2;   info->line_len[2] = L3;
-  info->lines[3] = c * n3;   info->line_len[3] = L2;
-  info->lines[4] = n2 * n3;  info->line_len[4] = L1;
+  // in processing order: S = padded lengths, N = physical counts
+  const long long Sa = p->L[a0], Sb = p->L[a1], Sc = p->L[a2], Nb = p->n[a1], Nc = p->n[a2];
+  info->lines[0] = Nb * Nc;  info->line_len[0] = Sa;
+  info->lines[1] = c * Nc;   info->line_len[1] = Sb;
+  info->lines[2] = c * Sb;   info->line_len[2] = Sc;
+  info->lines[3] = c * Nc;   info->line_len[3] = Sb;
+  info->lines[4] = Nb * Nc;  info->line_len[4] = Sa;
+  for (int k = 0; k < 3; ++k) info->order[k] = p->ord[k];
   double pts = 0.0;
   for (int k = 0; k < 5; ++k) pts += (double)info->lines[k] * (double)info->line_len[k];
-  pts += (double)info->lines[2] * (double)info->line_len[2];  // z: forward and inverse
+  pts += (double)info->lines[2] * (double)info->line_len[2];  // last axis: forward and inverse
   info->fft_points = pts;
   // §3 count of one forward 3D transform: rows x length per step, complex rows
-  info->paper_points = (double)(n2 * n3 * L1) + (double)(L1 * n3 * L2) + (double)(L1 * L2 * L3);
+  info->paper_points = (double)(Nb * Nc * Sa) + (double)(Sa * Nc * Sb) + (double)(Sa * Sb * Sc);
   info->paper_full_points = 3.0 * (double)(L1 * L2 * L3);
   const double b = (double)p->esz;
   const bool xyf = p->built && p->xyfuse;
   // the fused x/y kernels never write or read A: the intermediate pairs of
   // the x-transformed array drop out
-  info->alg_bytes = 2.0 * (double)(n1 * n2 * n3) * b + 8.0 * b * (double)(c * n3 * ((xyf ? 0 : n2) + L2)) +
-                    b * (double)c * (double)(p->H[1] + 1) * (double)(p->H[2] + 1);
+  info->alg_bytes = 2.0 * (double)(n1 * n2 * n3) * b + 8.0 * b * (double)(c * Nc * ((xyf ? 0 : Nb) + Sb)) +
+                    b * (double)(p->H[0] + 1) * (double)(p->H[1] + 1) * (double)(p->H[2] + 1);
   info->workspace_bytes = p->ws_bytes;
   info->launches = p->built ? (xyf ? 3 : 5) : 0;
   info->tensor_passes = (p->built && p->tctab) ? (1 << 2) : 0;
@@ -352,19 +393,16 @@ int ps_kernel_build(ps_plan p, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   p->device = dev;
   if (p->radix_pref) {  // the schedule's radix split of the generic stages
-    const bool even1 = p->L[0] % 2 == 0;
-    p->st[0] = factorize(even1 ? p->L[0] / 2 : p->L[0], p->radix_pref);
-    p->st[1] = factorize(p->L[1], p->radix_pref);
-    p->st[2] = factorize(p->L[2], p->radix_pref);
+    for (int j = 0; j < 3; ++j) p->st[j] = factorize(xform_len(p, j), p->radix_pref);
     for (int j = 0; j < 3; ++j)
       if (p->blue[j].M) p->blue[j].st = factorize(p->blue[j].M, p->radix_pref);
   }
   e = p->dtype == PS_F32 ? configure_passes<float>(p) : configure_passes<double>(p);
   if (e != cudaSuccess) return cuda_fail(e, "configure passes");
   const size_t csz = 2 * p->esz;
-  const size_t n2 = p->n[1], n3 = p->n[2];
-  const size_t szA = p->ldc * n2 * n3 * csz;
-  const size_t szB = p->ldc * (size_t)p->L[1] * n3 * csz;
+  // A: the array after the first forward pass, B: after the second
+  const size_t szA = p->ld1 * (size_t)p->ext1[1] * p->ext1[2] * csz;
+  const size_t szB = p->ld2 * (size_t)p->ext2[1] * p->ext2[2] * csz;
   const size_t szK = p->ldk * (p->H[1] + 1) * (p->H[2] + 1) * p->esz;
   struct { void** ptr; size_t bytes; const char* what; } allocs[] = {
       {&p->A, szA, "workspace A"},
@@ -392,7 +430,7 @@ int ps_kernel_build(ps_plan p, void* stream) {
   }
   for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
     if (!p->blue[j].M) continue;
-    const int N = (j == 0 && p->L[0] % 2 == 0) ? p->L[0] / 2 : p->L[j];
+    const int N = xform_len(p, j);
     void *twM = nullptr, *ch = nullptr, *bf = nullptr;
     e = cudaMalloc(&twM, (size_t)p->blue[j].M * csz);
     if (e == cudaSuccess) e = cudaMalloc(&ch, (size_t)N * csz);
@@ -445,7 +483,8 @@ int ps_kernel_get(ps_plan p, void* dst, void* stream) {
   if (!p->built) return fail(PS_ERR_NOT_BUILT, "ps_kernel_build has not run on this plan");
   if (!dst) return fail(PS_ERR_ARG, "dst is NULL");
   DeviceGuard g(p->device);
-  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)p->c * p->esz, p->K, p->ldk * p->esz, (size_t)p->c * p->esz,
+  const size_t D0 = (size_t)p->H[0] + 1;  // kx <= L1/2
+  cudaError_t e = cudaMemcpy2DAsync(dst, D0 * p->esz, p->K, p->ldk * p->esz, D0 * p->esz,
                                     (size_t)(p->H[1] + 1) * (p->H[2] + 1), cudaMemcpyDeviceToDevice,
                                     static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "copy K^F");

@@ -111,6 +111,13 @@ struct ps_plan_s {
   int n[3];
   int bc[3];
   int L[3];
+  // physical axes (0 x, 1 y, 2 z) in forward processing order (§3: periodic
+  // axes first, free axes last): ord[0] takes the real-to-complex transform
+  // and keeps L/2 + 1 outputs, ord[2] the K^F multiply; the inverse runs in
+  // the reverse order
+  int ord[3];
+  int ext1[3], ext2[3];  // extents (x, y, z) of the arrays after the first and second forward passes
+  size_t ld1, ld2;       // their x pitch in complex elements
   int H[3];      // L/2 (floor): last index of the even octant per axis
   int c;         // L1/2 + 1
   double h;
@@ -169,6 +176,23 @@ struct ps_plan_s {
 
 namespace ps {
 
+// The plan processes x first and y second (the specialised kernels' layout).
+inline bool canonical_order(const ps_plan_s* p) { return p->ord[0] == 0 && p->ord[1] == 1 && p->ord[2] == 2; }
+
+// Length of the complex 1D transforms along physical axis j: an even-length x
+// axis that takes the real-to-complex transform runs it as a complex
+// transform of half the length; every other axis at its full length (a
+// real-to-complex transform along y or z pairs two real lines).
+inline int xform_len(const ps_plan_s* p, int j) {
+  return (j == 0 && p->ord[0] == 0 && p->L[0] % 2 == 0) ? p->L[0] / 2 : p->L[j];
+}
+
+// Physical axis transformed by pass k (0 fwd first axis .. 4 inv first axis).
+inline int pass_axis(const ps_plan_s* p, int k) {
+  static const int slot[5] = {0, 1, 2, 1, 0};
+  return p->ord[slot[k]];
+}
+
 // Error reporting (thread-local message), defined in api.cu.
 void set_error(const char* fmt, ...);
 
@@ -184,6 +208,20 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
 template <typename T>
 cudaError_t launch_vjp_axpy(ps_plan_s* p, T* out, const T* V, const double* gE, bool accumulate,
                             cudaStream_t s);
+// passes_ord.cu: the solve for a processing order other than x, y, z
+template <typename T>
+cudaError_t launch_solve_ord(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream_t s, cudaEvent_t* ev);
+// energy partials (CTAs of the fused pass) of a plan in another order, and
+// the launch attributes of its kernels
+int ord_conv_ctas(const ps_plan_s* p);
+template <typename T>
+cudaError_t configure_ord(const ps_plan_s* p);
+// rows of each shared-memory buffer of a generic pass (passes.cu)
+int gen_rows(const ps_plan_s* p, int pass);
+// passes.cu: the generic x pass (P1 forward R2C, P5 inverse C2R) of a plan
+// that processes x first, on A with pitch ld1
+template <typename T>
+cudaError_t launch_x_pass(ps_plan_s* p, int pass, const void* src, void* dst, cudaStream_t s);
 cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s);
 // batch.cu: the batch as one cached CUDA graph of concurrent per-problem chains
 cudaError_t batch_solve_graph(int count, ps_plan_s* const* plans, const void* const* rho, void* const* V,

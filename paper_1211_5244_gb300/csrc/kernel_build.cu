@@ -295,7 +295,7 @@ cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s) {
   for (int j = 0; j < 3; ++j) {
     const BlueArgs& b = p->blue[j];
     if (!b.M) continue;
-    const int N = (j == 0 && p->L[0] % 2 == 0) ? p->L[0] / 2 : p->L[j];
+    const int N = xform_len(p, j);
     if (p->dtype == PS_F32) {
       twiddle_kernel<float><<<grid_for(b.M), 256, 0, s>>>((float2*)b.twM, b.M);
       chirp_kernel<float><<<grid_for(N), 256, 0, s>>>((float2*)b.chirp, N);

@@ -412,12 +412,15 @@ static int pick_tk(int rows, int twn, size_t csz, int tk0, int pad, int* ldt, si
   return 0;
 }
 
-// rows of each shared-memory buffer of a generic pass
-static int gen_rows(const ps_plan_s* p, int pass) {
-  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
-  const bool even1 = (p->L[0] % 2) == 0;
-  const int N = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
-  int r = axis == 0 ? N + 1 : N;
+// rows of each shared-memory buffer of a generic pass: the transform length,
+// the Bluestein length, and for the real-to-complex passes room for the half
+// spectra (x first: N + 1 = L1/2 + 1 rows, or two of c rows for an odd L1;
+// another first axis: two of c rows of the paired lines)
+int gen_rows(const ps_plan_s* p, int pass) {
+  const int axis = pass_axis(p, pass);
+  const int N = xform_len(p, axis);
+  int r = N;
+  if (pass == P1 || pass == P5) r = axis == 0 ? N + 1 : 2 * p->c;
   if (p->blue[axis].M > r) r = p->blue[axis].M;
   return r;
 }
@@ -431,9 +434,8 @@ static GenArgs gen_args(const ps_plan_s* p, int pass) {
   a.ldc = (int)p->ldc;
   a.ldk = (int)p->ldk;
   a.tk = p->cfg[pass].tk; a.ldt = p->cfg[pass].ldt;
-  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
-  const bool even1 = (p->L[0] % 2) == 0;
-  a.N = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
+  const int axis = pass_axis(p, pass);
+  a.N = xform_len(p, axis);
   a.tws = p->L[axis] / a.N;
   a.st = p->st[axis];
   a.bl = p->blue[axis];
@@ -455,20 +457,17 @@ cudaError_t configure_passes(ps_plan_s* p) {
   // the autotuner), else 16 (FP32) / 8 (FP64)
   int tk0 = sizeof(T) == 4 ? 16 : 8;
   if (p->gen_tk_max > 0) tk0 = p->gen_tk_max;
-  const bool even1 = (p->L[0] % 2) == 0;
-  const int N0 = even1 ? p->L[0] / 2 : p->L[0];
-  (void)N0;
   const int rows[5] = {gen_rows(p, P1), gen_rows(p, P2), gen_rows(p, P3), gen_rows(p, P4), gen_rows(p, P5)};
   for (int k = 0; k < 5; ++k) {
     PassCfg& cf = p->cfg[k];
     cf.threads = 256;
     cf.fast = 0;
-    const int axis = (k == P1 || k == P5) ? 0 : (k == P3 ? 2 : 1);
-    const int Nk = (axis == 0 && even1) ? p->L[0] / 2 : p->L[axis];
+    const int axis = pass_axis(p, k);
+    const int Nk = xform_len(p, axis);
     const int twn = p->blue[axis].M ? p->blue[axis].M : Nk;
-    // row pitch: tk + 1 for the x passes, whose tile loops transpose rows (a
+    // row pitch: tk + 1 for passes along x, whose tile loops transpose rows (a
     // pitch of tk would put a row's consecutive elements on one bank); tk
-    // for the y and z passes, whose tile rows are contiguous runs
+    // for passes along y and z, whose tile rows are contiguous runs
     cf.tk = pick_tk(rows[k], twn, sizeof(C), tk0, axis == 0 ? 1 : 0, &cf.ldt, &cf.gsmem, &cf.twn);
     cf.smem = cf.gsmem;
     if (cf.tk == 0) {
@@ -482,6 +481,12 @@ cudaError_t configure_passes(ps_plan_s* p) {
   if ((e = cudaFuncSetAttribute(py_generic<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(pz_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(p5_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  if (!canonical_order(p)) {
+    // the generic kernels along strided axes (passes_ord.cu); energy
+    // partials: one per CTA of the fused pass
+    p->npart = ord_conv_ctas(p);
+    return configure_ord<T>(p);
+  }
   if constexpr (sizeof(T) == 4) {
     e = configure_fast_f32(p);
     if (e != cudaSuccess) return e;
@@ -496,6 +501,7 @@ template <typename T>
 cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream_t s,
                          cudaEvent_t* ev) {
   using C = cpx<T>;
+  if (!canonical_order(p)) return launch_solve_ord<T>(p, rho, V, E, s, ev);
   C* A = static_cast<C*>(p->A);
   C* B = static_cast<C*>(p->B);
   const C* tw0 = static_cast<const C*>(p->tw[0]);
@@ -568,6 +574,24 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_x_pass(ps_plan_s* p, int pass, const void* src, void* dst, cudaStream_t s) {
+  using C = cpx<T>;
+  GenArgs a = gen_args<T>(p, pass);
+  const int nrows = p->n[1] * p->n[2];
+  const int rpc = (p->L[0] % 2 == 0) ? a.tk : 2 * a.tk;  // odd L1: two real rows per line
+  const C* tw0 = static_cast<const C*>(p->tw[0]);
+  if (pass == P1)
+    p1_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(
+        static_cast<const T*>(src), static_cast<C*>(dst), tw0, a);
+  else
+    p5_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(
+        static_cast<const C*>(src), static_cast<T*>(dst), tw0, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_x_pass<float>(ps_plan_s*, int, const void*, void*, cudaStream_t);
+template cudaError_t launch_x_pass<double>(ps_plan_s*, int, const void*, void*, cudaStream_t);
 template cudaError_t configure_passes<float>(ps_plan_s*);
 template cudaError_t configure_passes<double>(ps_plan_s*);
 template cudaError_t launch_solve<float>(ps_plan_s*, const float*, float*, double*, cudaStream_t,

@@ -15,9 +15,13 @@
 //   ztk     lines per tile of the persistent packed z kernel (8 or 16)
 //   ykind   y kernels: packed persistent, unpacked persistent, non-persistent
 //   xy      the fused x/y passes (thread-block clusters) or the separate ones
+//   order   the plan's processing order of the axes (§3's rule by default), or
+//           x first, which runs the specialised FP32 kernels where the
+//           lengths have them (more 1D transforms, faster kernels)
 // Results are kept in memory, and in a text file when PS_TUNE_CACHE names one
 // (one line per geometry: "n1 n2 n3 bc1 bc2 bc3 mode sms L1 L2 L3 tile radix
-// ztk ykind xy", mode = dtype + 2 math, 0 for a default choice).
+// ztk ykind xy xfirst", mode = dtype + 2 math + 4 (the plan's order as
+// 9 a0 + 3 a1 + a2), 0 for a default choice).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -33,7 +37,7 @@ namespace ps {
 namespace {
 
 // a tuned choice: padded lengths and the schedule fields of the plan
-enum { kL1, kL2, kL3, kTile, kRadix, kZtk, kYkind, kXy, kFields };
+enum { kL1, kL2, kL3, kTile, kRadix, kZtk, kYkind, kXy, kXfirst, kFields };
 
 std::mutex g_tune_mu;
 std::map<std::string, std::vector<int>> g_tuned;
@@ -61,9 +65,9 @@ void load_file() {
   char line[256];
   while (fgets(line, sizeof line, f)) {
     int n[3], bc[3], dt, sms, v[kFields] = {};
-    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &n[0], &n[1], &n[2], &bc[0],
-                           &bc[1], &bc[2], &dt, &sms, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7]);
-    if (got != 8 + kFields && got != 12) continue;  // 12: lengths and tile only
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &n[0], &n[1], &n[2], &bc[0],
+                           &bc[1], &bc[2], &dt, &sms, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8]);
+    if (got != 8 + kFields) continue;
     char key[128];
     snprintf(key, sizeof key, "%d %d %d %d %d %d %d %d", n[0], n[1], n[2], bc[0], bc[1], bc[2], dt, sms);
     g_tuned[key] = std::vector<int>(v, v + kFields);
@@ -91,6 +95,7 @@ int apply_choice(ps_plan p, const std::vector<int>& v) {
   p->z_tk = v[kZtk];
   p->y_kind = v[kYkind];
   p->xy_sched = v[kXy];
+  if (v[kXfirst]) return ps_plan_set_order(p, 0, 1, 2);
   return PS_OK;
 }
 
@@ -126,7 +131,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
   }
   char keybuf[128];
   snprintf(keybuf, sizeof keybuf, "%d %d %d %d %d %d %d %d", p->n[0], p->n[1], p->n[2], p->bc[0], p->bc[1],
-           p->bc[2], p->dtype + 2 * p->math, sms);
+           p->bc[2], p->dtype + 2 * p->math + 4 * (9 * p->ord[0] + 3 * p->ord[1] + p->ord[2]), sms);
   const std::string key(keybuf);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -145,22 +150,35 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   int rc = PS_OK;
 
-  // builds a trial plan with choice v, times `reps` solves after two
-  // untimed ones; *ms < 0 if the choice is not valid for this plan
+  // builds a trial plan with choice v and returns in *ms the time per solve:
+  // the lesser of two timed runs of at least `reps` solves each, lengthened
+  // to about a millisecond for small plans (timing noise would otherwise pick
+  // choices at random), after two untimed solves; *ms < 0 if the choice is
+  // not valid for this plan
   auto trial = [&](const std::vector<int>& v, float* ms, Applies* ap) {
     *ms = -1.f;
     ps_plan tp = nullptr;
     int r = ps_plan_create(p->n[0], p->n[1], p->n[2], p->h, p->bc[0], p->bc[1], p->bc[2], p->dtype, &tp);
     if (r == PS_OK) r = ps_plan_set_math(tp, p->math);
+    if (r == PS_OK) r = ps_plan_set_order(tp, p->ord[0], p->ord[1], p->ord[2]);
     if (r == PS_OK) r = apply_choice(tp, v);
     if (r == PS_OK) r = ps_kernel_build(tp, stream);
     for (int w = 0; r == PS_OK && w < 2; ++w) r = ps_solve(tp, rho, V, nullptr, stream);
     if (r == PS_OK) {
-      e = cudaEventRecord(t0, s);
-      for (int k = 0; r == PS_OK && k < reps; ++k) r = ps_solve(tp, rho, V, nullptr, stream);
-      if (e == cudaSuccess) e = cudaEventRecord(t1, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-      if (e == cudaSuccess && r == PS_OK) e = cudaEventElapsedTime(ms, t0, t1);
+      auto timed = [&](int count, float* out) {
+        e = cudaEventRecord(t0, s);
+        for (int k = 0; r == PS_OK && k < count; ++k) r = ps_solve(tp, rho, V, nullptr, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess && r == PS_OK) e = cudaEventElapsedTime(out, t0, t1);
+        *out /= (float)count;
+      };
+      float a = 0.f, b = 0.f;
+      timed(reps, &a);
+      const int count = a > 0.f ? std::min(400, std::max(reps, (int)(1.0f / a) + 1)) : reps;
+      if (e == cudaSuccess && r == PS_OK) timed(count, &a);
+      if (e == cudaSuccess && r == PS_OK) timed(count, &b);
+      *ms = std::min(a, b);
       if (ap) {
         for (int k = 0; k < 5; ++k) ap->generic |= !tp->cfg[k].fast;
         ap->zpipe = tp->zsoa_T == 16 && tp->cfg[P3].fast && !tp->tctab;
@@ -196,7 +214,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
     if (ok && std::find(cands.begin(), cands.end(), v) == cands.end()) cands.push_back(v);
   }
   float best_ms = -1.f;
-  std::vector<int> best = {p->L[0], p->L[1], p->L[2], 0, 0, 0, 0, 0};
+  std::vector<int> best = {p->L[0], p->L[1], p->L[2], 0, 0, 0, 0, 0, 0};
   Applies best_ap;
   for (size_t c = 0; e == cudaSuccess && rc == PS_OK && c < cands.size(); ++c) {
     float ms;
@@ -208,7 +226,9 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
       best_ap = ap;
     }
   }
-  // 2. the schedule, one choice at a time at the best lengths
+  // 2. the schedule, one choice at a time at the best lengths; a choice other
+  // than the default is kept only when it is at least 3% faster
+  constexpr float kKeep = 0.97f;
   auto try_field = [&](int field, std::initializer_list<int> values) {
     for (int val : values) {
       if (e != cudaSuccess || rc != PS_OK || best_ms < 0.f) return;
@@ -217,7 +237,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
       float ms;
       Applies ap;
       rc = trial(v, &ms, &ap);
-      if (rc == PS_OK && e == cudaSuccess && ms >= 0.f && ms < best_ms) {
+      if (rc == PS_OK && e == cudaSuccess && ms >= 0.f && ms < kKeep * best_ms) {
         best_ms = ms;
         best = v;
         best_ap = ap;
@@ -225,6 +245,22 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
     }
   };
   const int t0w = p->dtype == PS_F32 ? 16 : 8;
+  if (!canonical_order(p)) {
+    // x first: the specialised kernels may outrun the extra transforms; the
+    // choices below are then tuned for that order
+    std::vector<int> v = best;
+    v[kXfirst] = 1;
+    float ms;
+    Applies ap;
+    if (e == cudaSuccess && rc == PS_OK && best_ms >= 0.f) {
+      rc = trial(v, &ms, &ap);
+      if (rc == PS_OK && e == cudaSuccess && ms >= 0.f && ms < kKeep * best_ms) {
+        best_ms = ms;
+        best = v;
+        best_ap = ap;
+      }
+    }
+  }
   if (best_ap.generic) {
     try_field(kTile, {t0w / 2, t0w / 4});
     try_field(kRadix, {1});
@@ -239,7 +275,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
     Applies ap;
     if (e == cudaSuccess && rc == PS_OK && best_ms >= 0.f) {
       rc = trial(v, &ms, &ap);
-      if (rc == PS_OK && e == cudaSuccess && ap.xy && ms >= 0.f && ms < best_ms) {
+      if (rc == PS_OK && e == cudaSuccess && ap.xy && ms >= 0.f && ms < kKeep * best_ms) {
         best_ms = ms;
         best = v;
       }

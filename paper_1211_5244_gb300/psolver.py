@@ -40,7 +40,7 @@ class PlanInfo(ctypes.Structure):
         ("paper_full_points", ctypes.c_double), ("alg_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_int),
         ("tensor_passes", ctypes.c_int), ("blocks", ctypes.c_int * 5), ("fused", ctypes.c_int),
-        ("schedule", ctypes.c_int * 5),
+        ("order", ctypes.c_int * 3), ("schedule", ctypes.c_int * 5),
     ]
 
 
@@ -63,6 +63,7 @@ def load_library():
         "ps_plan_set_lengths": [vp, i, i, i],
         "ps_plan_set_math": [vp, i],
         "ps_plan_set_schedule": [vp, i, i, i, i, i],
+        "ps_plan_set_order": [vp, i, i, i],
         "ps_plan_autotune": [vp, i, vp],
         "ps_plan_query": [vp, ctypes.POINTER(PlanInfo)],
         "ps_kernel_build": [vp, vp],
@@ -117,7 +118,7 @@ class Plan:
     """One solve geometry: ps_plan_create (+ optional lengths) and ps_kernel_build."""
 
     def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None, autotune=False,
-                 math="cudacore", schedule=None):
+                 math="cudacore", schedule=None, order=None):
         lib = load_library()
         self.n = tuple(int(v) for v in n)
         self.bc = str(bc).lower()
@@ -133,6 +134,8 @@ class Plan:
         self.math = {"cudacore": PS_MATH_CUDACORE, "tf32x3": PS_MATH_TF32X3,
                      "bf16x3": PS_MATH_BF16X3}[str(math).lower()]
         _check(lib.ps_plan_set_math(self._h, self.math))
+        if order is not None:
+            _check(lib.ps_plan_set_order(self._h, int(order[0]), int(order[1]), int(order[2])))
         if schedule is not None:
             self.set_schedule(**schedule)
         if autotune:
@@ -298,7 +301,7 @@ class Plan:
         """ps_kernel_get: the stored K^F / (L1 L2 L3) octant, shape (L3/2+1, L2/2+1, c)."""
         import torch
         inf = self.info()
-        shape = (inf.L[2] // 2 + 1, inf.L[1] // 2 + 1, inf.c)
+        shape = (inf.L[2] // 2 + 1, inf.L[1] // 2 + 1, inf.L[0] // 2 + 1)
         out = torch.empty(shape, dtype=self.torch_dtype, device="cuda")
         _check(_lib.ps_kernel_get(self._h, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
         return out

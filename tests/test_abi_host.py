@@ -132,22 +132,49 @@ GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "work_fractions.js
 def test_work_fraction_matches_section3(bc, n):
     p = ps.Plan((n, n, n), bc, 0.3, "f32", build=False)
     info = p.info()
+    assert list(info.order) == GOLDEN["orders"][bc]
     num, den = GOLDEN["fractions"][bc]
     assert info.paper_points * den == info.paper_full_points * num
 
 
-@pytest.mark.parametrize("bc", ["fff", "pff", "ppf", "ppp", "fpf"])
+@pytest.mark.parametrize("bc", sorted(GOLDEN["orders"]))
 def test_lines_per_pass_match_listing(bc):
-    n1, n2, n3 = 12, 7, 9
-    p = ps.Plan((n1, n2, n3), bc, 0.3, "f64", build=False)
+    n = (12, 7, 9)
+    p = ps.Plan(n, bc, 0.3, "f64", build=False)
     info = p.info()
-    L1, L2, L3 = info.L
-    env = dict(n1=n1, n2=n2, n3=n3, L1=L1, L2=L2, L3=L3)
+    a, b, c = GOLDEN["orders"][bc]
+    L = list(info.L)
+    env = dict(Sa=L[a], Sb=L[b], Nb=n[b], Nc=n[c])
     rows = {k: eval(v, {}, env) for k, v in GOLDEN["listing_rows"].items()}
-    assert list(info.lines) == [rows["x"], rows["y"], rows["z"], rows["y"], rows["x"]]
-    assert list(info.line_len) == [L1, L2, L3, L2, L1]
-    for j, b in enumerate(bc):
-        assert info.L[j] == ((n1, n2, n3)[j] * (2 if b == "f" else 1))
+    assert list(info.lines) == [rows["first"], rows["second"], rows["third"], rows["second"], rows["first"]]
+    assert list(info.line_len) == [L[a], L[b], L[c], L[b], L[a]]
+    assert info.c == L[a] // 2 + 1
+    for j, bj in enumerate(bc):
+        assert info.L[j] == n[j] * (2 if bj == "f" else 1)
+
+
+@pytest.mark.parametrize("bcs", [("pff", "fpf", "ffp"), ("ppf", "pfp", "fpp")])
+def test_axis_assignments_of_one_class_move_the_same_bytes(bcs):
+    # with the axis rule the work and the traffic depend on how many axes are
+    # periodic, not on which: a cube of one BC class costs the same for each
+    # assignment of the axes
+    infos = [ps.Plan((64, 64, 64), bc, 0.3, "f32", build=False).info() for bc in bcs]
+    assert len({i.alg_bytes for i in infos}) == 1
+    assert len({i.paper_points for i in infos}) == 1
+    assert len({i.fft_points for i in infos}) == 1
+
+
+def test_set_order_rules():
+    lib = ps.load_library()
+    p = ps.Plan((10, 12, 7), "ffp", 0.3, "f32", build=False)
+    assert list(p.info().order) == [2, 0, 1]
+    for bad in ((0, 0, 1), (0, 1, 3), (-1, 1, 2)):
+        assert lib.ps_plan_set_order(p.handle, *bad) == 1
+    assert list(p.info().order) == [2, 0, 1]
+    assert lib.ps_plan_set_order(p.handle, 0, 1, 2) == 0
+    info = p.info()
+    assert list(info.order) == [0, 1, 2] and info.c == 11
+    assert lib.ps_plan_set_order(None, 0, 1, 2) == 1
 
 
 def test_algorithmic_bytes_256_free_fp32():

@@ -35,31 +35,32 @@ def test_pass_bytes_add_up_to_the_solve(n, bc, dt):
     assert sum(bench._pass_bytes(info, esz)) == pytest.approx(info.alg_bytes, rel=1e-12)
 
 
-def _paper_steps(n, bc, esz):
+def _paper_steps(n, bc, esz, order):
     """The §3 step list as separate kernels, each reading its input and writing
-    its output once (written out step by step)."""
-    n1, n2, n3 = n
-    free = [b == "f" for b in bc]
-    S1, S2, S3 = [2 * v if f else v for v, f in zip(n, free)]
-    c = S1 // 2 + 1
+    its output once (written out step by step), with the axes taken in the
+    processing order (first axis a, then b, then c3: x, y, z by default)."""
+    a, b, c3 = order
+    free = [f == "f" for f in bc]
+    S = [2 * v if f else v for v, f in zip(n, free)]
+    c = S[a] // 2 + 1
     r, cx = esz, 2 * esz
-    N = n1 * n2 * n3
+    N = n[0] * n[1] * n[2]
     steps = []
-    if free[0]:
-        steps.append(("spread_X", N * r, S1 * n2 * n3 * r))
-    steps.append(("1DFFT_X R2C", S1 * n2 * n3 * r, c * n2 * n3 * cx))
-    steps.append(("transpose(+spread)_Y", c * n2 * n3 * cx, c * S2 * n3 * cx))
-    steps.append(("1DFFT_Y", c * S2 * n3 * cx, c * S2 * n3 * cx))
-    steps.append(("transpose(+spread)_Z", c * S2 * n3 * cx, c * S2 * S3 * cx))
-    steps.append(("1DFFT_Z", c * S2 * S3 * cx, c * S2 * S3 * cx))
-    steps.append(("kernel multiplication", c * S2 * S3 * cx + c * S2 * S3 * r, c * S2 * S3 * cx))
-    steps.append(("inverse 1DFFT_Z", c * S2 * S3 * cx, c * S2 * S3 * cx))
-    steps.append(("compaction_Z+transpose", c * S2 * S3 * cx, c * S2 * n3 * cx))
-    steps.append(("inverse 1DFFT_Y", c * S2 * n3 * cx, c * S2 * n3 * cx))
-    steps.append(("compaction_Y+transpose", c * S2 * n3 * cx, c * n2 * n3 * cx))
-    steps.append(("inverse 1DFFT_X C2R", c * n2 * n3 * cx, S1 * n2 * n3 * r))
-    if free[0]:
-        steps.append(("compaction_X", S1 * n2 * n3 * r, N * r))
+    if free[a]:
+        steps.append(("spread first axis", N * r, S[a] * n[b] * n[c3] * r))
+    steps.append(("1DFFT first axis R2C", S[a] * n[b] * n[c3] * r, c * n[b] * n[c3] * cx))
+    steps.append(("transpose(+spread) second axis", c * n[b] * n[c3] * cx, c * S[b] * n[c3] * cx))
+    steps.append(("1DFFT second axis", c * S[b] * n[c3] * cx, c * S[b] * n[c3] * cx))
+    steps.append(("transpose(+spread) third axis", c * S[b] * n[c3] * cx, c * S[b] * S[c3] * cx))
+    steps.append(("1DFFT third axis", c * S[b] * S[c3] * cx, c * S[b] * S[c3] * cx))
+    steps.append(("kernel multiplication", c * S[b] * S[c3] * cx + c * S[b] * S[c3] * r, c * S[b] * S[c3] * cx))
+    steps.append(("inverse 1DFFT third axis", c * S[b] * S[c3] * cx, c * S[b] * S[c3] * cx))
+    steps.append(("compaction+transpose third axis", c * S[b] * S[c3] * cx, c * S[b] * n[c3] * cx))
+    steps.append(("inverse 1DFFT second axis", c * S[b] * n[c3] * cx, c * S[b] * n[c3] * cx))
+    steps.append(("compaction+transpose second axis", c * S[b] * n[c3] * cx, c * n[b] * n[c3] * cx))
+    steps.append(("inverse 1DFFT first axis C2R", c * n[b] * n[c3] * cx, S[a] * n[b] * n[c3] * r))
+    if free[a]:
+        steps.append(("compaction first axis", S[a] * n[b] * n[c3] * r, N * r))
     return sum(rd + wr for _, rd, wr in steps)
 
 
@@ -67,7 +68,7 @@ def _paper_steps(n, bc, esz):
 def test_paper_unfused_bytes_follow_the_step_list(n, bc, dt):
     info = ps.Plan(n, bc, 0.3, dt, build=False).info()
     esz = 4 if dt == "f32" else 8
-    assert bench._paper_unfused_bytes(info, esz) == _paper_steps(n, bc, esz)
+    assert bench._paper_unfused_bytes(info, esz) == _paper_steps(n, bc, esz, list(info.order))
 
 
 def test_paper_unfused_bytes_256_free():

@@ -28,10 +28,13 @@ def _np_dtype(dtype):
     return np.float32 if dtype == "f32" else np.float64
 
 
-def _gpu_solve(torch, rho, bc, h, dtype, L=None):
+XFIRST = (0, 1, 2)  # the processing order of the specialised FP32 kernels (x, then y, then z)
+
+
+def _gpu_solve(torch, rho, bc, h, dtype, L=None, order=None):
     from paper_1211_5244_gb300 import psolver
     n = rho.shape[::-1]
-    plan = psolver.Plan(n, bc, h, dtype, L=L)
+    plan = psolver.Plan(n, bc, h, dtype, L=L, order=order)
     r = torch.from_numpy(np.ascontiguousarray(rho.astype(_np_dtype(dtype)))).cuda()
     V, E = plan.solve(r)
     torch.cuda.synchronize()
@@ -62,6 +65,23 @@ def test_parity_ragged(torch_cuda, n, bc, dtype):
     rho = synth.random_density(n, seed=sum(n) + ALL_BCS.index(bc), subtract_mean="p" in bc)
     V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.37, dtype)
     _check(V, E, rho, bc, 0.37, dtype)
+
+
+ORDERS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("order", ORDERS, ids=lambda o: "".join("xyz"[a] for a in o))
+@pytest.mark.parametrize("n,bc", [((13, 10, 7), "fff"), ((12, 9, 15), "pfp"), ((11, 14, 8), "ffp"),
+                                  ((16, 7, 10), "ppp"), ((9, 16, 12), "fpf")])
+def test_parity_every_processing_order(torch_cuda, n, bc, order, dtype):
+    """Every order of the three axis passes (the R2C along x, y or z with the
+    pairing of real columns, strided line passes, the fused pass along any
+    axis, odd and even lengths) against the FP64 oracle."""
+    rho = synth.random_density(n, seed=sum(n) + sum(order), subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.33, dtype, order=order)
+    assert tuple(plan.info().order) == order
+    _check(V, E, rho, bc, 0.33, dtype)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -289,7 +309,7 @@ PADDED_CASES = [
 @pytest.mark.parametrize("n,bc,L", PADDED_CASES)
 def test_parity_padded_below_half(torch_cuda, n, bc, L):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=13 + sum(n), noise=1e-3, subtract_mean="p" in bc)
-    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L, order=XFIRST)
     assert list(plan.info().L) == list(L)
     # the specialised kernels take the padded passes
     blocks = list(plan.info().blocks)
@@ -310,7 +330,7 @@ ODD_L2_CASES = [
 @pytest.mark.parametrize("n,bc", ODD_L2_CASES)
 def test_parity_odd_y_length_fast_z(torch_cuda, n, bc):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=7 + sum(n), noise=1e-3, subtract_mean=True)
-    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", order=XFIRST)
     assert plan.info().L[1] % 2 == 1
     _check(V, E, rho, bc, 0.25, "f32")
 
@@ -329,7 +349,7 @@ ODD_N1_CASES = [
 @pytest.mark.parametrize("n,bc,L", ODD_N1_CASES)
 def test_parity_odd_n1_fast_x(torch_cuda, n, bc, L):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=37 + sum(n), noise=1e-3, subtract_mean="p" in bc)
-    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L, order=XFIRST)
     assert plan.info().blocks[0] > 0 and plan.info().blocks[4] > 0  # the specialised x kernels ran
     _check(V, E, rho, bc, 0.25, "f32", L=L)
 
@@ -354,7 +374,7 @@ def test_parity_fused_xy(torch_cuda, n, bc, math):
     torch = torch_cuda
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=43 + sum(n), noise=1e-3, subtract_mean="p" in bc)
     # not the default schedule (the separate passes are faster)
-    plan = psolver.Plan(n, bc, 0.25, "f32", math=math, schedule={"xy": 1})
+    plan = psolver.Plan(n, bc, 0.25, "f32", math=math, schedule={"xy": 1}, order=XFIRST)
     info = plan.info()
     assert info.fused == (1 << 1) | (1 << 4) and info.launches == 3, (info.fused, info.launches)
     r = torch.from_numpy(rho.astype(np.float32)).cuda()
@@ -408,7 +428,7 @@ LAST_COLUMN_CASES = [
 @pytest.mark.parametrize("n,bc", LAST_COLUMN_CASES)
 def test_parity_last_column_tiles(torch_cuda, n, bc):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=29 + sum(n), noise=1e-3, subtract_mean="p" in bc)
-    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", order=XFIRST)
     _check(V, E, rho, bc, 0.25, "f32")
 
 
@@ -428,7 +448,7 @@ TC_CASES = [
 def _tc_solve(torch, rho, bc, h):
     from paper_1211_5244_gb300 import psolver
     n = rho.shape[::-1]
-    plan = psolver.Plan(n, bc, h, "f32", math="tf32x3")
+    plan = psolver.Plan(n, bc, h, "f32", math="tf32x3", order=XFIRST)
     assert plan.info().tensor_passes == 1 << 2
     r = torch.from_numpy(np.ascontiguousarray(rho.astype(np.float32))).cuda()
     V, E = plan.solve(r)
@@ -517,7 +537,7 @@ FAST_CASES = [
 @pytest.mark.parametrize("n,bc", FAST_CASES)
 def test_parity_fast_kernels_fp32(torch_cuda, n, bc):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=sum(n), noise=1e-3, subtract_mean="p" in bc)
-    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32")
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", order=XFIRST)
     _check(V, E, rho, bc, 0.25, "f32")
 
 
@@ -651,6 +671,6 @@ def test_parity_schedules(torch_cuda, monkeypatch, sched, env, n, bc):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=17 + sum(n), noise=1e-3, subtract_mean="p" in bc)
-    plan = psolver.Plan(n, bc, 0.25, "f32", schedule=sched)
+    plan = psolver.Plan(n, bc, 0.25, "f32", schedule=sched, order=XFIRST)
     V, E = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
     _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.25, "f32")
