@@ -520,8 +520,8 @@ def _spec(args):
         w, bc = dict(synth.WORKLOADS["hartree192_f32"]), "fff"
     else:
         w0 = synth.WORKLOADS["bc128"]
-        if args.bc not in w0["bcs"]:
-            raise SystemExit(f"--bc must be one of {w0['bcs']}")
+        if len(args.bc) != 3 or any(b not in "pf" for b in args.bc):
+            raise SystemExit("--bc must name the x, y, z axes with p / f, e.g. pff")
         w, bc = {k: w0[k] for k in ("n", "h", "n_gauss", "noise", "seed")}, args.bc
     kernel = _localpot_octant(w) if args.workload == "localpot256" else None
     return w, bc, kernel
@@ -790,7 +790,11 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "free512", "bc128", "hartree192", "localpot256", "batched64"],
                     help="localpot256: the 256^3 free solve with a caller's even kernel (ps_kernel_set_real)")
-    ap.add_argument("--bc", default="fff", help="boundary conditions of --workload bc128 (fff, pff, ppf, ppp)")
+    ap.add_argument("--bc", default="fff",
+                    help="boundary conditions of --workload bc128, x y z: any of the 8 assignments (fff, pff, fpf, "
+                         "ffp, ppf, pfp, fpp, ppp)")
+    ap.add_argument("--order", default="rule", choices=["rule", "xfirst"],
+                    help="axis processing order: the paper's rule (periodic axes first) or x, y, z")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="hartree192: padded lengths 2n instead of the autotuner's choice")
@@ -827,7 +831,8 @@ def main():
     esz = 4 if dt == "f32" else 8
     rho_np = _density(w, rank, bc, dt)
     rho = torch.from_numpy(rho_np).cuda()
-    plan = psolver.Plan(w["n"], bc, w["h"], dt, math=args.math)
+    plan = psolver.Plan(w["n"], bc, w["h"], dt, math=args.math,
+                        order=(0, 1, 2) if args.order == "xfirst" else None)
     if kernel is not None:
         plan.set_kernel_real(kernel)
     info = plan.info()
@@ -908,6 +913,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
         "config": {"workload": desc, "n": list(n), "bc": bc, "h": w["h"], "L": list(info.L),
+                   "order": "".join("xyz"[a] for a in info.order),
                    "math": args.math, "tensor_passes": info.tensor_passes, "blocks": list(info.blocks),
                    "l2": "flushed (512 MiB write) before every step; per-step CUDA events",
                    "pass_times": "separate profiled loop of the same K steps, one event between passes",

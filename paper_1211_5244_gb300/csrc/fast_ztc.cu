@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(256, NZ == 8 ? 2 : 1)
       tc::commit(mb);
     }
     wait_mma();
+    if (s_abort) break;  // no further MMA or TMEM access: one commit stays outstanding
 
     // ---- stage 2 result X[k2 + 16 k1]: V^F = K^F X on the even octant,
     // energy, and the conjugate as the stage 3 operand (K = (k1, re/im))
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(256, NZ == 8 ? 2 : 1)
     if (next < ntiles) issue_k(next);  // the K^F slice has been read
     tc::cp_commit();
     wait_mma();
+    if (s_abort) break;
 
     // ---- stage 3 result conj(U[n1][k2]): transpose through T
     {
@@ -407,6 +409,16 @@ __global__ void __launch_bounds__(256, NZ == 8 ? 2 : 1)
     }
   }
   tc::cp_wait_all();
+  // An expired wait (wait_mma above) leaves the commit of its MMAs
+  // outstanding: the MMAs may still write this CTA's TMEM, and the commit
+  // arrives on an mbarrier in this CTA's shared memory. Before the TMEM is
+  // freed and the CTA exits, thread 0 waits for that commit once more, with
+  // the same bound (the phase it gave up on is the one before the last flip).
+  // A slow MMA then completes before its TMEM and mbarrier go away. If it
+  // does not complete even then, the tensor pipe has stopped and no order of
+  // teardown makes its TMEM safe; the status word tells the host that the
+  // results are invalid (ps_plan_device_status returns PS_ERR_TIMEOUT).
+  if (tid == 0 && s_abort) tc::mbar_wait(mb, phase ^ 1u);
   if (tid == 0 && s_abort) atomicExch(counter + 1, 1u);
   tc::fence_before();
   __syncthreads();
