@@ -140,6 +140,8 @@ def _pass_bytes(info, esz):
     Koct = (L[0] // 2 + 1) * (L[1] // 2 + 1) * (L[2] // 2 + 1) * esz
     if getattr(info, "fused", 0):
         return [N * esz + B, 0, 2 * B + Koct, B + N * esz, 0]
+    if getattr(info, "chunks", 1) > 1:  # x and y passes interleaved chunk by chunk: timed together
+        return [N * esz + 2 * A + B, 0, 2 * B + Koct, B + 2 * A + N * esz, 0]
     return [N * esz + A, A + B, 2 * B + Koct, B + A, A + N * esz]
 
 
@@ -556,14 +558,17 @@ def _rooflines(info, pass_ms, dtype, workload, math_mode):
     esz = 4 if dtype == "f32" else 8
     pbytes = _pass_bytes(info, esz)
     pflops = _pass_flops(info)
-    if getattr(info, "fused", 0):  # the fused kernels do the work of two passes each
+    if getattr(info, "fused", 0) or getattr(info, "chunks", 1) > 1:  # two passes per timed entry
         pflops = [pflops[0] + pflops[1], 0.0, pflops[2], pflops[3] + pflops[4], 0.0]
     dom = max(range(5), key=lambda k: pass_ms[k])
     fused = getattr(info, "fused", 0)
+    if getattr(info, "chunks", 1) > 1:
+        fused = (1 << 1) | (1 << 4)  # interleaved in chunks: x and y of one direction timed together
     passes = {}
     for k in range(5):
         if fused & (1 << k):
-            passes[PASS_NAMES[k]] = {"fused_into": PASS_NAMES[k - 1 if k == 1 else 3], "ms": pass_ms[k]}
+            key = "fused_into" if getattr(info, "fused", 0) else "timed_with"
+            passes[PASS_NAMES[k]] = {key: PASS_NAMES[k - 1 if k == 1 else 3], "ms": pass_ms[k]}
             continue
         passes[PASS_NAMES[k]] = {"ms": pass_ms[k], "alg_bytes": pbytes[k],
                                  "GB/s": pbytes[k] / (pass_ms[k] / 1e3) / 1e9,
@@ -793,6 +798,8 @@ def main():
     ap.add_argument("--bc", default="fff",
                     help="boundary conditions of --workload bc128, x y z: any of the 8 assignments (fff, pff, fpf, "
                          "ffp, ppf, pfp, fpp, ppp)")
+    ap.add_argument("--chunks", type=int, default=0,
+                    help="chunks of z planes for the x and y passes (0: the plan's default)")
     ap.add_argument("--order", default="rule", choices=["rule", "xfirst"],
                     help="axis processing order: the paper's rule (periodic axes first) or x, y, z")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
@@ -832,7 +839,8 @@ def main():
     rho_np = _density(w, rank, bc, dt)
     rho = torch.from_numpy(rho_np).cuda()
     plan = psolver.Plan(w["n"], bc, w["h"], dt, math=args.math,
-                        order=(0, 1, 2) if args.order == "xfirst" else None)
+                        order=(0, 1, 2) if args.order == "xfirst" else None,
+                        schedule={"chunks": args.chunks} if args.chunks else None)
     if kernel is not None:
         plan.set_kernel_real(kernel)
     info = plan.info()
@@ -913,7 +921,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
         "config": {"workload": desc, "n": list(n), "bc": bc, "h": w["h"], "L": list(info.L),
-                   "order": "".join("xyz"[a] for a in info.order),
+                   "order": "".join("xyz"[a] for a in info.order), "chunks": info.chunks,
                    "math": args.math, "tensor_passes": info.tensor_passes, "blocks": list(info.blocks),
                    "l2": "flushed (512 MiB write) before every step; per-step CUDA events",
                    "pass_times": "separate profiled loop of the same K steps, one event between passes",

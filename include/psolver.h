@@ -119,11 +119,16 @@ typedef struct {
                                used when rho and V are 16-byte aligned)         */
   int order[3];             /* physical axes (0 x, 1 y, 2 z) in forward
                                processing order (ps_plan_set_order)             */
-  int schedule[5];          /* kernel schedule requested (0 = default): generic
+  int schedule[6];          /* kernel schedule requested (0 = default): generic
                                lines per tile, generic radix split (1: radix 4
                                only), lines per tile of the persistent packed z
                                kernel, y kernel form (1 unpacked persistent, 2
-                               non-persistent), fused x/y passes (1)            */
+                               non-persistent), fused x/y passes (1), chunks   */
+  int chunks;               /* chunks of z planes in which the x and y passes
+                               run (forward x then y per chunk, inverse y then
+                               x), through one chunk of the x-transformed array
+                               that stays in L2 (1: whole passes; 0 before the
+                               build; used when rho and V are 8-byte aligned)  */
 } ps_plan_info;
 
 /*
@@ -174,8 +179,9 @@ int ps_plan_set_order(ps_plan plan, int a0, int a1, int a2);
  * choice that applies to the plan is timed in turn and kept if faster: the
  * lines per tile of the generic passes, their radix split (radix 8 first or
  * radix 4 only), the lines per tile of the persistent packed z kernel, the y
- * kernel form (packed persistent, unpacked persistent, non-persistent) and
- * the fused x/y passes (see ps_plan_info.fused). One trial plan per candidate
+ * kernel form (packed persistent, unpacked persistent, non-persistent), the
+ * fused x/y passes (see ps_plan_info.fused), the chunks of the x and y passes
+ * and, for a plan whose order is not x first, the x-first order. One trial plan per candidate
  * is built on the current device and `reps` solves of it are timed on
  * `stream` (reps < 1 means 5); the choice is set on `plan` (not built; see
  * ps_plan_info.schedule). Results are cached per geometry and device in
@@ -200,9 +206,11 @@ int ps_plan_set_math(ps_plan plan, int math_mode);
  *   ztk     lines per tile of the persistent packed z kernel: 0, 8 or 16
  *   ykind   y kernels: 0 default, 1 unpacked persistent, 2 non-persistent
  *   xy      1: fused x/y passes where the shapes have them (ps_plan_info.fused)
+ *   chunks  the x and y passes chunk by chunk of z planes (2 .. 64), or whole
+ *           (0 or 1; see ps_plan_info.chunks)
  * Errors: PS_ERR_ARG (plan NULL or built, a value out of range).
  */
-int ps_plan_set_schedule(ps_plan plan, int tile, int radix, int ztk, int ykind, int xy);
+int ps_plan_set_schedule(ps_plan plan, int tile, int radix, int ztk, int ykind, int xy, int chunks);
 
 /* ps_plan_query -- fill *info (host only; valid before and after the build). */
 int ps_plan_query(ps_plan plan, ps_plan_info* info);

@@ -314,7 +314,7 @@ int ps_plan_set_math(ps_plan p, int math_mode) {
   return PS_OK;
 }
 
-int ps_plan_set_schedule(ps_plan p, int tile, int radix, int ztk, int ykind, int xy) {
+int ps_plan_set_schedule(ps_plan p, int tile, int radix, int ztk, int ykind, int xy, int chunks) {
   if (!p) return fail(PS_ERR_ARG, "plan is NULL");
   if (p->built) return fail(PS_ERR_ARG, "the schedule must be set before ps_kernel_build");
   if (tile < 0 || tile > 16 || (tile & (tile - 1)) != 0)
@@ -323,11 +323,13 @@ int ps_plan_set_schedule(ps_plan p, int tile, int radix, int ztk, int ykind, int
   if (ztk != 0 && ztk != 8 && ztk != 16) return fail(PS_ERR_ARG, "ztk = %d: 0, 8 or 16", ztk);
   if (ykind < 0 || ykind > 2) return fail(PS_ERR_ARG, "ykind = %d: 0, 1 or 2", ykind);
   if (xy != 0 && xy != 1) return fail(PS_ERR_ARG, "xy = %d: 0 or 1", xy);
+  if (chunks < 0 || chunks > 64) return fail(PS_ERR_ARG, "chunks = %d: 0 .. 64", chunks);
   p->gen_tk_max = tile;
   p->radix_pref = radix;
   p->z_tk = ztk;
   p->y_kind = ykind;
   p->xy_sched = xy;
+  p->chunk_req = chunks;
   return PS_OK;
 }
 
@@ -375,6 +377,8 @@ int ps_plan_query(ps_plan p, ps_plan_info* info) {
   info->schedule[2] = p->z_tk;
   info->schedule[3] = p->y_kind;
   info->schedule[4] = p->xy_sched;
+  info->schedule[5] = p->chunk_req;
+  info->chunks = p->built ? p->chunks : 0;
   for (int k = 0; k < 5; ++k)
     info->blocks[k] = (p->built && p->cfg[k].fast) ? (int)(p->cfg[k].grid.x * p->cfg[k].grid.y) : 0;
   if (xyf) {

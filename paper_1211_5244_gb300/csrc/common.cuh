@@ -102,6 +102,7 @@ struct PassCfg {
   const void* fn;  // the specialised kernel
   dim3 grid, block;
   int cluster;  // CTAs per thread-block cluster (0: launched without clusters)
+  int xrows;    // specialised x passes: rows per CTA
   FastArgs fa;
 };
 
@@ -168,6 +169,11 @@ struct ps_plan_s {
   int z_tk;        // lines per tile of the persistent packed z kernel (8 or 16)
   int y_kind;      // y passes: 1 unpacked persistent kernels, 2 non-persistent ones
   int radix_pref;  // generic Stockham stages: 0 radix 8 first, 1 radix 4 and 2 only
+  int chunk_req;   // chunks of z planes for the x and y passes (0: chosen by size, 1: none)
+  // the x and y passes run chunk by chunk of z planes (x then y for each
+  // chunk forward, y then x inverse) through the first chunk's rows of A, which
+  // stay in L2 between the two passes; 1: whole passes
+  int chunks;
   // per-pass timing (ps_plan_set_profiling): 6 events per recorded solve
   bool profiling;
   std::vector<cudaEvent_t> events;

@@ -88,5 +88,9 @@ cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, doub
                         cudaStream_t s);
 // Launches the fused forward (kind 0: rho -> B) or inverse (kind 1: B -> V) x/y kernel.
 cudaError_t launch_xy(ps_plan_s* p, int kind, const void* src, void* dst, cudaStream_t s);
+// Launches x pass P1 / P5 or y pass P2 / P4 on the z planes z0 .. z0 + nz - 1:
+// rho, V and B at those planes, A (src or dst) at its first plane.
+cudaError_t launch_fast_chunk(ps_plan_s* p, int pass, const void* rhoV, void* B, void* A, int z0, int nz,
+                              cudaStream_t s);
 
 }  // namespace ps

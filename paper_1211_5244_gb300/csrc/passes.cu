@@ -22,6 +22,7 @@
 // axis of A and B, so every global access is a run of tk consecutive complex
 // numbers. K^F is stored once, scaled by 1/(L1 L2 L3), as its even octant in
 // the [kz][ky][kx] layout the z pass reads (§3: the transposed kernel).
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 
@@ -516,6 +517,37 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   // the forward one copies rows of rho in 16-byte pieces
   const bool xyf = p->xyfuse && ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(V)) & 15) == 0;
   cudaError_t e;
+  auto pass3 = [&]() -> cudaError_t {
+    if (p->cfg[P3].fast) return launch_fast(p, P3, B, B, E, escale, s);
+    GenArgs a = gen_args<T>(p, P3);
+    dim3 g((p->c + a.tk - 1) / a.tk, p->L[1]);
+    pz_generic<T><<<g, p->cfg[P3].threads, p->cfg[P3].gsmem, s>>>(B, static_cast<const T*>(p->K), tw2, a,
+                                                                 p->partials, p->counter, escale, E);
+    return cudaGetLastError();
+  };
+  if (!xyf && a8 && p->chunks > 1) {
+    // x and y passes chunk by chunk of z planes through the first chunk of A
+    const int n3 = p->n[2];
+    const int nz = (n3 + p->chunks - 1) / p->chunks;
+    if (ev) cudaEventRecord(ev[0], s);
+    for (int z0 = 0; z0 < n3; z0 += nz) {
+      const int cz = std::min(nz, n3 - z0);
+      if ((e = launch_fast_chunk(p, P1, rho, B, A, z0, cz, s)) != cudaSuccess) return e;
+      if ((e = launch_fast_chunk(p, P2, rho, B, A, z0, cz, s)) != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if ((e = pass3()) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], s);
+    for (int z0 = 0; z0 < n3; z0 += nz) {
+      const int cz = std::min(nz, n3 - z0);
+      if ((e = launch_fast_chunk(p, P4, V, B, A, z0, cz, s)) != cudaSuccess) return e;
+      if ((e = launch_fast_chunk(p, P5, V, B, A, z0, cz, s)) != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[4], s);
+    if (ev) cudaEventRecord(ev[5], s);
+    return cudaGetLastError();
+  }
   if (ev) cudaEventRecord(ev[0], s);
   // P1
   if (xyf) {
@@ -540,14 +572,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   }
   if (ev) cudaEventRecord(ev[2], s);
   // P3
-  if (p->cfg[P3].fast) {
-    if ((e = launch_fast(p, P3, B, B, E, escale, s)) != cudaSuccess) return e;
-  } else {
-    GenArgs a = gen_args<T>(p, P3);
-    dim3 g((p->c + a.tk - 1) / a.tk, p->L[1]);
-    pz_generic<T><<<g, p->cfg[P3].threads, p->cfg[P3].gsmem, s>>>(
-        B, static_cast<const T*>(p->K), tw2, a, p->partials, p->counter, escale, E);
-  }
+  if ((e = pass3()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], s);
   // P4
   if (xyf) {

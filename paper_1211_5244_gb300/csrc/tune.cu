@@ -15,12 +15,13 @@
 //   ztk     lines per tile of the persistent packed z kernel (8 or 16)
 //   ykind   y kernels: packed persistent, unpacked persistent, non-persistent
 //   xy      the fused x/y passes (thread-block clusters) or the separate ones
+//   chunks  the x and y passes whole or in chunks of z planes (L2 reuse)
 //   order   the plan's processing order of the axes (§3's rule by default), or
 //           x first, which runs the specialised FP32 kernels where the
 //           lengths have them (more 1D transforms, faster kernels)
 // Results are kept in memory, and in a text file when PS_TUNE_CACHE names one
 // (one line per geometry: "n1 n2 n3 bc1 bc2 bc3 mode sms L1 L2 L3 tile radix
-// ztk ykind xy xfirst", mode = dtype + 2 math + 4 (the plan's order as
+// ztk ykind xy xfirst chunks", mode = dtype + 2 math + 4 (the plan's order as
 // 9 a0 + 3 a1 + a2), 0 for a default choice).
 #include <algorithm>
 #include <cstdio>
@@ -37,7 +38,7 @@ namespace ps {
 namespace {
 
 // a tuned choice: padded lengths and the schedule fields of the plan
-enum { kL1, kL2, kL3, kTile, kRadix, kZtk, kYkind, kXy, kXfirst, kFields };
+enum { kL1, kL2, kL3, kTile, kRadix, kZtk, kYkind, kXy, kXfirst, kChunks, kFields };
 
 std::mutex g_tune_mu;
 std::map<std::string, std::vector<int>> g_tuned;
@@ -65,8 +66,9 @@ void load_file() {
   char line[256];
   while (fgets(line, sizeof line, f)) {
     int n[3], bc[3], dt, sms, v[kFields] = {};
-    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &n[0], &n[1], &n[2], &bc[0],
-                           &bc[1], &bc[2], &dt, &sms, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8]);
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &n[0], &n[1], &n[2],
+                           &bc[0], &bc[1], &bc[2], &dt, &sms, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
+                           &v[8], &v[9]);
     if (got != 8 + kFields) continue;
     char key[128];
     snprintf(key, sizeof key, "%d %d %d %d %d %d %d %d", n[0], n[1], n[2], bc[0], bc[1], bc[2], dt, sms);
@@ -95,6 +97,7 @@ int apply_choice(ps_plan p, const std::vector<int>& v) {
   p->z_tk = v[kZtk];
   p->y_kind = v[kYkind];
   p->xy_sched = v[kXy];
+  p->chunk_req = v[kChunks];
   if (v[kXfirst]) return ps_plan_set_order(p, 0, 1, 2);
   return PS_OK;
 }
@@ -105,6 +108,7 @@ struct Applies {
   bool zpipe = false;    // the z pass runs the persistent packed kernel
   bool ypacked = false;  // the y passes run the packed persistent kernels
   bool xy = false;       // the fused x/y kernels run
+  bool chunkable = false;  // the x and y passes may run in chunks of z planes
 };
 
 }  // namespace
@@ -184,6 +188,8 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
         ap->zpipe = tp->zsoa_T == 16 && tp->cfg[P3].fast && !tp->tctab;
         ap->ypacked = tp->ysoa == 3;
         ap->xy = tp->xyfuse != 0;
+        ap->chunkable = !tp->xyfuse && tp->cfg[P1].fast && tp->cfg[P2].fast && tp->cfg[P4].fast &&
+                        tp->cfg[P5].fast && tp->cfg[P2].fa.nrows == tp->n[2] && tp->n[2] >= 4;
       }
     }
     if (tp) ps_plan_destroy(tp);
@@ -214,7 +220,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
     if (ok && std::find(cands.begin(), cands.end(), v) == cands.end()) cands.push_back(v);
   }
   float best_ms = -1.f;
-  std::vector<int> best = {p->L[0], p->L[1], p->L[2], 0, 0, 0, 0, 0, 0};
+  std::vector<int> best = {p->L[0], p->L[1], p->L[2], 0, 0, 0, 0, 0, 0, 0};
   Applies best_ap;
   for (size_t c = 0; e == cudaSuccess && rc == PS_OK && c < cands.size(); ++c) {
     float ms;
@@ -266,6 +272,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
     try_field(kRadix, {1});
   }
   if (best_ap.zpipe) try_field(kZtk, {16});
+  if (best_ap.chunkable) try_field(kChunks, {2, 4});
   if (best_ap.ypacked) try_field(kYkind, {1, 2});
   {
     // the fused x/y passes: only where the plan's shapes have them

@@ -40,7 +40,7 @@ class PlanInfo(ctypes.Structure):
         ("paper_full_points", ctypes.c_double), ("alg_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_int),
         ("tensor_passes", ctypes.c_int), ("blocks", ctypes.c_int * 5), ("fused", ctypes.c_int),
-        ("order", ctypes.c_int * 3), ("schedule", ctypes.c_int * 5),
+        ("order", ctypes.c_int * 3), ("schedule", ctypes.c_int * 6), ("chunks", ctypes.c_int),
     ]
 
 
@@ -62,7 +62,7 @@ def load_library():
         "ps_plan_create": [i, i, i, d, i, i, i, i, ctypes.POINTER(vp)],
         "ps_plan_set_lengths": [vp, i, i, i],
         "ps_plan_set_math": [vp, i],
-        "ps_plan_set_schedule": [vp, i, i, i, i, i],
+        "ps_plan_set_schedule": [vp, i, i, i, i, i, i],
         "ps_plan_set_order": [vp, i, i, i],
         "ps_plan_autotune": [vp, i, vp],
         "ps_plan_query": [vp, ctypes.POINTER(PlanInfo)],
@@ -143,9 +143,10 @@ class Plan:
         if build:
             self.build(stream)
 
-    def set_schedule(self, tile=0, radix=0, ztk=0, ykind=0, xy=0):
+    def set_schedule(self, tile=0, radix=0, ztk=0, ykind=0, xy=0, chunks=0):
         """ps_plan_set_schedule: the kernel schedule by hand (before the build)."""
-        _check(_lib.ps_plan_set_schedule(self._h, int(tile), int(radix), int(ztk), int(ykind), int(xy)))
+        _check(_lib.ps_plan_set_schedule(self._h, int(tile), int(radix), int(ztk), int(ykind), int(xy),
+                                         int(chunks)))
         return self
 
     # ------------------------------------------------------------ lifecycle

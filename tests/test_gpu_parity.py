@@ -388,6 +388,30 @@ def test_parity_fused_xy(torch_cuda, n, bc, math):
     assert torch.equal(V, V2)
 
 
+# The x and y passes chunk by chunk of z planes (x then y per chunk forward,
+# y then x inverse, through one chunk of A): ragged last chunks, one plane per
+# chunk, and the default count of the 256^3 workload.
+CHUNK_CASES = [
+    ((256, 256, 20), "fff", 3, 3),     # chunks of 7, 7, 6 planes (y packed persistent L = 512)
+    ((64, 128, 40), "fff", 4, 4),      # y unpacked persistent L = 256, x M = 64
+    ((128, 128, 17), "pff", 17, 17),   # one plane per chunk
+    ((96, 256, 24), "ppf", 5, 1),      # x M = 48 on the generic kernels: chunks do not apply
+    ((256, 512, 12), "fpf", 2, 2),     # y packed full L = 512
+]
+
+
+@pytest.mark.parametrize("n,bc,chunks,used", CHUNK_CASES)
+def test_parity_chunked_xy_passes(torch_cuda, n, bc, chunks, used):
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=53 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    plan = psolver.Plan(n, bc, 0.25, "f32", schedule={"chunks": chunks}, order=XFIRST)
+    info = plan.info()
+    assert info.chunks == used, (info.chunks, list(info.blocks))
+    V, E = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.25, "f32")
+
+
 @pytest.mark.parametrize("n,bc,off", [((64, 48, 40), "fff", 1), ((128, 20, 18), "pff", 1), ((512, 6, 5), "fff", 1),
                                       ((256, 256, 6), "fff", 1), ((256, 256, 6), "fff", 2)])
 def test_parity_rho_v_not_8_byte_aligned(torch_cuda, n, bc, off):
