@@ -55,10 +55,9 @@ PASS_NAMES = ["p1_fwd_x_r2c", "p2_fwd_y", "p3_z_fwd_mul_inv", "p4_inv_y", "p5_in
 Z_KERNEL_FILES = ("fast_zsoa.cu", "fft_soa.cuh", "fft_regs.cuh", "fft_fast.cuh", "reduce.cuh", "common.cuh",
                   "../../include/psolver.h")
 TRAFFIC = {
-    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 364461824 + 218542592, "files": Z_KERNEL_FILES,
-                                          "src": "60afe10d8806bbaa"},
+    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 367507200 + 221845504, "files": Z_KERNEL_FILES,
+                                          "src": "931f189342b6617e"},
 }
-
 
 def _src_hash(files=None):
     """Hash of the CUDA sources (all of them, or the named files)."""
@@ -798,6 +797,8 @@ def main():
     ap.add_argument("--bc", default="fff",
                     help="boundary conditions of --workload bc128, x y z: any of the 8 assignments (fff, pff, fpf, "
                          "ffp, ppf, pfp, fpp, ppp)")
+    ap.add_argument("--xy", type=int, default=0, choices=[0, 1],
+                    help="1: the fused x/y kernels (thread-block clusters) where the shapes have them")
     ap.add_argument("--chunks", type=int, default=0,
                     help="chunks of z planes for the x and y passes (0: the plan's default)")
     ap.add_argument("--order", default="rule", choices=["rule", "xfirst"],
@@ -840,7 +841,7 @@ def main():
     rho = torch.from_numpy(rho_np).cuda()
     plan = psolver.Plan(w["n"], bc, w["h"], dt, math=args.math,
                         order=(0, 1, 2) if args.order == "xfirst" else None,
-                        schedule={"chunks": args.chunks} if args.chunks else None)
+                        schedule=({"chunks": args.chunks, "xy": args.xy} if (args.chunks or args.xy) else None))
     if kernel is not None:
         plan.set_kernel_real(kernel)
     info = plan.info()
