@@ -118,6 +118,7 @@ struct ps_plan_s {
   // the reverse order
   int ord[3];
   int ext1[3], ext2[3];  // extents (x, y, z) of the arrays after the first and second forward passes
+  int fastord;           // an order other than x, y, z that starts with x runs the specialised kernels
   size_t ld1, ld2;       // their x pitch in complex elements
   int H[3];      // L/2 (floor): last index of the even octant per axis
   int c;         // L1/2 + 1

@@ -299,9 +299,20 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     return cudaSuccess;
   };
   FastArgs base{};
-  // passes that read what the previous pass wrote last first (PS_L2ORDER=0: off)
+  // the processing order starts with x (the R2C); b and c are its second and
+  // third axes (y and z by default; z and y for the surface assignment pfp
+  // under the axis rule), reached through strides: the y-pass kernels run
+  // along b, the z-pass kernels along c
+  const bool canon = canonical_order(p);
+  const int ab = p->ord[1], ac = p->ord[2];
+  const int nb = p->n[ab], Lb = p->L[ab], nc = p->n[ac], Lc = p->L[ac];
+  const long long sA[3] = {1, ldc, (long long)n2 * ldc};               // A: [z][y][kx]
+  const long long sB[3] = {1, ldc, (long long)p->ext2[1] * ldc};       // B: axis b at its padded length
+  const long long Ks[3] = {1, (long long)p->ldk, (long long)(p->H[1] + 1) * p->ldk};  // K^F octant
+  // passes that read what the previous pass wrote last first (PS_L2ORDER=0:
+  // off); with x, y, z only
   const char* l2o = getenv("PS_L2ORDER");
-  const int l2order = (l2o && atoi(l2o) == 0) ? 0 : 1;
+  const int l2order = (!canon || (l2o && atoi(l2o) == 0)) ? 0 : 1;
   base.c = p->c;
   base.L1 = L1;
   base.L2 = L2;
@@ -329,58 +340,58 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       p->xP = M == 32 ? 8 : (M == 64 ? 8 : (M == 128 ? 16 : (M == 256 ? 16 : 32)));
       dim3 grid((n2 * n3 + rows - 1) / rows);
       FastArgs xinv = base;
-      xinv.rev = l2order;  // the inverse y pass wrote the last z planes last
+      xinv.rev = l2order;  // the inverse y pass wrote the last z planes last (x, y, z order)
       if ((e = set(P1, f0, grid, threads, smem, base)) != cudaSuccess) return e;
       if ((e = set(P5, f1, grid, threads, smem, xinv)) != cudaSuccess) return e;
       p->cfg[P1].xrows = p->cfg[P5].xrows = rows;
     }
   }
-  // y passes
-  // y passes: n2 <= L2/2 (zero padding) or n2 = L2 (periodic)
-  if (pow2(L2) && (n2 <= L2 / 2 || n2 == L2)) {
-    const bool half = n2 <= L2 / 2;
+  // y passes (along b): nb <= Lb/2 (zero padding) or nb = Lb (periodic)
+  if (pow2(Lb) && (nb <= Lb / 2 || nb == Lb)) {
+    const bool half = nb <= Lb / 2;
     int threads0 = 0, threads1 = 0;
     size_t smem0 = 0, smem1 = 0;  // the forward and inverse kernels may differ
     // persistent prefetching kernels where they exist: the packed FP32x2 ones
-    // at L2 = 512 (n2 = L2/2 or L2; at 256^3 forward 76.5 against 83 us for
-    // the unpacked kernel, inverse 79.9 against 80.2 us), the unpacked ones at
-    // L2 = 256 and counts below L2/2. The plan's schedule y_kind = 1 takes the
+    // at L = 512 (n = L/2 or L; at 256^3 forward 76.5 against 83 us for the
+    // unpacked kernel, inverse 79.9 against 80.2 us), the unpacked ones at
+    // L = 256 and counts below L/2. The plan's schedule y_kind = 1 takes the
     // unpacked persistent kernels for both directions, y_kind = 2 the
     // non-persistent ones.
     const bool plain = p->y_kind == 2;
-    const bool exact = 2 * n2 == L2 || n2 == L2;
+    const bool exact = 2 * nb == Lb || nb == Lb;
     const bool soa0 = !plain && exact && p->y_kind != 1;
     const bool soa1 = soa0;
     int tk0 = 16, tk1 = 16;  // lines per tile (kx columns) of the chosen kernels
-    const void* f0 = soa0 ? ysoa_kernel(L2, 0, half, &threads0, &smem0) : nullptr;
-    const void* f1 = soa1 ? ysoa_kernel(L2, 1, half, &threads1, &smem1) : nullptr;
+    const void* f0 = soa0 ? ysoa_kernel(Lb, 0, half, &threads0, &smem0) : nullptr;
+    const void* f1 = soa1 ? ysoa_kernel(Lb, 1, half, &threads1, &smem1) : nullptr;
     p->ysoa = (f0 ? 1 : 0) | (f1 ? 2 : 0);
-    if (!f0 && !plain) f0 = ypipe_kernel(L2, 0, half, &threads0, &smem0, &tk0);
-    if (!f1 && !plain) f1 = ypipe_kernel(L2, 1, half, &threads1, &smem1, &tk1);
+    if (!f0 && !plain) f0 = ypipe_kernel(Lb, 0, half, &threads0, &smem0, &tk0);
+    if (!f1 && !plain) f1 = ypipe_kernel(Lb, 1, half, &threads1, &smem1, &tk1);
     const bool ypersist = f0 && f1;
     if (!ypersist) {
       p->ysoa = 0;
-      f0 = strided_kernel(L2, 0, half, &threads0, &smem0, &tk0);
-      f1 = strided_kernel(L2, 1, half, &threads1, &smem1, &tk1);
+      f0 = strided_kernel(Lb, 0, half, &threads0, &smem0, &tk0);
+      f1 = strided_kernel(Lb, 1, half, &threads1, &smem1, &tk1);
     }
     if (f0 && f1) {
       FastArgs fwd = base, inv = base;
       fwd.ntk_loc = (p->c + tk0 - 1) / tk0;
       inv.ntk_loc = (p->c + tk1 - 1) / tk1;
-      fwd.nl = inv.nl = n2;
+      fwd.nl = inv.nl = nb;
       fwd.rev = l2order;  // the x pass wrote the last z planes last
-      fwd.src_plane = (long long)n2 * ldc; fwd.src_elem = ldc;   // A[z][y][kx]
-      fwd.dst_plane = (long long)L2 * ldc; fwd.dst_elem = ldc;   // B[z][ky][kx]
-      inv.src_plane = (long long)L2 * ldc; inv.src_elem = ldc;
-      inv.dst_plane = (long long)n2 * ldc; inv.dst_elem = ldc;
-      dim3 grid0(fwd.ntk_loc, n3), grid1(inv.ntk_loc, n3);
+      // lines along b, one plane per index along c, tiles across kx
+      fwd.src_plane = sA[ac]; fwd.src_elem = sA[ab];   // A
+      fwd.dst_plane = sB[ac]; fwd.dst_elem = sB[ab];   // B
+      inv.src_plane = sB[ac]; inv.src_elem = sB[ab];
+      inv.dst_plane = sA[ac]; inv.dst_elem = sA[ab];
+      dim3 grid0(fwd.ntk_loc, nc), grid1(inv.ntk_loc, nc);
       if (ypersist) {
-        fwd.nrows = inv.nrows = n3;  // z planes walked by the persistent CTAs
+        fwd.nrows = inv.nrows = nc;  // planes walked by the persistent CTAs
         int dev = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         auto persistent_grid = [&](const void* f, int threads, size_t smem, int ntk_f, dim3* grid) -> cudaError_t {
-          const long long tiles = (long long)ntk_f * n3;
+          const long long tiles = (long long)ntk_f * nc;
           cudaError_t err = cudaSuccess;
           if (smem > 48 * 1024 &&
               (err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -410,7 +421,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   p->xyfuse = 0;
   {
     const bool allow = p->xy_sched == 1;
-    if (allow && L1 == 512 && (n1 == 256 || n1 == 512) && L2 == 512 && n2 == 256 && p->xP == 16 &&
+    if (allow && canon && L1 == 512 && (n1 == 256 || n1 == 512) && L2 == 512 && n2 == 256 && p->xP == 16 &&
         (p->ysoa & 3) == 3 && p->cfg[P1].fast && p->cfg[P5].fast) {
       bool ok = true;
       for (int kind = 0; kind < 2 && ok; ++kind) {
@@ -469,13 +480,13 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   // to the x kernel and leaves the persistent y kernel under two tiles per
   // CTA), so it runs when the schedule's chunk_req asks for it.
   p->chunks = 1;
-  if (!p->xyfuse && p->cfg[P1].fast && p->cfg[P2].fast && p->cfg[P4].fast && p->cfg[P5].fast &&
+  if (canon && !p->xyfuse && p->cfg[P1].fast && p->cfg[P2].fast && p->cfg[P4].fast && p->cfg[P5].fast &&
       p->cfg[P2].fa.nrows == n3 && p->cfg[P4].fa.nrows == n3 && p->chunk_req > 1)
     p->chunks = std::min(p->chunk_req, n3);
   // z pass on the tensor cores (PS_MATH_TF32X3, L3 = 512): persistent, one
   // wave of resident CTAs over tiles of 8 kx lines
   p->tctab_floats = 0;
-  if (p->math == PS_MATH_TF32X3 && L3 == 512 && (n3 == 256 || n3 == 512)) {
+  if (canon && p->math == PS_MATH_TF32X3 && L3 == 512 && (n3 == 256 || n3 == 512)) {
     const bool half = n3 == 256;
     int threads;
     size_t smem;
@@ -509,31 +520,36 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       return cudaSuccess;
     }
   }
-  // z pass: the persistent prefetching packed kernel where it exists (L3 = 128
-  // and 512), the persistent unpacked one at L3 = 256 and 1024, else the
-  // non-persistent unpacked one.
-  if (pow2(L3) && (n3 <= L3 / 2 || n3 == L3)) {
-    const bool half = n3 <= L3 / 2;
+  // z pass (along c): the persistent prefetching packed kernel where it
+  // exists (L = 128 and 512), the persistent unpacked one at L = 256 and
+  // 1024, else the non-persistent unpacked one
+  if (pow2(Lc) && (nc <= Lc / 2 || nc == Lc)) {
+    const bool half = nc <= Lc / 2;
     int threads;
     size_t smem;
     // lines per tile of the persistent packed kernel: 8 (four CTAs of 42 KB
     // per SM; at 256^3 228 us against 251 us for 16 lines and 280 us for 4),
     // or 16 where the plan's schedule z_tk asks for it
     int pipe_tk = p->z_tk == 16 ? 16 : 8;
-    const void* f = zpipe_kernel(L3, half, &pipe_tk, &threads, &smem);
+    const void* f = zpipe_kernel(Lc, half, &pipe_tk, &threads, &smem);
     bool persistent = f != nullptr;
-    p->zsoa_T = f ? (L3 == 128 ? 8 : 16) : 0;
+    p->zsoa_T = f ? (Lc == 128 ? 8 : 16) : 0;
     int ztile = pipe_tk;
-    // L3 = 256 and 1024: the persistent unpacked kernel
-    if (!f && (f = zpipe_u_kernel(L3, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
-    if (!f) f = strided_kernel(L3, 2, half, &threads, &smem, &ztile);
+    // L = 256 and 1024: the persistent unpacked kernel
+    if (!f && (f = zpipe_u_kernel(Lc, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
+    if (!f) f = strided_kernel(Lc, 2, half, &threads, &smem, &ztile);
     if (f) {
       FastArgs z = base;
-      z.nl = n3;
+      z.nl = nc;
       z.ntk_loc = (p->c + ztile - 1) / ztile;
-      z.src_plane = ldc; z.src_elem = (long long)L2 * ldc;      // B[z][ky][kx], line along z
-      z.dst_plane = ldc; z.dst_elem = (long long)L2 * ldc;
-      dim3 grid((p->c + ztile - 1) / ztile, L2);
+      // lines along c, tile rows along b (Lb of them, paired k and Lb - k),
+      // tiles across kx; K^F octant strides of the row and the line axis
+      z.src_plane = sB[ab]; z.src_elem = sB[ac];
+      z.dst_plane = sB[ab]; z.dst_elem = sB[ac];
+      z.L2 = Lb;
+      z.ldk = (int)Ks[ab];
+      z.kz_stride = Ks[ac];
+      dim3 grid((p->c + ztile - 1) / ztile, Lb);
       if (persistent) {
         // one wave of resident CTAs walks all tiles
         if (smem > 48 * 1024 &&
@@ -643,7 +659,7 @@ cudaError_t launch_fast_chunk(ps_plan_s* p, int pass, const void* rhoV, void* B,
     cf.grid = dim3((unsigned)std::min<long long>(cf.grid.x, tiles));
   }
   const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
-  const int axis = (pass == P1 || pass == P5) ? 0 : 1;
+  const int axis = pass_axis(p, pass);
   const void* tw = ((pass == P2 && (p->ysoa & 1)) || (pass == P4 && (p->ysoa & 2))) ? p->tw4y : p->tw[axis];
   return launch_cfg(cf, fa, src, dst, K, tw, p->partials, p->counter, 0.0, nullptr, s);
 }
@@ -651,7 +667,7 @@ cudaError_t launch_fast_chunk(ps_plan_s* p, int pass, const void* rhoV, void* B,
 cudaError_t launch_fast(ps_plan_s* p, int pass, const void* src, void* dst, double* E, double escale,
                         cudaStream_t s) {
   PassCfg& cf = p->cfg[pass];
-  const int axis = (pass == P1 || pass == P5) ? 0 : (pass == P3 ? 2 : 1);
+  const int axis = pass_axis(p, pass);
   // x passes get the twiddle matrix in the K slot
   const float* K = static_cast<const float*>((pass == P1 || pass == P5) ? p->twx : p->K);
   const void* tw = (pass == P3 && p->tctab) ? p->tctab

@@ -482,11 +482,25 @@ cudaError_t configure_passes(ps_plan_s* p) {
   if ((e = cudaFuncSetAttribute(py_generic<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(pz_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(p5_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  p->fastord = 0;
   if (!canonical_order(p)) {
     // the generic kernels along strided axes (passes_ord.cu); energy
     // partials: one per CTA of the fused pass
     p->npart = ord_conv_ctas(p);
-    return configure_ord<T>(p);
+    if ((e = configure_ord<T>(p)) != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4) {
+      // x first (x, z, y): the specialised x kernels, and the y- and z-pass
+      // kernels along z and y through strides, when all three middle passes have them
+      if (p->ord[0] == 0) {
+        if ((e = configure_fast_f32(p)) != cudaSuccess) return e;
+        p->fastord = p->cfg[P2].fast && p->cfg[P3].fast && p->cfg[P4].fast;
+        if (p->fastord) {
+          const int ntk = (p->c + p->cfg[P3].tk - 1) / p->cfg[P3].tk;
+          p->npart = std::max(p->npart, ntk * p->L[p->ord[1]]);
+        }
+      }
+    }
+    return cudaSuccess;
   }
   if constexpr (sizeof(T) == 4) {
     e = configure_fast_f32(p);
@@ -502,7 +516,7 @@ template <typename T>
 cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream_t s,
                          cudaEvent_t* ev) {
   using C = cpx<T>;
-  if (!canonical_order(p)) return launch_solve_ord<T>(p, rho, V, E, s, ev);
+  if (!canonical_order(p) && !p->fastord) return launch_solve_ord<T>(p, rho, V, E, s, ev);
   C* A = static_cast<C*>(p->A);
   C* B = static_cast<C*>(p->B);
   const C* tw0 = static_cast<const C*>(p->tw[0]);

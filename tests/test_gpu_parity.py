@@ -84,6 +84,29 @@ def test_parity_every_processing_order(torch_cuda, n, bc, order, dtype):
     _check(V, E, rho, bc, 0.33, dtype)
 
 
+# x first, then z, then y (the axis rule for pfp, or set by hand): the
+# specialised FP32 kernels along z and y through strides, K^F read with its
+# ky and kz strides swapped; packed, persistent and register kernels on both.
+XZY_CASES = [
+    ((64, 128, 64), "pfp", (0, 2, 1)),     # z L = 64 (register y-pass kernel), y L = 256 (persistent unpacked)
+    ((128, 256, 256), "pfp", (0, 2, 1)),   # z L = 256 persistent, y L = 512 packed persistent
+    ((64, 64, 128), "fff", (0, 2, 1)),     # z L = 256 half, y L = 128 packed
+    ((32, 40, 512), "ppf", (0, 2, 1)),     # y periodic 40: generic strided passes, x on the register kernels
+]
+
+
+@pytest.mark.parametrize("n,bc,order", XZY_CASES)
+def test_parity_fast_kernels_x_z_y(torch_cuda, n, bc, order):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=61 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", order=order)
+    info = plan.info()
+    assert tuple(info.order) == order
+    pow2 = lambda v: v & (v - 1) == 0
+    if pow2(info.L[1]) and pow2(info.L[2]):
+        assert all(b > 0 for b in info.blocks), list(info.blocks)  # every pass on a specialised kernel
+    _check(V, E, rho, bc, 0.25, "f32")
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("n,bc", [((31, 17, 13), "ppp"), ((29, 23, 11), "pff"), ((157, 5, 6), "pfp"),
                                   ((24, 131, 7), "ppf")])
