@@ -36,25 +36,27 @@ def _errs(V, Vo):
 
 
 CASES = [
-    ((37, 29, 23), "fff", "f64"),
-    ((20, 17, 12), "pfp", "f64"),
-    ((9, 14, 11), "ppp", "f64"),
-    ((16, 24, 9), "ppp", "f32"),
-    ((64, 40, 32), "fff", "f32"),   # specialised FP32 kernels
-    ((33, 18, 21), "fpf", "f32"),
-    ((12, 5, 64), "fpf", "f32"),    # odd L2 with the packed z kernel
+    ((37, 29, 23), "fff", "f64", None),
+    ((20, 17, 12), "pfp", "f64", None),       # the axis rule's order x z y
+    ((9, 14, 11), "ppp", "f64", None),
+    ((16, 24, 9), "ppp", "f32", None),
+    ((64, 40, 32), "fff", "f32", None),       # specialised FP32 kernels
+    ((33, 18, 21), "fpf", "f32", None),       # order y x z: R2C along y, conv along z
+    ((24, 16, 20), "ffp", "f64", None),       # order z x y: conv along y
+    ((12, 5, 64), "fpf", "f32", (0, 1, 2)),   # x first: odd L2 with the packed z kernel
+    ((64, 128, 64), "pfp", "f32", None),      # x z y on the specialised kernels
 ]
 
 
-@pytest.mark.parametrize("n,bc,dtype", CASES)
-def test_custom_kernel_matches_oracle(torch_cuda, n, bc, dtype):
+@pytest.mark.parametrize("n,bc,dtype,order", CASES)
+def test_custom_kernel_matches_oracle(torch_cuda, n, bc, dtype, order):
     from paper_1211_5244_gb300 import psolver
     torch = torch_cuda
     h = 0.3
     k = _octant(n, bc, seed=sum(n))
     rho = synth.gaussian_mixture(n, h, 4, seed=2 + sum(n), noise=1e-3)
     npdt = np.float32 if dtype == "f32" else np.float64
-    plan = psolver.Plan(n, bc, h, dtype).set_kernel_real(k)
+    plan = psolver.Plan(n, bc, h, dtype, order=order).set_kernel_real(k)
     V, E = plan.solve(torch.from_numpy(rho.astype(npdt)).cuda())
     rho_seen = rho.astype(npdt).astype(np.float64)
     Vo, Eo = op.convolve(rho_seen, bc, h, k)

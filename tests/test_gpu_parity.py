@@ -233,6 +233,40 @@ def test_batched_mixed_dtypes_match_oracle(torch_cuda, monkeypatch, order):
         assert torch.equal(V, V1) and torch.equal(E, E1)
 
 
+def test_batched_every_assignment_matches_oracle(torch_cuda):
+    """A batch over all 8 free/periodic assignments (each plan in the axis
+    rule's order, so generic strided passes, the specialised kernels and the
+    x z y order share one graph), FP32 and FP64, against the oracle."""
+    torch = torch_cuda
+    from paper_1211_5244_gb300 import psolver
+    plans, rhos, meta = [], [], []
+    for i, bc in enumerate(ALL_BCS):
+        for dtype, n in (("f32", (32, 64, 32)), ("f64", (14 + i, 11, 9 + i))):
+            plans.append(psolver.Plan(n, bc, 0.3, dtype))
+            r = synth.gaussian_mixture(n, 0.3, 3, seed=70 + i, noise=1e-3, subtract_mean="p" in bc)
+            rhos.append(torch.from_numpy(r.astype(_np_dtype(dtype))).cuda())
+            meta.append((bc, dtype))
+    Vs, Es = psolver.solve_batched(plans, rhos)
+    torch.cuda.synchronize()
+    for (bc, dtype), r, V, E in zip(meta, rhos, Vs, Es):
+        _check(V.double().cpu().numpy(), float(E.item()), r.double().cpu().numpy(), bc, 0.3, dtype)
+
+
+@pytest.mark.parametrize("n,bc", [((64, 64, 32), "ffp"), ((32, 64, 64), "fpp")])
+def test_autotuned_order_matches_oracle(torch_cuda, n, bc):
+    """FP32 power-of-two shapes whose rule order starts with y or z: the
+    autotuner may keep the rule's order or take x first (the specialised
+    kernels); either way the result is the oracle's."""
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    rule = psolver.Plan(n, bc, 0.3, "f32", build=False).info().order
+    plan = psolver.Plan(n, bc, 0.3, "f32", autotune=True)
+    assert tuple(plan.info().order) in (tuple(rule), (0, 1, 2))
+    rho = synth.gaussian_mixture(n, 0.3, 4, seed=9, noise=1e-3, subtract_mean=True)
+    V, E = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, "f32")
+
+
 def test_batched_c4_workload_matches_oracle(torch_cuda):
     """The uneven batch of the benchmark recipe: 64 FP32 problems, n ~ U{24..160}
     per axis (primes such as 131, 137 and 157 among them), boundary conditions
