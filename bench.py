@@ -950,11 +950,18 @@ def main():
     headline = args.workload == WORKLOAD and dt == "f32" and args.math == "cudacore"
     if headline and not args.no_extras:
         # the same workload with the z pass on the tensor cores (TF32 split
-        # products), timed the same way, and its error against the same oracle
-        line["tf32x3"] = _tf32x3_measure(w, bc, rho, K, args.warmup, flush, stream, dist, ref)
-        # the uneven batched workload, timed the same way, every item against the oracle
-        line["batched64"] = _batched_measure(K, args.warmup, rank, dist,
-                                             with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        # products), timed the same way, and its error against the same oracle;
+        # then the uneven batched workload, every item against the oracle. A
+        # failure in either is reported in its object; the headline stands.
+        try:
+            line["tf32x3"] = _tf32x3_measure(w, bc, rho, K, args.warmup, flush, stream, dist, ref)
+        except Exception as exc:
+            line["tf32x3"] = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            line["batched64"] = _batched_measure(K, args.warmup, rank, dist,
+                                                 with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        except Exception as exc:
+            line["batched64"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
