@@ -14,6 +14,7 @@ HBM roofline of the dominant kernel and of the whole solve.
 Other workloads (one JSON line each, same keys):
     --workload free512      512^3 free FP32 (padded FFT 1024^3)
     --workload bc128 --bc B 128^3, B in fff / pff (wire) / ppf (surface) / ppp
+                            (--n NX,NY,NZ: another grid with the same recipe)
     --workload hartree192   192^3 free: forward solve + adjoint backward
                             (torch.autograd through ps_solve_vjp) per step
     --workload localpot256  the 256^3 solve with a caller's even kernel
@@ -524,6 +525,11 @@ def _spec(args):
         if len(args.bc) != 3 or any(b not in "pf" for b in args.bc):
             raise SystemExit("--bc must name the x, y, z axes with p / f, e.g. pff")
         w, bc = {k: w0[k] for k in ("n", "h", "n_gauss", "noise", "seed")}, args.bc
+        if args.n:
+            n = tuple(int(v) for v in args.n.split(","))
+            if len(n) != 3 or min(n) < 2:
+                raise SystemExit("--n must give three sizes >= 2, e.g. 128,128,512")
+            w["n"] = n
     kernel = _localpot_octant(w) if args.workload == "localpot256" else None
     return w, bc, kernel
 
@@ -803,6 +809,8 @@ def main():
                     help="chunks of z planes for the x and y passes (0: the plan's default)")
     ap.add_argument("--order", default="rule", choices=["rule", "xfirst"],
                     help="axis processing order: the paper's rule (periodic axes first) or x, y, z")
+    ap.add_argument("--n", default="",
+                    help="grid of --workload bc128 as NX,NY,NZ (default 128,128,128)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="hartree192: padded lengths 2n instead of the autotuner's choice")
