@@ -24,6 +24,10 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+int blue_regs_length(int M, int N) {
+  return (M >= 32 && M <= 256 && (M & (M - 1)) == 0 && M >= 2 * N) ? M : 0;
+}
+
 }  // namespace ps
 
 using namespace ps;
@@ -257,7 +261,17 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
       // 200 KiB shared-memory budget of the generic kernels
       const size_t csz = 2 * (p->dtype == PS_F32 ? 4 : 8);
       const int max_M = (int)std::min<size_t>(kMaxLen, 200 * 1024 / (2 * 2 * csz));
-      const int M = bluestein_length(N, max_M);
+      int M = bluestein_length(N, max_M);
+      // FP32: the power of two >= 2N - 1 where the register four-step form
+      // exists (about twice the points of the smooth length, at a fraction of
+      // the cost per point of the Stockham stages); PS_BLUE_REGS=0 (or
+      // PS_BLUE_M=min) keeps the smooth length
+      const char* rv = getenv("PS_BLUE_REGS");
+      const char* mv = getenv("PS_BLUE_M");
+      const bool regs = !(rv && atoi(rv) == 0) && !(mv && strcmp(mv, "min") == 0);
+      int m2 = 1;
+      while (m2 < 2 * N - 1) m2 *= 2;
+      if (p->dtype == PS_F32 && regs && blue_regs_length(m2, N)) M = m2;
       if (M <= max_M) {
         p->blue[j].M = M;
         p->blue[j].st = factorize(M);

@@ -98,6 +98,8 @@ struct PassCfg {
   size_t gsmem; // dynamic shared memory bytes of the generic kernel of the pass (the x passes
                 // fall back to it when rho or V is not 8-byte aligned)
   int twn;      // generic passes: twiddle entries kept in shared memory (0: read from global memory)
+  int bm;       // generic FP32 passes in Bluestein form: the power-of-two M of the register
+                // four-step convolution (0: Stockham stages)
   int fast;     // 1 if a compile-time specialised kernel runs this pass
   const void* fn;  // the specialised kernel
   dim3 grid, block;
@@ -205,6 +207,9 @@ void set_error(const char* fmt, ...);
 
 // Radix factorisation used by the generic kernels (pref 1: no radix-8 stages).
 Stages factorize(int N, int pref = 0);
+// M if a Bluestein convolution of length M for a transform of length N runs
+// in the register four-step form (M a power of two, 32 <= M <= 1024, M >= 2N), else 0
+int blue_regs_length(int M, int N);
 
 // Launchers (defined in passes.cu / kernel_build.cu). They only enqueue.
 template <typename T>

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "fft_regs.cuh"
 
 namespace ps {
 
@@ -291,6 +292,95 @@ __device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, 
     r[k * ldt + t] = DIR < 0 ? cmul(r[k * ldt + t], ch[k]) : cmulc(r[k * ldt + t], ch[k]);
   __syncthreads();
   return r;
+}
+
+// The Bluestein form of line_transform for FP32 lines whose convolution length
+// M = P * Q is a power of two with M >= 2N: the length-M transforms as
+// four-step transforms on compile-time register DFTs instead of Stockham
+// stages. With m = b + Q a and k = k1 + P k2 (a, k1 < P; b, k2 < Q):
+//   step 1, column b of a line: y[k1] = sum_a u[b + Q a] W_P^{a k1}, with
+//     u[m] = x[m] c[m] for m < N (zero above; a >= P/2 is past M/2 >= N),
+//     times W_M^{b k1}, to row k1 Q + b of `b`;
+//   steps 2-3, row k1: the Q-point DFT over b gives U[k1 + P k2]; times Bf
+//     (the transform of the conjugate chirp over M); the inverse Q-point DFT
+//     over k2 and conj W_M^{b k1} give column b of the inverse's second
+//     step, to row b P + k1 of `a`;
+//   step 4, column b: the inverse P-point DFT over k1 gives v[b + Q a], kept
+//     for m < N, times c[m], to row m of `b`.
+// Three barriers instead of two per Stockham stage and one per multiply.
+// DIR = +1 conjugates the chirp and Bf as line_transform does. Returns b.
+template <int P, int Q, int DIR>
+__device__ float2* blue_regs(float2* a, float2* b, int N, int tk, int ldt, const float2* ttab, int tstr,
+                             const BlueArgs& bl) {
+  const float2* __restrict__ ch = static_cast<const float2*>(bl.chirp);
+  const float2* __restrict__ Bf = static_cast<const float2*>(bl.Bf);
+  const int ltk = __ffs(tk) - 1;
+  for (int i = threadIdx.x; i < (Q << ltk); i += blockDim.x) {
+    const int t = i & (tk - 1), col = i >> ltk;
+    float2 y[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+      const int m = col + Q * r;
+      y[r] = make_float2(0.f, 0.f);
+      if (r < P / 2 && m < N) {
+        const float2 x = a[m * ldt + t], c = __ldg(&ch[m]);
+        y[r] = DIR < 0 ? cmul(x, c) : cmulc(x, c);
+      }
+    }
+    regs::rdft<P, -1, true>(y);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) b[(k1 * Q + col) * ldt + t] = k1 ? cmul(y[k1], ttab[col * k1 * tstr]) : y[k1];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < (P << ltk); i += blockDim.x) {
+    const int t = i & (tk - 1), k1 = i >> ltk;
+    float2 z[Q];
+#pragma unroll
+    for (int c2 = 0; c2 < Q; ++c2) z[c2] = b[(k1 * Q + c2) * ldt + t];
+    regs::rdft<Q, -1, false>(z);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const float2 f = __ldg(&Bf[k1 + P * k2]);
+      z[k2] = DIR < 0 ? cmul(z[k2], f) : cmulc(z[k2], f);
+    }
+    regs::rdft<Q, 1, false>(z);
+#pragma unroll
+    for (int c2 = 0; c2 < Q; ++c2) a[(c2 * P + k1) * ldt + t] = c2 ? cmulc(z[c2], ttab[c2 * k1 * tstr]) : z[c2];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < (Q << ltk); i += blockDim.x) {
+    const int t = i & (tk - 1), col = i >> ltk;
+    float2 y[P];
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) y[k1] = a[(col * P + k1) * ldt + t];
+    regs::rdft<P, 1, false>(y);
+#pragma unroll
+    for (int r = 0; r < P / 2; ++r) {
+      const int m = col + Q * r;
+      if (m < N) {
+        const float2 c = __ldg(&ch[m]);
+        b[m * ldt + t] = DIR < 0 ? cmul(y[r], c) : cmulc(y[r], c);
+      }
+    }
+  }
+  __syncthreads();
+  return b;
+}
+
+// P of the four-step split M = P * Q of blue_regs (Q = M / P)
+constexpr int blue_p(int M) { return M <= 32 ? 4 : M <= 128 ? 8 : M <= 512 ? 16 : 32; }
+
+// The line transform of a generic pass: blue_regs when BM (a power-of-two
+// Bluestein length, FP32) is set, else line_transform.
+template <int DIR, typename T, int BM>
+__device__ __forceinline__ cpx<T>* gen_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, const Stages& st,
+                                                 const cpx<T>* ttab, int tstr, const BlueArgs& bl) {
+  if constexpr (BM > 0) {
+    static_assert(sizeof(T) == 4, "register Bluestein form is FP32");
+    return blue_regs<blue_p(BM), BM / blue_p(BM), DIR>(a, b, N, tk, ldt, ttab, tstr, bl);
+  } else {
+    return line_transform<DIR, T>(a, b, N, tk, ldt, st, ttab, tstr, bl);
+  }
 }
 
 }  // namespace ps

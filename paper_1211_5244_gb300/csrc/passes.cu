@@ -53,7 +53,7 @@ struct GenArgs {
 
 // ---------------------------------------------------------------- P1
 
-template <typename T>
+template <typename T, int BM = 0>
 __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx<T>* __restrict__ A,
                                                   const cpx<T>* __restrict__ tw, GenArgs a) {
   using C = cpx<T>;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
     }
   }
   __syncthreads();
-  C* out = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* out = gen_transform<-1, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   if (even) {
     // X[k] = E[k] + W_L^k O[k],  E = (Z[k] + conj Z[N-k]) / 2,  O = -i (Z[k] - conj Z[N-k]) / 2
     const int N = a.N;
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
 // Transform along y of the tile kx0 .. kx0 + tk - 1 at one z:
 //   DIR = -1: n2 inputs from A (rest zero), L2 outputs to B
 //   DIR = +1: L2 inputs from B, n2 outputs to A
-template <int DIR, typename T>
+template <int DIR, typename T, int BM = 0>
 __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
                                                   const cpx<T>* __restrict__ tw, GenArgs a) {
   using C = cpx<T>;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
     }
   }
   __syncthreads();
-  C* out = line_transform<DIR, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* out = gen_transform<DIR, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   for (int w = threadIdx.x; w < a.tk * nout; w += blockDim.x) {
     const int t = w & (a.tk - 1), y = w >> a.ltk;
     if (kx0 + t < a.c) d[(size_t)y * a.ldc + t] = out[y * a.ldt + t];
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
 
 // ---------------------------------------------------------------- P3
 
-template <typename T>
+template <typename T, int BM = 0>
 __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const T* __restrict__ K,
                                                   const cpx<T>* __restrict__ tw, GenArgs a,
                                                   double* partials, unsigned* counter,
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     }
   }
   __syncthreads();
-  C* spec = line_transform<-1, T>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* spec = gen_transform<-1, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   C* other = (spec == buf0) ? buf1 : buf0;
   // multiply by the octant of K^F; accumulate w(kx) K |rho^F|^2 for the energy
   const int kyo = min(ky, a.L2 - ky);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     }
   }
   __syncthreads();
-  C* res = line_transform<1, T>(spec, other, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* res = gen_transform<1, T, BM>(spec, other, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   for (int w = threadIdx.x; w < a.tk * a.n3; w += blockDim.x) {
     const int t = w & (a.tk - 1), z = w >> a.ltk;
     if (kx0 + t < a.c) line[z * zstride + t] = res[z * a.ldt + t];
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
 
 // ---------------------------------------------------------------- P5
 
-template <typename T>
+template <typename T, int BM = 0>
 __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, T* __restrict__ V,
                                                   const cpx<T>* __restrict__ tw, GenArgs a) {
   using C = cpx<T>;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
     }
   }
   __syncthreads();
-  C* out = line_transform<1, T>(buf1, buf0, N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* out = gen_transform<1, T, BM>(buf1, buf0, N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
   for (int w = threadIdx.x; w < rpc * a.n1; w += blockDim.x) {
     const int t = div_by(w, a.mn1), i = w - t * a.n1;
     const int row = row0 + t;
@@ -327,6 +327,39 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
     }
     V[(size_t)row * a.n1 + i] = v;
   }
+}
+
+// ---------------------------------------------------------------- kernel table
+
+// The five generic kernels of one Bluestein form: BM = 0 runs the Stockham
+// stages (any length), BM > 0 the register four-step convolution of length
+// BM (FP32, a power of two from 32 to 1024).
+template <typename T>
+struct GenKernels {
+  void (*p1)(const T*, cpx<T>*, const cpx<T>*, GenArgs);
+  void (*pyf)(const cpx<T>*, cpx<T>*, const cpx<T>*, GenArgs);
+  void (*pyi)(const cpx<T>*, cpx<T>*, const cpx<T>*, GenArgs);
+  void (*pz)(cpx<T>*, const T*, const cpx<T>*, GenArgs, double*, unsigned*, double, double*);
+  void (*p5)(const cpx<T>*, T*, const cpx<T>*, GenArgs);
+};
+
+template <typename T, int BM>
+static GenKernels<T> gen_kernels_of() {
+  return {p1_generic<T, BM>, py_generic<-1, T, BM>, py_generic<1, T, BM>, pz_generic<T, BM>, p5_generic<T, BM>};
+}
+
+template <typename T>
+static GenKernels<T> gen_kernels(int bm) {
+  if constexpr (sizeof(T) == 4) {
+    switch (bm) {
+      case 32: return gen_kernels_of<T, 32>();
+      case 64: return gen_kernels_of<T, 64>();
+      case 128: return gen_kernels_of<T, 128>();
+      case 256: return gen_kernels_of<T, 256>();
+      default: break;
+    }
+  }
+  return gen_kernels_of<T, 0>();
 }
 
 // ---------------------------------------------------------------- VJP term
@@ -471,17 +504,20 @@ cudaError_t configure_passes(ps_plan_s* p) {
     // for passes along y and z, whose tile rows are contiguous runs
     cf.tk = pick_tk(rows[k], twn, sizeof(C), tk0, axis == 0 ? 1 : 0, &cf.ldt, &cf.gsmem, &cf.twn);
     cf.smem = cf.gsmem;
+    cf.bm = sizeof(T) == 4 ? blue_regs_length(p->blue[axis].M, Nk) : 0;
     if (cf.tk == 0) {
       set_error("transform length %d needs more shared memory than a CTA has", rows[k]);
       return cudaErrorInvalidConfiguration;
     }
   }
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(p1_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(py_generic<-1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(py_generic<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(pz_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(p5_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess) return e;
+  for (int k = -1; k < 5; ++k) {  // the Stockham kernels and those of each pass's Bluestein form
+    const GenKernels<T> g = gen_kernels<T>(k < 0 ? 0 : p->cfg[k].bm);
+    for (const void* f : {(const void*)g.p1, (const void*)g.pyf, (const void*)g.pyi, (const void*)g.pz,
+                          (const void*)g.p5})
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget)) != cudaSuccess)
+        return e;
+  }
   p->fastord = 0;
   if (!canonical_order(p)) {
     // the generic kernels along strided axes (passes_ord.cu); energy
@@ -535,8 +571,8 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
     if (p->cfg[P3].fast) return launch_fast(p, P3, B, B, E, escale, s);
     GenArgs a = gen_args<T>(p, P3);
     dim3 g((p->c + a.tk - 1) / a.tk, p->L[1]);
-    pz_generic<T><<<g, p->cfg[P3].threads, p->cfg[P3].gsmem, s>>>(B, static_cast<const T*>(p->K), tw2, a,
-                                                                 p->partials, p->counter, escale, E);
+    gen_kernels<T>(p->cfg[P3].bm).pz<<<g, p->cfg[P3].threads, p->cfg[P3].gsmem, s>>>(
+        B, static_cast<const T*>(p->K), tw2, a, p->partials, p->counter, escale, E);
     return cudaGetLastError();
   };
   if (!xyf && a8 && p->chunks > 1) {
@@ -571,7 +607,8 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   } else {
     GenArgs a = gen_args<T>(p, P1);
     const int rpc = (p->L[0] % 2 == 0) ? a.tk : 2 * a.tk;  // odd L1: two real rows per line
-    p1_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(rho, A, tw0, a);
+    gen_kernels<T>(p->cfg[P1].bm).p1<<<(nrows + rpc - 1) / rpc, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(
+        rho, A, tw0, a);
   }
   if (ev) cudaEventRecord(ev[1], s);
   // P2
@@ -582,7 +619,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   } else {
     GenArgs a = gen_args<T>(p, P2);
     dim3 g((p->c + a.tk - 1) / a.tk, p->n[2]);
-    py_generic<-1, T><<<g, p->cfg[P2].threads, p->cfg[P2].gsmem, s>>>(A, B, tw1, a);
+    gen_kernels<T>(p->cfg[P2].bm).pyf<<<g, p->cfg[P2].threads, p->cfg[P2].gsmem, s>>>(A, B, tw1, a);
   }
   if (ev) cudaEventRecord(ev[2], s);
   // P3
@@ -596,7 +633,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   } else {
     GenArgs a = gen_args<T>(p, P4);
     dim3 g((p->c + a.tk - 1) / a.tk, p->n[2]);
-    py_generic<1, T><<<g, p->cfg[P4].threads, p->cfg[P4].gsmem, s>>>(B, A, tw1, a);
+    gen_kernels<T>(p->cfg[P4].bm).pyi<<<g, p->cfg[P4].threads, p->cfg[P4].gsmem, s>>>(B, A, tw1, a);
   }
   if (ev) cudaEventRecord(ev[4], s);
   // P5
@@ -607,7 +644,8 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   } else {
     GenArgs a = gen_args<T>(p, P5);
     const int rpc = (p->L[0] % 2 == 0) ? a.tk : 2 * a.tk;  // odd L1: two real rows per line
-    p5_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(A, V, tw0, a);
+    gen_kernels<T>(p->cfg[P5].bm).p5<<<(nrows + rpc - 1) / rpc, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(
+        A, V, tw0, a);
   }
   if (ev) cudaEventRecord(ev[5], s);
   return cudaGetLastError();
@@ -621,10 +659,10 @@ cudaError_t launch_x_pass(ps_plan_s* p, int pass, const void* src, void* dst, cu
   const int rpc = (p->L[0] % 2 == 0) ? a.tk : 2 * a.tk;  // odd L1: two real rows per line
   const C* tw0 = static_cast<const C*>(p->tw[0]);
   if (pass == P1)
-    p1_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(
+    gen_kernels<T>(p->cfg[P1].bm).p1<<<(nrows + rpc - 1) / rpc, p->cfg[P1].threads, p->cfg[P1].gsmem, s>>>(
         static_cast<const T*>(src), static_cast<C*>(dst), tw0, a);
   else
-    p5_generic<T><<<(nrows + rpc - 1) / rpc, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(
+    gen_kernels<T>(p->cfg[P5].bm).p5<<<(nrows + rpc - 1) / rpc, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(
         static_cast<const C*>(src), static_cast<T*>(dst), tw0, a);
   return cudaGetLastError();
 }

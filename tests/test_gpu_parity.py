@@ -739,6 +739,7 @@ SCHEDULES = [
     ({"xy": 1}, {}),                     # fused x/y kernels where they apply (256 x 256 planes)
     ({}, {"PS_L2ORDER": "0"}),           # every pass in forward plane order
     ({}, {"PS_BLUE_M": "min"}),          # smallest 5-smooth Bluestein length (137: 288, not 280)
+    ({}, {"PS_BLUE_REGS": "0"}),         # Bluestein on Stockham stages at the cheapest smooth length
 ]
 
 
