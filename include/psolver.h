@@ -129,6 +129,10 @@ typedef struct {
                                x), through one chunk of the x-transformed array
                                that stays in L2 (1: whole passes; 0 before the
                                build; used when rho and V are 8-byte aligned)  */
+  int axis_schedule[3][2];  /* per physical axis (x, y, z): generic lines per
+                               tile and radix split of the passes along it, as
+                               set by ps_plan_set_axis_schedule (0 and -1: the
+                               plan-wide schedule[0] and schedule[1])          */
 } ps_plan_info;
 
 /*
@@ -211,6 +215,19 @@ int ps_plan_set_math(ps_plan plan, int math_mode);
  * Errors: PS_ERR_ARG (plan NULL or built, a value out of range).
  */
 int ps_plan_set_schedule(ps_plan plan, int tile, int radix, int ztk, int ykind, int xy, int chunks);
+
+/*
+ * ps_plan_set_axis_schedule -- the generic-kernel choices of ps_plan_set_schedule
+ * for the passes along one physical axis (0 x, 1 y, 2 z) only, before the
+ * build; they take precedence over the plan-wide ones (ps_plan_autotune tunes
+ * them axis by axis). Same results up to rounding.
+ *   tile    most lines per tile of the generic passes along the axis: 0 (the
+ *           plan-wide tile), 1, 2, 4, 8 or 16
+ *   radix   their Stockham stages: -1 (the plan-wide radix), 0 radix 8 first,
+ *           1 radix 4 and 2 only
+ * Errors: PS_ERR_ARG (plan NULL or built, axis or a value out of range).
+ */
+int ps_plan_set_axis_schedule(ps_plan plan, int axis, int tile, int radix);
 
 /* ps_plan_query -- fill *info (host only; valid before and after the build). */
 int ps_plan_query(ps_plan plan, ps_plan_info* info);

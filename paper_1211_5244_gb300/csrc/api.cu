@@ -220,6 +220,7 @@ int ps_plan_create(int n1, int n2, int n3, double h, int bc_x, int bc_y, int bc_
   p->math = PS_MATH_CUDACORE;
   p->esz = dtype == PS_F32 ? 4 : 8;
   p->device = -1;
+  for (int j = 0; j < 3; ++j) p->radix_ax[j] = -1;
   const int rc = ps_plan_set_lengths(p, 0, 0, 0);  // validates lengths, derives c, H, stages
   if (rc != PS_OK) {
     delete p;
@@ -347,6 +348,18 @@ int ps_plan_set_schedule(ps_plan p, int tile, int radix, int ztk, int ykind, int
   return PS_OK;
 }
 
+int ps_plan_set_axis_schedule(ps_plan p, int axis, int tile, int radix) {
+  if (!p) return fail(PS_ERR_ARG, "plan is NULL");
+  if (p->built) return fail(PS_ERR_ARG, "the schedule must be set before ps_kernel_build");
+  if (axis < 0 || axis > 2) return fail(PS_ERR_ARG, "axis = %d: 0, 1 or 2", axis);
+  if (tile < 0 || tile > 16 || (tile & (tile - 1)) != 0)
+    return fail(PS_ERR_ARG, "tile = %d: 0 or a power of two up to 16", tile);
+  if (radix < -1 || radix > 1) return fail(PS_ERR_ARG, "radix = %d: -1, 0 or 1", radix);
+  p->tile_ax[axis] = tile;
+  p->radix_ax[axis] = radix;
+  return PS_OK;
+}
+
 int ps_plan_query(ps_plan p, ps_plan_info* info) {
   if (!p || !info) return fail(PS_ERR_ARG, "plan or info is NULL");
   memset(info, 0, sizeof *info);
@@ -393,6 +406,10 @@ int ps_plan_query(ps_plan p, ps_plan_info* info) {
   info->schedule[4] = p->xy_sched;
   info->schedule[5] = p->chunk_req;
   info->chunks = p->built ? p->chunks : 0;
+  for (int j = 0; j < 3; ++j) {
+    info->axis_schedule[j][0] = p->tile_ax[j];
+    info->axis_schedule[j][1] = p->radix_ax[j];
+  }
   for (int k = 0; k < 5; ++k)
     info->blocks[k] = (p->built && p->cfg[k].fast) ? (int)(p->cfg[k].grid.x * p->cfg[k].grid.y) : 0;
   if (xyf) {
@@ -410,10 +427,11 @@ int ps_kernel_build(ps_plan p, void* stream) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   p->device = dev;
-  if (p->radix_pref) {  // the schedule's radix split of the generic stages
-    for (int j = 0; j < 3; ++j) p->st[j] = factorize(xform_len(p, j), p->radix_pref);
-    for (int j = 0; j < 3; ++j)
-      if (p->blue[j].M) p->blue[j].st = factorize(p->blue[j].M, p->radix_pref);
+  for (int j = 0; j < 3; ++j) {  // the schedule's radix split of the generic stages, per axis
+    const int r = axis_radix(p, j);
+    if (!r) continue;
+    p->st[j] = factorize(xform_len(p, j), r);
+    if (p->blue[j].M) p->blue[j].st = factorize(p->blue[j].M, r);
   }
   e = p->dtype == PS_F32 ? configure_passes<float>(p) : configure_passes<double>(p);
   if (e != cudaSuccess) return cuda_fail(e, "configure passes");

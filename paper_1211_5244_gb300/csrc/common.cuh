@@ -172,6 +172,8 @@ struct ps_plan_s {
   int z_tk;        // lines per tile of the persistent packed z kernel (8 or 16)
   int y_kind;      // y passes: 1 unpacked persistent kernels, 2 non-persistent ones
   int radix_pref;  // generic Stockham stages: 0 radix 8 first, 1 radix 4 and 2 only
+  int tile_ax[3];  // per physical axis: most lines per generic tile of its passes (0: gen_tk_max)
+  int radix_ax[3]; // per physical axis: radix split of its Stockham stages (-1: radix_pref)
   int chunk_req;   // chunks of z planes for the x and y passes (0: chosen by size, 1: none)
   // the x and y passes run chunk by chunk of z planes (x then y for each
   // chunk forward, y then x inverse) through the first chunk's rows of A, which
@@ -182,6 +184,12 @@ struct ps_plan_s {
   std::vector<cudaEvent_t> events;
   size_t events_used;
 };
+
+namespace ps {
+// the generic tile width limit and radix split of the passes along physical axis j
+inline int axis_tile(const ps_plan_s* p, int j) { return p->tile_ax[j] ? p->tile_ax[j] : p->gen_tk_max; }
+inline int axis_radix(const ps_plan_s* p, int j) { return p->radix_ax[j] >= 0 ? p->radix_ax[j] : p->radix_pref; }
+}  // namespace ps
 
 namespace ps {
 

@@ -487,10 +487,10 @@ template <typename T>
 cudaError_t configure_passes(ps_plan_s* p) {
   using C = cpx<T>;
   const size_t budget = 200 * 1024;
-  // most lines per generic tile: the plan's schedule (ps_plan_set_schedule or
-  // the autotuner), else 16 (FP32) / 8 (FP64)
-  int tk0 = sizeof(T) == 4 ? 16 : 8;
-  if (p->gen_tk_max > 0) tk0 = p->gen_tk_max;
+  // most lines per generic tile: the plan's schedule for the pass's axis
+  // (ps_plan_set_axis_schedule, else ps_plan_set_schedule, or the autotuner),
+  // else 16 (FP32) / 8 (FP64)
+  const int tk_def = sizeof(T) == 4 ? 16 : 8;
   const int rows[5] = {gen_rows(p, P1), gen_rows(p, P2), gen_rows(p, P3), gen_rows(p, P4), gen_rows(p, P5)};
   for (int k = 0; k < 5; ++k) {
     PassCfg& cf = p->cfg[k];
@@ -498,6 +498,7 @@ cudaError_t configure_passes(ps_plan_s* p) {
     cf.fast = 0;
     const int axis = pass_axis(p, k);
     const int Nk = xform_len(p, axis);
+    const int tk0 = axis_tile(p, axis) > 0 ? axis_tile(p, axis) : tk_def;
     const int twn = p->blue[axis].M ? p->blue[axis].M : Nk;
     // row pitch: tk + 1 for passes along x, whose tile loops transpose rows (a
     // pitch of tk would put a row's consecutive elements on one bank); tk

@@ -12,6 +12,8 @@
 //           8 / 4 / 2 in FP64: more CTAs per line set, shorter chains)
 //   radix   radix split of the generic Stockham stages (radix 8 first, or
 //           radix 4 and 2 only)
+//   tile and radix again per axis: for the generic passes along each
+//           physical axis on its own (ps_plan_set_axis_schedule)
 //   ztk     lines per tile of the persistent packed z kernel (8 or 16)
 //   ykind   y kernels: packed persistent, unpacked persistent, non-persistent
 //   xy      the fused x/y passes (thread-block clusters) or the separate ones
@@ -21,8 +23,9 @@
 //           lengths have them (more 1D transforms, faster kernels)
 // Results are kept in memory, and in a text file when PS_TUNE_CACHE names one
 // (one line per geometry: "n1 n2 n3 bc1 bc2 bc3 mode sms L1 L2 L3 tile radix
-// ztk ykind xy xfirst chunks", mode = dtype + 2 math + 4 (the plan's order as
-// 9 a0 + 3 a1 + a2), 0 for a default choice).
+// ztk ykind xy xfirst chunks tile_x tile_y tile_z radix_x+1 radix_y+1
+// radix_z+1", mode = dtype + 2 math + 4 (the plan's order as 9 a0 + 3 a1 +
+// a2), 0 for a default choice).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -38,7 +41,8 @@ namespace ps {
 namespace {
 
 // a tuned choice: padded lengths and the schedule fields of the plan
-enum { kL1, kL2, kL3, kTile, kRadix, kZtk, kYkind, kXy, kXfirst, kChunks, kFields };
+enum { kL1, kL2, kL3, kTile, kRadix, kZtk, kYkind, kXy, kXfirst, kChunks, kTileAx, kRadixAx = kTileAx + 3,
+       kFields = kRadixAx + 3 };
 
 std::mutex g_tune_mu;
 std::map<std::string, std::vector<int>> g_tuned;
@@ -63,16 +67,22 @@ void load_file() {
   if (!path || !*path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  char line[256];
+  char line[512];
   while (fgets(line, sizeof line, f)) {
-    int n[3], bc[3], dt, sms, v[kFields] = {};
-    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &n[0], &n[1], &n[2],
-                           &bc[0], &bc[1], &bc[2], &dt, &sms, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
-                           &v[8], &v[9]);
-    if (got != 8 + kFields) continue;
+    // 8 key fields, then the choice; lines of another field count are skipped
+    std::vector<long> w;
+    char* q = line;
+    while (true) {
+      char* end = nullptr;
+      const long x = strtol(q, &end, 10);
+      if (end == q) break;
+      w.push_back(x);
+      q = end;
+    }
+    if (w.size() != (size_t)(8 + kFields)) continue;
     char key[128];
-    snprintf(key, sizeof key, "%d %d %d %d %d %d %d %d", n[0], n[1], n[2], bc[0], bc[1], bc[2], dt, sms);
-    g_tuned[key] = std::vector<int>(v, v + kFields);
+    snprintf(key, sizeof key, "%ld %ld %ld %ld %ld %ld %ld %ld", w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]);
+    g_tuned[key] = std::vector<int>(w.begin() + 8, w.end());
   }
   fclose(f);
 }
@@ -98,6 +108,10 @@ int apply_choice(ps_plan p, const std::vector<int>& v) {
   p->y_kind = v[kYkind];
   p->xy_sched = v[kXy];
   p->chunk_req = v[kChunks];
+  for (int j = 0; j < 3; ++j) {
+    p->tile_ax[j] = v[kTileAx + j];
+    p->radix_ax[j] = v[kRadixAx + j] - 1;
+  }
   if (v[kXfirst]) return ps_plan_set_order(p, 0, 1, 2);
   return PS_OK;
 }
@@ -105,6 +119,7 @@ int apply_choice(ps_plan p, const std::vector<int>& v) {
 // What a built trial plan says about the choices that apply to it.
 struct Applies {
   bool generic = false;  // some pass runs the generic kernels
+  bool generic_ax[3] = {false, false, false};  // ... along physical axis j
   bool zpipe = false;    // the z pass runs the persistent packed kernel
   bool ypacked = false;  // the y passes run the packed persistent kernels
   bool xy = false;       // the fused x/y kernels run
@@ -184,7 +199,10 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
       if (e == cudaSuccess && r == PS_OK) timed(count, &b);
       *ms = std::min(a, b);
       if (ap) {
-        for (int k = 0; k < 5; ++k) ap->generic |= !tp->cfg[k].fast;
+        for (int k = 0; k < 5; ++k) {
+          ap->generic |= !tp->cfg[k].fast;
+          ap->generic_ax[pass_axis(tp, k)] |= !tp->cfg[k].fast;
+        }
         ap->zpipe = tp->zsoa_T == 16 && tp->cfg[P3].fast && !tp->tctab;
         ap->ypacked = tp->ysoa == 3;
         ap->xy = tp->xyfuse != 0;
@@ -220,7 +238,8 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
     if (ok && std::find(cands.begin(), cands.end(), v) == cands.end()) cands.push_back(v);
   }
   float best_ms = -1.f;
-  std::vector<int> best = {p->L[0], p->L[1], p->L[2], 0, 0, 0, 0, 0, 0, 0};
+  std::vector<int> best(kFields, 0);
+  for (int j = 0; j < 3; ++j) best[kL1 + j] = p->L[j];
   Applies best_ap;
   for (size_t c = 0; e == cudaSuccess && rc == PS_OK && c < cands.size(); ++c) {
     float ms;
@@ -235,7 +254,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
   // 2. the schedule, one choice at a time at the best lengths; a choice other
   // than the default is kept only when it is at least 3% faster
   constexpr float kKeep = 0.97f;
-  auto try_field = [&](int field, std::initializer_list<int> values) {
+  auto try_field = [&](int field, const std::vector<int>& values) {
     for (int val : values) {
       if (e != cudaSuccess || rc != PS_OK || best_ms < 0.f) return;
       std::vector<int> v = best;
@@ -270,6 +289,16 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
   if (best_ap.generic) {
     try_field(kTile, {t0w / 2, t0w / 4});
     try_field(kRadix, {1});
+    // then axis by axis: the other tile widths and the other radix split
+    for (int j = 0; j < 3; ++j) {
+      if (!best_ap.generic_ax[j]) continue;
+      const int cur = best[kTile] ? best[kTile] : t0w;
+      std::vector<int> tiles;
+      for (int t : {t0w, t0w / 2, t0w / 4})
+        if (t != cur) tiles.push_back(t);
+      try_field(kTileAx + j, tiles);
+      try_field(kRadixAx + j, {best[kRadix] ? 1 : 2});
+    }
   }
   if (best_ap.zpipe) try_field(kZtk, {16});
   if (best_ap.chunkable) try_field(kChunks, {2, 4});

@@ -41,6 +41,7 @@ class PlanInfo(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_int),
         ("tensor_passes", ctypes.c_int), ("blocks", ctypes.c_int * 5), ("fused", ctypes.c_int),
         ("order", ctypes.c_int * 3), ("schedule", ctypes.c_int * 6), ("chunks", ctypes.c_int),
+        ("axis_schedule", (ctypes.c_int * 2) * 3),
     ]
 
 
@@ -63,6 +64,7 @@ def load_library():
         "ps_plan_set_lengths": [vp, i, i, i],
         "ps_plan_set_math": [vp, i],
         "ps_plan_set_schedule": [vp, i, i, i, i, i, i],
+        "ps_plan_set_axis_schedule": [vp, i, i, i],
         "ps_plan_set_order": [vp, i, i, i],
         "ps_plan_autotune": [vp, i, vp],
         "ps_plan_query": [vp, ctypes.POINTER(PlanInfo)],
@@ -118,7 +120,7 @@ class Plan:
     """One solve geometry: ps_plan_create (+ optional lengths) and ps_kernel_build."""
 
     def __init__(self, n, bc, h, dtype="f32", L=None, build=True, stream=None, autotune=False,
-                 math="cudacore", schedule=None, order=None):
+                 math="cudacore", schedule=None, order=None, axis_schedule=None):
         lib = load_library()
         self.n = tuple(int(v) for v in n)
         self.bc = str(bc).lower()
@@ -138,6 +140,8 @@ class Plan:
             _check(lib.ps_plan_set_order(self._h, int(order[0]), int(order[1]), int(order[2])))
         if schedule is not None:
             self.set_schedule(**schedule)
+        for axis, sched in (axis_schedule or {}).items():
+            self.set_axis_schedule(axis, **sched)
         if autotune:
             _check(lib.ps_plan_autotune(self._h, 5, _stream_handle(stream)))
         if build:
@@ -147,6 +151,11 @@ class Plan:
         """ps_plan_set_schedule: the kernel schedule by hand (before the build)."""
         _check(_lib.ps_plan_set_schedule(self._h, int(tile), int(radix), int(ztk), int(ykind), int(xy),
                                          int(chunks)))
+        return self
+
+    def set_axis_schedule(self, axis, tile=0, radix=-1):
+        """ps_plan_set_axis_schedule: generic tile and radix split along one axis."""
+        _check(_lib.ps_plan_set_axis_schedule(self._h, int(axis), int(tile), int(radix)))
         return self
 
     # ------------------------------------------------------------ lifecycle

@@ -99,6 +99,22 @@ def test_set_schedule_rules(lib):
     lib.ps_plan_destroy(p)
 
 
+def test_set_axis_schedule_rules(lib):
+    rc, p = _create(lib, n=(10, 12, 7), bc=(0, 1, 1))
+    assert rc == 0
+    info = ps.PlanInfo()
+    assert lib.ps_plan_query(p, ctypes.byref(info)) == 0
+    assert [list(a) for a in info.axis_schedule] == [[0, -1]] * 3  # plan-wide choices by default
+    for bad in ((3, 0, 0), (-1, 0, 0), (0, 3, 0), (0, 32, 0), (0, -2, 0), (0, 0, 2), (0, 0, -2)):
+        assert lib.ps_plan_set_axis_schedule(p, *bad) == 1, bad
+    assert lib.ps_plan_set_axis_schedule(p, 1, 4, 1) == 0
+    assert lib.ps_plan_set_axis_schedule(p, 2, 0, 0) == 0
+    assert lib.ps_plan_query(p, ctypes.byref(info)) == 0
+    assert [list(a) for a in info.axis_schedule] == [[0, -1], [4, 1], [0, 0]]
+    assert lib.ps_plan_set_axis_schedule(None, 0, 0, 0) == 1
+    lib.ps_plan_destroy(p)
+
+
 def test_solve_on_unbuilt_plan_is_rejected_before_any_launch(lib):
     rc, p = _create(lib)
     fake_in, fake_out = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000)

@@ -756,3 +756,25 @@ def test_parity_schedules(torch_cuda, monkeypatch, sched, env, n, bc):
     plan = psolver.Plan(n, bc, 0.25, "f32", schedule=sched, order=XFIRST)
     V, E = plan.solve(torch.from_numpy(rho.astype(np.float32)).cuda())
     _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.25, "f32")
+
+
+# Per-axis generic tiles and radix splits (ps_plan_set_axis_schedule) on
+# shapes whose passes run the generic kernels along all three axes (smooth,
+# Bluestein in register form and on Stockham stages), FP32 and FP64.
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n,bc,axis_sched", [
+    ((45, 27, 35), "ppp", {0: dict(tile=4, radix=1), 1: dict(tile=1), 2: dict(radix=1)}),
+    ((37, 61, 139), "ppp", {0: dict(tile=2), 1: dict(radix=1), 2: dict(tile=8, radix=0)}),
+    ((29, 23, 11), "pff", {0: dict(tile=1, radix=1), 2: dict(tile=2)}),
+])
+def test_parity_axis_schedules(torch_cuda, n, bc, axis_sched, dtype):
+    from paper_1211_5244_gb300 import psolver
+    torch = torch_cuda
+    rho = synth.gaussian_mixture(n, 0.3, 4, seed=23 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    plan = psolver.Plan(n, bc, 0.3, dtype, axis_schedule=axis_sched, order=XFIRST)
+    info = plan.info()
+    for axis, sched in axis_sched.items():
+        assert list(info.axis_schedule[axis]) == [sched.get("tile", 0), sched.get("radix", -1)]
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    V, E = plan.solve(torch.from_numpy(rho).to(tdt).cuda())
+    _check(V.double().cpu().numpy(), float(E.item()), rho, bc, 0.3, dtype)
