@@ -205,7 +205,7 @@ int ps_plan_set_math(ps_plan plan, int math_mode);
  * (ps_plan_autotune chooses it by timing). Every choice gives the same result
  * up to rounding; a choice that does not apply to the plan's shapes is
  * ignored. 0 keeps a field's default.
- *   tile    most lines per tile of the generic passes: 0, 1, 2, 4, 8 or 16
+ *   tile    most lines per tile of the generic passes: 0, 1, 2, 4, 8, 16 or 32
  *   radix   generic Stockham stages: 0 radix 8 first, 1 radix 4 and 2 only
  *   ztk     lines per tile of the persistent packed z kernel: 0, 8 or 16
  *   ykind   y kernels: 0 default, 1 unpacked persistent, 2 non-persistent
@@ -222,7 +222,7 @@ int ps_plan_set_schedule(ps_plan plan, int tile, int radix, int ztk, int ykind, 
  * build; they take precedence over the plan-wide ones (ps_plan_autotune tunes
  * them axis by axis). Same results up to rounding.
  *   tile    most lines per tile of the generic passes along the axis: 0 (the
- *           plan-wide tile), 1, 2, 4, 8 or 16
+ *           plan-wide tile), 1, 2, 4, 8, 16 or 32
  *   radix   their Stockham stages: -1 (the plan-wide radix), 0 radix 8 first,
  *           1 radix 4 and 2 only
  * Errors: PS_ERR_ARG (plan NULL or built, axis or a value out of range).

@@ -332,8 +332,8 @@ int ps_plan_set_math(ps_plan p, int math_mode) {
 int ps_plan_set_schedule(ps_plan p, int tile, int radix, int ztk, int ykind, int xy, int chunks) {
   if (!p) return fail(PS_ERR_ARG, "plan is NULL");
   if (p->built) return fail(PS_ERR_ARG, "the schedule must be set before ps_kernel_build");
-  if (tile < 0 || tile > 16 || (tile & (tile - 1)) != 0)
-    return fail(PS_ERR_ARG, "tile = %d: 0 or a power of two up to 16", tile);
+  if (tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
+    return fail(PS_ERR_ARG, "tile = %d: 0 or a power of two up to 32", tile);
   if (radix != 0 && radix != 1) return fail(PS_ERR_ARG, "radix = %d: 0 or 1", radix);
   if (ztk != 0 && ztk != 8 && ztk != 16) return fail(PS_ERR_ARG, "ztk = %d: 0, 8 or 16", ztk);
   if (ykind < 0 || ykind > 2) return fail(PS_ERR_ARG, "ykind = %d: 0, 1 or 2", ykind);
@@ -352,8 +352,8 @@ int ps_plan_set_axis_schedule(ps_plan p, int axis, int tile, int radix) {
   if (!p) return fail(PS_ERR_ARG, "plan is NULL");
   if (p->built) return fail(PS_ERR_ARG, "the schedule must be set before ps_kernel_build");
   if (axis < 0 || axis > 2) return fail(PS_ERR_ARG, "axis = %d: 0, 1 or 2", axis);
-  if (tile < 0 || tile > 16 || (tile & (tile - 1)) != 0)
-    return fail(PS_ERR_ARG, "tile = %d: 0 or a power of two up to 16", tile);
+  if (tile < 0 || tile > 32 || (tile & (tile - 1)) != 0)
+    return fail(PS_ERR_ARG, "tile = %d: 0 or a power of two up to 32", tile);
   if (radix < -1 || radix > 1) return fail(PS_ERR_ARG, "radix = %d: -1, 0 or 1", radix);
   p->tile_ax[axis] = tile;
   p->radix_ax[axis] = radix;

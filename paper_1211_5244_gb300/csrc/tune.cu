@@ -8,8 +8,9 @@
 // trial plan per candidate on the device and keeps the fastest, then tunes
 // the schedule at those lengths one choice at a time (each kept only if it
 // is faster), among the choices that apply to the plan:
-//   tile    lines per tile of the generic passes (16 / 8 / 4 in FP32,
-//           8 / 4 / 2 in FP64: more CTAs per line set, shorter chains)
+//   tile    lines per tile of the generic passes (32 / 16 / 8 / 4 in FP32,
+//           16 / 8 / 4 / 2 in FP64: wider tiles give each thread more
+//           butterflies per stage, narrower ones more CTAs per line set)
 //   radix   radix split of the generic Stockham stages (radix 8 first, or
 //           radix 4 and 2 only)
 //   tile and radix again per axis: for the generic passes along each
@@ -287,14 +288,14 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
     }
   }
   if (best_ap.generic) {
-    try_field(kTile, {t0w / 2, t0w / 4});
+    try_field(kTile, {2 * t0w, t0w / 2, t0w / 4});
     try_field(kRadix, {1});
     // then axis by axis: the other tile widths and the other radix split
     for (int j = 0; j < 3; ++j) {
       if (!best_ap.generic_ax[j]) continue;
       const int cur = best[kTile] ? best[kTile] : t0w;
       std::vector<int> tiles;
-      for (int t : {t0w, t0w / 2, t0w / 4})
+      for (int t : {2 * t0w, t0w, t0w / 2, t0w / 4})
         if (t != cur) tiles.push_back(t);
       try_field(kTileAx + j, tiles);
       try_field(kRadixAx + j, {best[kRadix] ? 1 : 2});

@@ -88,7 +88,7 @@ def test_set_lengths_rules(lib):
 def test_set_schedule_rules(lib):
     rc, p = _create(lib, n=(10, 12, 7), bc=(0, 1, 1))
     assert rc == 0
-    for bad in ((3, 0, 0, 0, 0, 0), (32, 0, 0, 0, 0, 0), (0, 2, 0, 0, 0, 0), (0, 0, 4, 0, 0, 0),
+    for bad in ((3, 0, 0, 0, 0, 0), (64, 0, 0, 0, 0, 0), (0, 2, 0, 0, 0, 0), (0, 0, 4, 0, 0, 0),
                 (0, 0, 0, 3, 0, 0), (0, 0, 0, 0, 2, 0), (-1, 0, 0, 0, 0, 0), (0, 0, 0, 0, 0, 65)):
         assert lib.ps_plan_set_schedule(p, *bad) == 1, bad
     assert lib.ps_plan_set_schedule(p, 4, 1, 16, 2, 1, 8) == 0
@@ -105,7 +105,7 @@ def test_set_axis_schedule_rules(lib):
     info = ps.PlanInfo()
     assert lib.ps_plan_query(p, ctypes.byref(info)) == 0
     assert [list(a) for a in info.axis_schedule] == [[0, -1]] * 3  # plan-wide choices by default
-    for bad in ((3, 0, 0), (-1, 0, 0), (0, 3, 0), (0, 32, 0), (0, -2, 0), (0, 0, 2), (0, 0, -2)):
+    for bad in ((3, 0, 0), (-1, 0, 0), (0, 3, 0), (0, 64, 0), (0, -2, 0), (0, 0, 2), (0, 0, -2)):
         assert lib.ps_plan_set_axis_schedule(p, *bad) == 1, bad
     assert lib.ps_plan_set_axis_schedule(p, 1, 4, 1) == 0
     assert lib.ps_plan_set_axis_schedule(p, 2, 0, 0) == 0

@@ -734,6 +734,7 @@ SCHEDULES = [
     ({"ztk": 16}, {}),                   # 16 lines per z tile, separate input stage
     ({"ykind": 1}, {}),                  # unpacked persistent y kernels
     ({"ykind": 2}, {}),                  # non-persistent y kernels
+    ({"tile": 32}, {}),                  # generic passes: up to 32 lines per tile
     ({"tile": 4}, {}),                   # generic passes: at most 4 lines per tile
     ({"tile": 1, "radix": 1}, {}),       # one line per tile, radix-4 stages
     ({"xy": 1}, {}),                     # fused x/y kernels where they apply (256 x 256 planes)
@@ -766,6 +767,7 @@ def test_parity_schedules(torch_cuda, monkeypatch, sched, env, n, bc):
     ((45, 27, 35), "ppp", {0: dict(tile=4, radix=1), 1: dict(tile=1), 2: dict(radix=1)}),
     ((37, 61, 139), "ppp", {0: dict(tile=2), 1: dict(radix=1), 2: dict(tile=8, radix=0)}),
     ((29, 23, 11), "pff", {0: dict(tile=1, radix=1), 2: dict(tile=2)}),
+    ((61, 50, 37), "ppp", {0: dict(tile=32), 1: dict(tile=32, radix=1), 2: dict(tile=32)}),
 ])
 def test_parity_axis_schedules(torch_cuda, n, bc, axis_sched, dtype):
     from paper_1211_5244_gb300 import psolver
