@@ -312,8 +312,8 @@ __device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, 
 template <int P, int Q, int DIR>
 __device__ float2* blue_regs(float2* a, float2* b, int N, int tk, int ldt, const float2* ttab, int tstr,
                              const BlueArgs& bl) {
-  const float2* __restrict__ ch = static_cast<const float2*>(bl.chirp);
-  const float2* __restrict__ Bf = static_cast<const float2*>(bl.Bf);
+  const float2* ch = static_cast<const float2*>(bl.chirp);  // shared or global memory
+  const float2* Bf = static_cast<const float2*>(bl.Bf);
   const int ltk = __ffs(tk) - 1;
   for (int i = threadIdx.x; i < (Q << ltk); i += blockDim.x) {
     const int t = i & (tk - 1), col = i >> ltk;
@@ -323,7 +323,7 @@ __device__ float2* blue_regs(float2* a, float2* b, int N, int tk, int ldt, const
       const int m = col + Q * r;
       y[r] = make_float2(0.f, 0.f);
       if (r < P / 2 && m < N) {
-        const float2 x = a[m * ldt + t], c = __ldg(&ch[m]);
+        const float2 x = a[m * ldt + t], c = ch[m];
         y[r] = DIR < 0 ? cmul(x, c) : cmulc(x, c);
       }
     }
@@ -340,7 +340,7 @@ __device__ float2* blue_regs(float2* a, float2* b, int N, int tk, int ldt, const
     regs::rdft<Q, -1, false>(z);
 #pragma unroll
     for (int k2 = 0; k2 < Q; ++k2) {
-      const float2 f = __ldg(&Bf[k1 + P * k2]);
+      const float2 f = Bf[k1 + P * k2];
       z[k2] = DIR < 0 ? cmul(z[k2], f) : cmulc(z[k2], f);
     }
     regs::rdft<Q, 1, false>(z);
@@ -358,12 +358,33 @@ __device__ float2* blue_regs(float2* a, float2* b, int N, int tk, int ldt, const
     for (int r = 0; r < P / 2; ++r) {
       const int m = col + Q * r;
       if (m < N) {
-        const float2 c = __ldg(&ch[m]);
+        const float2 c = ch[m];
         b[m * ldt + t] = DIR < 0 ? cmul(y[r], c) : cmulc(y[r], c);
       }
     }
   }
   __syncthreads();
+  return b;
+}
+
+// The tables of the register form in shared memory, after the W_M table of
+// load_twiddles, when the table has room for them (in_smem: 2 BM + N
+// entries): the transformed chirp Bf at tsm + BM and the chirp at tsm + 2 BM.
+// Returns the BlueArgs the transform reads. No barrier: the caller's next
+// __syncthreads covers it.
+template <int BM, typename T>
+__device__ __forceinline__ BlueArgs blue_tables(cpx<T>* tsm, const BlueArgs& bl, int N, bool in_smem) {
+  BlueArgs b = bl;
+  if constexpr (BM > 0) {
+    if (in_smem) {
+      const cpx<T>* __restrict__ bf = static_cast<const cpx<T>*>(bl.Bf);
+      const cpx<T>* __restrict__ ch = static_cast<const cpx<T>*>(bl.chirp);
+      for (int j = threadIdx.x; j < BM; j += blockDim.x) tsm[BM + j] = bf[j];
+      for (int j = threadIdx.x; j < N; j += blockDim.x) tsm[2 * BM + j] = ch[j];
+      b.Bf = tsm + BM;
+      b.chirp = tsm + 2 * BM;
+    }
+  }
   return b;
 }
 

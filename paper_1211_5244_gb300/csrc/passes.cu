@@ -45,7 +45,8 @@ struct GenArgs {
   int tws;  // twiddle-table stride (table length / N)
   int rows; // rows of each shared-memory buffer (>= N, and >= M in Bluestein form)
   int ltk;  // log2 tk (tk is a power of two)
-  int twn;  // entries of the shared-memory twiddle table (N, or M in Bluestein form); 0: global
+  int twn;  // entries of the shared-memory twiddle table (N, or M in Bluestein form, 2M + N with
+            // the register form's tables); 0: global
   unsigned mn1, mc, mN1;  // div_magic of n1, c and N + 1
   Stages st;
   BlueArgs bl;
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
+  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
   const int nrows = a.n2 * a.n3;
   const bool even = (a.L1 % 2) == 0;
   // even L1: row t is the complex line z[m] = x[2m] + i x[2m+1] of length N;
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
     }
   }
   __syncthreads();
-  C* out = gen_transform<-1, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* out = gen_transform<-1, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, bl);
   if (even) {
     // X[k] = E[k] + W_L^k O[k],  E = (Z[k] + conj Z[N-k]) / 2,  O = -i (Z[k] - conj Z[N-k]) / 2
     const int N = a.N;
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
+  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
   const int kx0 = blockIdx.x * a.tk;
   const int z = blockIdx.y;
   const int nin = DIR < 0 ? a.n2 : a.L2;
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
     }
   }
   __syncthreads();
-  C* out = gen_transform<DIR, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* out = gen_transform<DIR, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, bl);
   for (int w = threadIdx.x; w < a.tk * nout; w += blockDim.x) {
     const int t = w & (a.tk - 1), y = w >> a.ltk;
     if (kx0 + t < a.c) d[(size_t)y * a.ldc + t] = out[y * a.ldt + t];
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
+  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
   const int kx0 = blockIdx.x * a.tk;
   const int ky = blockIdx.y;
   const size_t zstride = (size_t)a.L2 * a.ldc;
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     }
   }
   __syncthreads();
-  C* spec = gen_transform<-1, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* spec = gen_transform<-1, T, BM>(buf0, buf1, a.N, a.tk, a.ldt, a.st, ttab, tstr, bl);
   C* other = (spec == buf0) ? buf1 : buf0;
   // multiply by the octant of K^F; accumulate w(kx) K |rho^F|^2 for the energy
   const int kyo = min(ky, a.L2 - ky);
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
     }
   }
   __syncthreads();
-  C* res = gen_transform<1, T, BM>(spec, other, a.N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* res = gen_transform<1, T, BM>(spec, other, a.N, a.tk, a.ldt, a.st, ttab, tstr, bl);
   for (int w = threadIdx.x; w < a.tk * a.n3; w += blockDim.x) {
     const int t = w & (a.tk - 1), z = w >> a.ltk;
     if (kx0 + t < a.c) line[z * zstride + t] = res[z * a.ldt + t];
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
+  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
   const int nrows = a.n2 * a.n3;
   const bool even = (a.L1 % 2) == 0;
   // even L1: row t's spectrum gives the complex line of length N; odd L1:
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
     }
   }
   __syncthreads();
-  C* out = gen_transform<1, T, BM>(buf1, buf0, N, a.tk, a.ldt, a.st, ttab, tstr, a.bl);
+  C* out = gen_transform<1, T, BM>(buf1, buf0, N, a.tk, a.ldt, a.st, ttab, tstr, bl);
   for (int w = threadIdx.x; w < rpc * a.n1; w += blockDim.x) {
     const int t = div_by(w, a.mn1), i = w - t * a.n1;
     const int row = row0 + t;
@@ -499,13 +504,24 @@ cudaError_t configure_passes(ps_plan_s* p) {
     const int axis = pass_axis(p, k);
     const int Nk = xform_len(p, axis);
     const int tk0 = axis_tile(p, axis) > 0 ? axis_tile(p, axis) : tk_def;
-    const int twn = p->blue[axis].M ? p->blue[axis].M : Nk;
+    const int bm = sizeof(T) == 4 ? blue_regs_length(p->blue[axis].M, Nk) : 0;
+    const int twn = p->blue[axis].M ? p->blue[axis].M : Nk;  // W_N, or W_M in Bluestein form
     // row pitch: tk + 1 for passes along x, whose tile loops transpose rows (a
     // pitch of tk would put a row's consecutive elements on one bank); tk
     // for passes along y and z, whose tile rows are contiguous runs
     cf.tk = pick_tk(rows[k], twn, sizeof(C), tk0, axis == 0 ? 1 : 0, &cf.ldt, &cf.gsmem, &cf.twn);
     cf.smem = cf.gsmem;
-    cf.bm = sizeof(T) == 4 ? blue_regs_length(p->blue[axis].M, Nk) : 0;
+    cf.bm = bm;
+    // the register form's transformed chirp and chirp join the shared-memory
+    // table when they fit within the same budget at this tile width
+    if (bm && cf.twn > 0) {
+      const size_t ext = cf.gsmem + (size_t)(bm + Nk) * sizeof(C);
+      if (ext <= (cf.gsmem <= (size_t)72 * 1024 ? (size_t)72 * 1024 : budget)) {
+        cf.gsmem = ext;
+        cf.smem = ext;
+        cf.twn = 2 * bm + Nk;
+      }
+    }
     if (cf.tk == 0) {
       set_error("transform length %d needs more shared memory than a CTA has", rows[k]);
       return cudaErrorInvalidConfiguration;
