@@ -271,8 +271,8 @@ __device__ cpx<T>* line_transform(cpx<T>* a, cpx<T>* b, int N, int tk, int ldt, 
   using C = cpx<T>;
   if (bl.M == 0) return stockham<DIR, T>(a, b, N, tk, ldt, st, ttab, tstr);
   const int M = bl.M;
-  const C* __restrict__ ch = static_cast<const C*>(bl.chirp);
-  const C* __restrict__ Bf = static_cast<const C*>(bl.Bf);
+  const C* ch = static_cast<const C*>(bl.chirp);  // shared or global memory
+  const C* Bf = static_cast<const C*>(bl.Bf);
   const int ltk = __ffs(tk) - 1;
   const int t = threadIdx.x & (tk - 1);  // blockDim.x is a multiple of tk
   const int mstep = blockDim.x >> ltk;
@@ -367,23 +367,22 @@ __device__ float2* blue_regs(float2* a, float2* b, int N, int tk, int ldt, const
   return b;
 }
 
-// The tables of the register form in shared memory, after the W_M table of
-// load_twiddles, when the table has room for them (in_smem: 2 BM + N
-// entries): the transformed chirp Bf at tsm + BM and the chirp at tsm + 2 BM.
+// The Bluestein tables in shared memory, after the W_M table of
+// load_twiddles, when the table has room for them (in_smem: 2M + N
+// entries): the transformed chirp Bf at tsm + M and the chirp at tsm + 2M.
 // Returns the BlueArgs the transform reads. No barrier: the caller's next
 // __syncthreads covers it.
-template <int BM, typename T>
+template <typename T>
 __device__ __forceinline__ BlueArgs blue_tables(cpx<T>* tsm, const BlueArgs& bl, int N, bool in_smem) {
   BlueArgs b = bl;
-  if constexpr (BM > 0) {
-    if (in_smem) {
-      const cpx<T>* __restrict__ bf = static_cast<const cpx<T>*>(bl.Bf);
-      const cpx<T>* __restrict__ ch = static_cast<const cpx<T>*>(bl.chirp);
-      for (int j = threadIdx.x; j < BM; j += blockDim.x) tsm[BM + j] = bf[j];
-      for (int j = threadIdx.x; j < N; j += blockDim.x) tsm[2 * BM + j] = ch[j];
-      b.Bf = tsm + BM;
-      b.chirp = tsm + 2 * BM;
-    }
+  const int M = bl.M;
+  if (M > 0 && in_smem) {
+    const cpx<T>* __restrict__ bf = static_cast<const cpx<T>*>(bl.Bf);
+    const cpx<T>* __restrict__ ch = static_cast<const cpx<T>*>(bl.chirp);
+    for (int j = threadIdx.x; j < M; j += blockDim.x) tsm[M + j] = bf[j];
+    for (int j = threadIdx.x; j < N; j += blockDim.x) tsm[2 * M + j] = ch[j];
+    b.Bf = tsm + M;
+    b.chirp = tsm + 2 * M;
   }
   return b;
 }

@@ -46,7 +46,7 @@ struct GenArgs {
   int rows; // rows of each shared-memory buffer (>= N, and >= M in Bluestein form)
   int ltk;  // log2 tk (tk is a power of two)
   int twn;  // entries of the shared-memory twiddle table (N, or M in Bluestein form, 2M + N with
-            // the register form's tables); 0: global
+            // the Bluestein tables); 0: global
   unsigned mn1, mc, mN1;  // div_magic of n1, c and N + 1
   Stages st;
   BlueArgs bl;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) p1_generic(const T* __restrict__ rho, cpx
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
-  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
+  const BlueArgs bl = blue_tables<T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.bl.M && a.twn >= 2 * a.bl.M + a.N);
   const int nrows = a.n2 * a.n3;
   const bool even = (a.L1 % 2) == 0;
   // even L1: row t is the complex line z[m] = x[2m] + i x[2m+1] of length N;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) py_generic(const cpx<T>* __restrict__ src
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
-  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
+  const BlueArgs bl = blue_tables<T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.bl.M && a.twn >= 2 * a.bl.M + a.N);
   const int kx0 = blockIdx.x * a.tk;
   const int z = blockIdx.y;
   const int nin = DIR < 0 ? a.n2 : a.L2;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) pz_generic(cpx<T>* __restrict__ Bw, const
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
-  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
+  const BlueArgs bl = blue_tables<T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.bl.M && a.twn >= 2 * a.bl.M + a.N);
   const int kx0 = blockIdx.x * a.tk;
   const int ky = blockIdx.y;
   const size_t zstride = (size_t)a.L2 * a.ldc;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
   C* buf1 = buf0 + a.rows * a.ldt;
   int tstr;  // the twiddles of the transform: in shared memory after the buffers when a.twn > 0
   const C* ttab = load_twiddles<T>(buf1 + a.rows * a.ldt, tw, a.N, a.tws, a.bl, a.twn > 0, &tstr);
-  const BlueArgs bl = blue_tables<BM, T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.twn >= 2 * BM + a.N);
+  const BlueArgs bl = blue_tables<T>(buf1 + a.rows * a.ldt, a.bl, a.N, a.bl.M && a.twn >= 2 * a.bl.M + a.N);
   const int nrows = a.n2 * a.n3;
   const bool even = (a.L1 % 2) == 0;
   // even L1: row t's spectrum gives the complex line of length N; odd L1:
@@ -512,14 +512,15 @@ cudaError_t configure_passes(ps_plan_s* p) {
     cf.tk = pick_tk(rows[k], twn, sizeof(C), tk0, axis == 0 ? 1 : 0, &cf.ldt, &cf.gsmem, &cf.twn);
     cf.smem = cf.gsmem;
     cf.bm = bm;
-    // the register form's transformed chirp and chirp join the shared-memory
-    // table when they fit within the same budget at this tile width
-    if (bm && cf.twn > 0) {
-      const size_t ext = cf.gsmem + (size_t)(bm + Nk) * sizeof(C);
+    // Bluestein form: the transformed chirp and the chirp join the
+    // shared-memory table when they fit within the same budget at this tile width
+    const int M = p->blue[axis].M;
+    if (M && cf.twn > 0) {
+      const size_t ext = cf.gsmem + (size_t)(M + Nk) * sizeof(C);
       if (ext <= (cf.gsmem <= (size_t)72 * 1024 ? (size_t)72 * 1024 : budget)) {
         cf.gsmem = ext;
         cf.smem = ext;
-        cf.twn = 2 * bm + Nk;
+        cf.twn = 2 * M + Nk;
       }
     }
     if (cf.tk == 0) {
