@@ -382,10 +382,6 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
   const void* fn = nullptr;
   int T = 0, TK = 8;
   switch (L) {
-    case 256: fn = half ? (const void*)k_zpipe_u<16, 16, true, 16> : (const void*)k_zpipe_u<16, 16, false, 16>;
-      T = 16;
-      TK = 16;
-      break;
     case 1024: fn = half ? (const void*)k_zpipe_u<32, 32, true, 8> : (const void*)k_zpipe_u<32, 32, false, 8>; T = 32;
       break;
     default: return nullptr;

@@ -520,9 +520,9 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       return cudaSuccess;
     }
   }
-  // z pass (along c): the persistent prefetching packed kernel where it
-  // exists (L = 128 and 512), the persistent unpacked one at L = 256 and
-  // 1024, else the non-persistent unpacked one
+  // z pass (along c): the persistent prefetching packed kernels where they
+  // exist (L = 128, 256 and 512), the persistent unpacked one at L = 1024,
+  // else the non-persistent unpacked one
   if (pow2(Lc) && (nc <= Lc / 2 || nc == Lc)) {
     const bool half = nc <= Lc / 2;
     int threads;
@@ -535,7 +535,9 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     bool persistent = f != nullptr;
     p->zsoa_T = f ? (Lc == 128 ? 8 : 16) : 0;
     int ztile = pipe_tk;
-    // L = 256 and 1024: the persistent unpacked kernel
+    // L = 256: the packed kernel on pairs of columns and rows; L = 1024: the
+    // persistent unpacked kernel
+    if (!f && (f = zpipe_q_kernel(Lc, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
     if (!f && (f = zpipe_u_kernel(Lc, half, &threads, &smem, &ztile)) != nullptr) persistent = true;
     if (!f) f = strided_kernel(Lc, 2, half, &threads, &smem, &ztile);
     if (f) {

@@ -301,6 +301,206 @@ const void* zpipe_kernel(int L, bool half, int* tk_io, int* threads, size_t* sme
   return fn;
 }
 
+// ---------------------------------------------------------------- packed, L = 256
+
+// Persistent z pass for L3 = 256 = 16 * 16 on packed FP32x2 pairs: 8 threads
+// per line, each carrying two columns of step 1 (b = j, j + 8) and then two
+// rows of step 2 (k1 = j, j + 8) as one pair, so that every DFT of the line is
+// a 16-point DFT of a pair and no stage crosses the lanes. The exchange holds
+// slot (r, c) = the pair (column r, column r + 8) at row c, one 16-byte word;
+// step 2 forms its row pairs from two slots, step 3 returns them the same way.
+// The twiddles W_256^{b k1} of both lanes come from a paired table built in
+// shared memory from W_256^i: tp[r][c] = (W^{r c}, W^{(r + 8) c}), r < 8, c < 16,
+// used as (j, k1) by step 1 and (j, b) by step 3. TK lines per tile; the next
+// tile's input rows land in the exchange once step 4 has read it, the next
+// K^F slice once step 2 has used the current one.
+template <bool HALF, int TK>
+__global__ void __launch_bounds__(TK * 8, 4)
+    k_zpipe_q(const void*, void* line_v, const float* __restrict__ K, const float2* __restrict__ tw, FastArgs a,
+              double* partials, unsigned* counter, double escale, double* E) {
+  constexpr int T = 8, P = 16, Q = 16, L = P * Q;
+  constexpr int NA = HALF ? P / 2 : P;  // nonzero inputs / kept outputs per column
+  constexpr int ROWS = NA * Q;          // input rows per line (n3)
+  constexpr int KROWS = L / 2 + 1;      // rows of the K^F octant
+  constexpr int TP = P + 1;             // paired twiddle table row pitch
+  extern __shared__ float4 smem4[];
+  float4* sh4 = smem4;                                          // exchange [T * P][TK]
+  float2* stage = reinterpret_cast<float2*>(smem4);             // input rows [ROWS][TK] (same space)
+  float* kstage = reinterpret_cast<float*>(smem4 + T * P * TK);  // K^F [KROWS][TK]
+  float4* tp = reinterpret_cast<float4*>(kstage + KROWS * TK);  // [T][TP]
+  static_assert((KROWS * TK) % 4 == 0, "paired table alignment");
+  for (int i = threadIdx.x; i < T * P; i += blockDim.x) {  // before the first barrier
+    const int r = i / P, c = i % P;
+    const float2 w0 = __ldg(&tw[r * c]), w1 = __ldg(&tw[(r + T) * c]);
+    tp[r * TP + c] = make_float4(w0.x, w1.x, w0.y, w1.y);
+  }
+  const int t = threadIdx.x % TK;
+  const int j = threadIdx.x / TK;
+  auto xi = [](int r, int c) { return (r * P + c) * TK; };  // exchange slot (r, c) of line t: xi(r, c) + t
+  const int ntk = a.ntk_loc;
+  const int ntiles = ntk * a.L2;
+  float2* const base = static_cast<float2*>(line_v);
+  const long long es = a.src_elem;
+
+  constexpr int NT = TK * T;
+  constexpr int IPR = TK / 2;  // 16-byte pieces per input row
+  constexpr int ISTEP = NT / IPR;
+  static_assert(NT % IPR == 0 && ROWS % ISTEP == 0, "input copy shape");
+  constexpr int IIT = ROWS / ISTEP;
+  const int irow0 = threadIdx.x / IPR;
+  const long long igoff = (long long)irow0 * es + 2 * (threadIdx.x % IPR);
+  const long long igstep = (long long)ISTEP * es;
+  float2* const is0 = stage + irow0 * TK + 2 * (threadIdx.x % IPR);
+  const int ivalid = a.nl - irow0;
+  constexpr int KPR = TK / 4;  // 16-byte pieces per K^F row
+  constexpr int KSTEP = NT / KPR;
+  static_assert(NT % KPR == 0, "K copy shape");
+  constexpr int KIT = (KROWS + KSTEP - 1) / KSTEP;
+  const int krow0 = threadIdx.x / KPR;
+  const long long kgoff = (long long)krow0 * a.kz_stride + 4 * (threadIdx.x % KPR);
+  const long long kgstep = (long long)KSTEP * a.kz_stride;
+  float* const ks0 = kstage + krow0 * TK + 4 * (threadIdx.x % KPR);
+
+  const int dkt = gridDim.x % ntk, dyi = gridDim.x / ntk;
+  auto step_tile = [&](int& kt, int& yi) {
+    kt += dkt;
+    yi += dyi;
+    if (kt >= ntk) {
+      kt -= ntk;
+      ++yi;
+    }
+  };
+  auto issue_input = [&](int kt, int yi) {
+    const float2* src0 = base + paired_ky(yi, a.L2) * a.src_plane + (a.kt0 + kt) * TK;
+    const float2* src = src0 + igoff;
+#pragma unroll
+    for (int i = 0; i < IIT; ++i) {
+      if (ISTEP * i < ivalid)
+        cp_async16(is0 + i * ISTEP * TK, src);
+      else  // beyond the physical z rows: zeros (nothing is read)
+        cp_async16_zero(is0 + i * ISTEP * TK, src0);
+      src += igstep;
+    }
+  };
+  auto issue_k = [&](int kt, int yi) {
+    const int ky = paired_ky(yi, a.L2);
+    const int kyo = min(ky, a.L2 - ky);
+    const float* src = K + (long long)kyo * a.ldk + (a.kt0 + kt) * TK + kgoff;
+#pragma unroll
+    for (int i = 0; i < KIT; ++i) {
+      if ((i + 1) * KSTEP <= KROWS || krow0 + i * KSTEP < KROWS) cp_async16(ks0 + i * KSTEP * TK, src);
+      src += kgstep;
+    }
+  };
+
+  float eacc = 0.f;
+  int tile = blockIdx.x;
+  int kt = tile % ntk, yi = tile / ntk;
+  int nkt = kt, nyi = yi;
+  step_tile(nkt, nyi);
+  if (tile < ntiles) issue_k(kt, yi);  // K^F is not written by any pass
+  pdl_wait();
+  if (tile < ntiles) issue_input(kt, yi);
+  cp_async_commit();
+  const float2 zero = make_float2(0.f, 0.f);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    const int kx = (a.kt0 + kt) * TK + t;
+    const bool valid = kx < a.c;
+    const int ky = paired_ky(yi, a.L2);
+    float2* line = base + ky * a.src_plane + kx;
+    cp_async_wait_all();
+    __syncthreads();  // this tile's input rows and K^F slice have landed
+
+    // step 1, columns j and j + 8: DFT over aa of x[b + Q aa]
+    c2 y[P];
+#pragma unroll
+    for (int aa = 0; aa < P; ++aa) {
+      y[aa] = {zero, zero};
+      if (aa < NA && valid) {
+        const float2 u0 = stage[(j + Q * aa) * TK + t];
+        const float2 u1 = stage[(j + T + Q * aa) * TK + t];
+        y[aa] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+      }
+    }
+    __syncthreads();  // the input rows are in registers: the space becomes the exchange
+    soa::dft2<P, -1, HALF>(y);
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) y[k1] = cmul_pair<-1>(y[k1], tp[j * TP + k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) sh4[xi(j, k1) + t] = pack(y[k1]);
+    __syncthreads();
+
+    // steps 2 and 3, rows j and j + 8: DFT over b, K^F, inverse DFT
+    c2 z[Q];
+#pragma unroll
+    for (int b = 0; b < T; ++b) {
+      const c2 s0 = unpack(sh4[xi(b, j) + t]), s1 = unpack(sh4[xi(b, j + T) + t]);
+      z[b] = {make_float2(s0.re.x, s1.re.x), make_float2(s0.im.x, s1.im.x)};
+      z[b + T] = {make_float2(s0.re.y, s1.re.y), make_float2(s0.im.y, s1.im.y)};
+    }
+    soa::dft2<Q, -1, false>(z);
+    float2 e2 = zero;
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      // lanes k1 = j and j + 8: kz = k1 + P k2, the even octant at min(kz, L - kz)
+      const int kz0 = j + P * k2, kz1 = kz0 + T;
+      const int o0 = kz0 <= L / 2 ? kz0 : L - kz0, o1 = kz1 <= L / 2 ? kz1 : L - kz1;
+      const float2 kk = valid ? make_float2(kstage[o0 * TK + t], kstage[o1 * TK + t]) : zero;
+      const float2 p2 = soa::fma2(z[k2].re, z[k2].re, soa::mul2(z[k2].im, z[k2].im));
+      e2 = soa::fma2(kk, p2, e2);
+      z[k2] = {soa::mul2(z[k2].re, kk), soa::mul2(z[k2].im, kk)};
+    }
+    eacc += (e2.x + e2.y) * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
+    soa::dft2<Q, 1, false>(z);
+#pragma unroll
+    for (int b = 1; b < Q; ++b) z[b] = cmul_pair<1>(z[b], tp[j * TP + b]);
+    __syncthreads();  // the forward exchange and the K^F slice have been read
+    if (next < ntiles) issue_k(nkt, nyi);
+    cp_async_commit();
+#pragma unroll
+    for (int b = 0; b < T; ++b) {
+      sh4[xi(b, j) + t] = make_float4(z[b].re.x, z[b + T].re.x, z[b].im.x, z[b + T].im.x);
+      sh4[xi(b, j + T) + t] = make_float4(z[b].re.y, z[b + T].re.y, z[b].im.y, z[b + T].im.y);
+    }
+    __syncthreads();
+
+    // step 4, columns j and j + 8: inverse DFT over k1, outputs aa < NA
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) y[k1] = unpack(sh4[xi(j, k1) + t]);
+    __syncthreads();  // the exchange has been read: the next tile's rows may land in it
+    if (next < ntiles) issue_input(nkt, nyi);
+    cp_async_commit();
+    soa::dft2<P, 1, false, HALF>(y);  // only the NA stored outputs when HALF
+    if (valid) {
+      float2* p0 = line + (long long)j * es;
+      float2* p1 = p0 + (long long)T * es;
+      const long long step = (long long)Q * es;
+#pragma unroll
+      for (int aa = 0; aa < NA; ++aa) {
+        if (j + Q * aa < a.nl) *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+        if (j + T + Q * aa < a.nl) *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+        p0 += step;
+        p1 += step;
+      }
+    }
+    kt = nkt;
+    yi = nyi;
+    step_tile(nkt, nyi);
+  }
+  cp_async_wait_all();
+  if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
+}
+
+const void* zpipe_q_kernel(int L, bool half, int* threads, size_t* smem, int* tk) {
+  if (L != 256) return nullptr;
+  constexpr int TK = 16;
+  *threads = TK * 8;
+  // exchange (also the input rows), K^F slice, paired twiddle table
+  *smem = (size_t)8 * 16 * TK * sizeof(float4) + (size_t)129 * TK * sizeof(float) + (size_t)8 * 17 * sizeof(float4);
+  *tk = TK;
+  return half ? (const void*)k_zpipe_q<true, TK> : (const void*)k_zpipe_q<false, TK>;
+}
 // ---------------------------------------------------------------- packed y passes
 
 // Persistent packed y pass for L2 = 512 (T = 16): KIND 0 forward (n2 inputs,

@@ -63,8 +63,10 @@ const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem);
 
 // The persistent, prefetching y-pass kernels (L2 = 256, 512), or nullptr.
 const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk);
-// persistent unpacked z kernel (L = 256, 1024) and its lines per tile
+// persistent unpacked z kernel (L = 1024) and its lines per tile
 const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk);
+// persistent packed z kernel for L = 256 (pairs of columns, then of rows)
+const void* zpipe_q_kernel(int L, bool half, int* threads, size_t* smem, int* tk);
 
 // The persistent, prefetching packed z-pass kernel (L3 = 512), or nullptr.
 // tk lines per tile (8 or 16).
