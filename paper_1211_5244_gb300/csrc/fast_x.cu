@@ -354,9 +354,9 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     // persistent prefetching kernels where they exist: the packed FP32x2 ones
     // at L = 512 (n = L/2 or L; at 256^3 forward 76.5 against 83 us for the
     // unpacked kernel, inverse 79.9 against 80.2 us), the unpacked ones at
-    // L = 256 and counts below L/2. The plan's schedule y_kind = 1 takes the
-    // unpacked persistent kernels for both directions, y_kind = 2 the
-    // non-persistent ones.
+    // L = 256 and 1024 and at L = 512 with other counts. The plan's schedule
+    // y_kind = 1 takes the unpacked persistent kernels for both directions,
+    // y_kind = 2 the non-persistent ones.
     const bool plain = p->y_kind == 2;
     const bool exact = 2 * nb == Lb || nb == Lb;
     const bool soa0 = !plain && exact && p->y_kind != 1;
