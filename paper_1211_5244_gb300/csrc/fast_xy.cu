@@ -85,15 +85,9 @@ __device__ __forceinline__ float2 xmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 xmulc(float2 a, float2 b) {
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
-__device__ __forceinline__ c2 unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
-__device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
-
-template <int DIR>
-__device__ __forceinline__ c2 cmul_pair(c2 v, float4 w) {
-  const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
-  if (DIR < 0) return {soa::sub2(soa::mul2(v.re, wr), soa::mul2(v.im, wi)), soa::fma2(v.re, wi, soa::mul2(v.im, wr))};
-  return {soa::fma2(v.im, wi, soa::mul2(v.re, wr)), soa::sub2(soa::mul2(v.im, wr), soa::mul2(v.re, wi))};
-}
+using soa::cmul_pair;
+using soa::pack;
+using soa::unpack;
 
 // radix-2 stages across the two lanes of a pair (as in fast_zsoa.cu)
 template <int B>

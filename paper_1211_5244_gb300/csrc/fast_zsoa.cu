@@ -18,19 +18,12 @@
 namespace ps {
 
 using soa::c2;
+using soa::cmul_pair;
+using soa::pack;
+using soa::unpack;
 
 namespace {
 
-__device__ __forceinline__ c2 unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
-__device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
-
-// v * w (DIR = -1) or v * conj(w) (DIR = +1), lane by lane, w a table pair
-template <int DIR>
-__device__ __forceinline__ c2 cmul_pair(c2 v, float4 w) {
-  const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
-  if (DIR < 0) return {soa::sub2(soa::mul2(v.re, wr), soa::mul2(v.im, wi)), soa::fma2(v.re, wi, soa::mul2(v.im, wr))};
-  return {soa::fma2(v.im, wi, soa::mul2(v.re, wr)), soa::sub2(soa::mul2(v.im, wr), soa::mul2(v.re, wi))};
-}
 
 // radix-2 DIF stage of a 2T-point forward DFT across the lanes of z[b]
 // (lanes x_b, x_{b+T}): z[b] <- (x_b + x_{b+T}, (x_b - x_{b+T}) W_{2T}^b)

@@ -37,6 +37,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ c2 operator+(c2 a, c2 b) { return {add2(a.re, b.re), add2(a.im, b.im)}; }
 __device__ __forceinline__ c2 operator-(c2 a, c2 b) { return {sub2(a.re, b.re), sub2(a.im, b.im)}; }
 
+// a pair as one 16-byte word (re_0, re_1, im_0, im_1) and back
+__device__ __forceinline__ c2 unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+
+// v * w (DIR = -1) or v * conj(w) (DIR = +1), lane by lane, w a pair of
+// complex factors as (re_0, re_1, im_0, im_1)
+template <int DIR>
+__device__ __forceinline__ c2 cmul_pair(c2 v, float4 w) {
+  const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+  if (DIR < 0) return {sub2(mul2(v.re, wr), mul2(v.im, wi)), fma2(v.re, wi, mul2(v.im, wr))};
+  return {fma2(v.im, wi, mul2(v.re, wr)), sub2(mul2(v.im, wr), mul2(v.re, wi))};
+}
+
 // a + DIR i b and a - DIR i b, with the multiplication by i folded in
 template <int DIR>
 __device__ __forceinline__ c2 add_i(c2 a, c2 b) {  // a + (DIR i) b
