@@ -450,7 +450,7 @@ int ps_kernel_build(ps_plan p, void* stream) {
       {reinterpret_cast<void**>(&p->partials), (size_t)p->npart * sizeof(double), "energy partials"},
       {reinterpret_cast<void**>(&p->counter), 2 * sizeof(unsigned), "energy counter and status"},
       {&p->tctab, p->tctab_floats * sizeof(float), "tensor-core z tables"},
-      {&p->tw4z, p->zsoa_T ? (size_t)p->zsoa_T * p->zsoa_T * 16 : 0, "paired z twiddles"},
+      {&p->tw4z, p->zsoa_T ? (size_t)p->zsoa_T * p->zsoa_P * 16 : 0, "paired z twiddles"},
       {&p->twx, p->xP ? (size_t)p->xP * p->xP * 8 : 0, "x twiddle matrix"},
       {&p->tw4y, p->ysoa ? (size_t)16 * 16 * 16 : 0, "paired y twiddles"},
   };

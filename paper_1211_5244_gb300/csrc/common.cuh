@@ -143,7 +143,8 @@ struct ps_plan_s {
   void* twx;     // x passes: W_M^{r c}, r, c < xP (float2, M = L1/2), or NULL
   int xP;        // size of twx (the larger step of the x-pass factorisation)
   int ysoa;      // packed y kernels (L2 = 512): bit 0 forward, bit 1 inverse
-  int zsoa_T;    // T of the packed z kernel (L3 = 2 T^2), 0 if not used
+  int zsoa_T;    // T of the packed z kernel (L3 = P * 2T), 0 if not used
+  int zsoa_P;    // P of the packed z kernel (T, or 12 at L3 = 384)
   void* tctab;   // tensor-core z pass: DFT matrices (hi, lo) and twiddles, or NULL
   size_t tctab_floats;
   double* partials;     // per-CTA energy partials of the z pass

@@ -280,6 +280,7 @@ static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 cudaError_t configure_fast_f32(ps_plan_s* p) {
   const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
+  p->zsoa_T = p->zsoa_P = 0;
   const int L1 = p->L[0], L2 = p->L[1], L3 = p->L[2];
   const long long ldc = (long long)p->ldc;
   cudaError_t e;
@@ -516,14 +517,15 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
       if ((e = set(P3, f, dim3((unsigned)(g < tiles ? g : tiles)), threads, smem, z)) != cudaSuccess) return e;
       p->cfg[P3].tk = 8;
       p->zsoa_T = 0;
+      p->zsoa_P = 0;
       p->tctab_floats = ztc_table_floats(half);
       return cudaSuccess;
     }
   }
   // z pass (along c): the persistent prefetching packed kernels where they
-  // exist (L = 128, 256 and 512), the persistent unpacked one at L = 1024,
-  // else the non-persistent unpacked one
-  if (pow2(Lc) && (nc <= Lc / 2 || nc == Lc)) {
+  // exist (L = 128, 256, 384 and 512), the persistent unpacked one at
+  // L = 1024, else the non-persistent unpacked one
+  if ((pow2(Lc) || Lc == 384) && (nc <= Lc / 2 || nc == Lc)) {
     const bool half = nc <= Lc / 2;
     int threads;
     size_t smem;
@@ -531,9 +533,11 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     // per SM; at 256^3 228 us against 251 us for 16 lines and 280 us for 4),
     // or 16 where the plan's schedule z_tk asks for it
     int pipe_tk = p->z_tk == 16 ? 16 : 8;
-    const void* f = zpipe_kernel(Lc, half, &pipe_tk, &threads, &smem);
+    int zP = 0;
+    const void* f = zpipe_kernel(Lc, half, &pipe_tk, &threads, &smem, &zP);
     bool persistent = f != nullptr;
     p->zsoa_T = f ? (Lc == 128 ? 8 : 16) : 0;
+    p->zsoa_P = f ? zP : 0;
     int ztile = pipe_tk;
     // L = 256: the packed kernel on pairs of columns and rows; L = 1024: the
     // persistent unpacked kernel

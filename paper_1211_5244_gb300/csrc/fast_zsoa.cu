@@ -1,15 +1,16 @@
-// z pass (forward transform, K^F multiply, inverse transform) for L3 = 2 T^2
-// (T = 8: 128, T = 16: 512) on packed FP32x2 pairs.
+// z pass (forward transform, K^F multiply, inverse transform) for L3 = P * 2T
+// (P = T = 8: 128, P = T = 16: 512; P = 12, T = 16: 384) on packed FP32x2 pairs.
 //
-// Same four-step factorisation as fast_strided.cu with P = T, Q = 2T and T
-// threads per line, but every thread carries its two step-1 transforms
+// Same four-step factorisation as fast_strided.cu with P rows, Q = 2T columns
+// and T threads per line, but every thread carries its two step-1 transforms
 // (b = j and b = j + T) as one structure-of-arrays pair, so their additions
-// run as FP32x2 instructions. The exchange stores each pair as one 16-byte
+// run as FP32x2 instructions. With P < T (L = 384) the threads j >= P hold no
+// row in steps 2 and 3 and wait at the barriers. The exchange stores each pair as one 16-byte
 // word. The Q-point step splits into a radix-2 stage across the pair
 // (lanes b and b + T) and two T-point transforms that again form a pair
 // (even and odd outputs). The same pairing returns in the inverse. The
 // twiddles W_L^{b k1} of both lanes come from one float4 table,
-// tw4[r * T + c] = (Re W^{rc}, Re W^{(r+T)c}, Im W^{rc}, Im W^{(r+T)c}),
+// tw4[r * P + c] = (Re W^{rc}, Re W^{(r+T)c}, Im W^{rc}, Im W^{(r+T)c}), r < T, c < P,
 // used as (r, c) = (j, k1) by the forward and (b, j) by the inverse step.
 #include "fft_fast.cuh"
 #include "fft_soa.cuh"
@@ -61,11 +62,12 @@ __device__ __forceinline__ void dit_all(c2 (&z)[T], std::integer_sequence<int, B
 // rows) and copies the next tile's n3 input rows and its K^F octant slice into
 // shared memory with cp.async while it computes the current tile, so the
 // global-load latency of one tile overlaps the arithmetic of the previous one.
-template <int T, bool HALF, int TK>
+template <int T, int P, bool HALF, int TK>
 __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     k_zconv_pipe(const void*, void* line_v, const float* __restrict__ K, const float4* __restrict__ tw4,
                  FastArgs a, double* partials, unsigned* counter, double escale, double* E) {
-  constexpr int P = T, Q = 2 * T, L = P * Q;
+  constexpr int Q = 2 * T, L = P * Q;
+  static_assert(P <= T, "a thread holds at most one row of steps 2 and 3");
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = NA * Q;          // input rows per line (n3)
   constexpr int KROWS = L / 2 + 1;      // rows of the K^F octant
@@ -195,35 +197,41 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
     for (int k1 = 0; k1 < P; ++k1) sh4[xi(j, k1) + t] = pack(y[k1]);
     __syncthreads();
 
+    // steps 2 and 3 on row k1 = j (rows exist for j < P only)
+    const bool has_row = P == T || j < P;
     c2 z[T];
+    if (has_row) {
 #pragma unroll
-    for (int b = 0; b < T; ++b) z[b] = unpack(sh4[xi(b, j) + t]);
-    dif_all<T>(z, std::make_integer_sequence<int, T>{});
-    soa::dft2<T, -1, false>(z);
+      for (int b = 0; b < T; ++b) z[b] = unpack(sh4[xi(b, j) + t]);
+      dif_all<T>(z, std::make_integer_sequence<int, T>{});
+      soa::dft2<T, -1, false>(z);
 
-    float2 e2 = make_float2(0.f, 0.f);
+      float2 e2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int m = 0; m < T; ++m) {
-      // kz0 = j + 2 T m and kz1 = kz0 + T (j < T) are both below L/2 exactly
-      // when m < T/2; above, the even octant is read at L - kz
-      const int kz0 = j + P * 2 * m, kz1 = kz0 + P;
-      const int o0 = m < T / 2 ? kz0 : L - kz0, o1 = m < T / 2 ? kz1 : L - kz1;
-      const float2 kk = valid ? make_float2(kstage[o0 * TK + t], kstage[o1 * TK + t]) : make_float2(0.f, 0.f);
-      const float2 p2 = soa::fma2(z[m].re, z[m].re, soa::mul2(z[m].im, z[m].im));
-      e2 = soa::fma2(kk, p2, e2);
-      z[m] = {soa::mul2(z[m].re, kk), soa::mul2(z[m].im, kk)};
+      for (int m = 0; m < T; ++m) {
+        // kz0 = j + 2 P m and kz1 = kz0 + P (j < P) are both below L/2 = P T
+        // exactly when m < T/2; above, the even octant is read at L - kz
+        const int kz0 = j + P * 2 * m, kz1 = kz0 + P;
+        const int o0 = m < T / 2 ? kz0 : L - kz0, o1 = m < T / 2 ? kz1 : L - kz1;
+        const float2 kk = valid ? make_float2(kstage[o0 * TK + t], kstage[o1 * TK + t]) : make_float2(0.f, 0.f);
+        const float2 p2 = soa::fma2(z[m].re, z[m].re, soa::mul2(z[m].im, z[m].im));
+        e2 = soa::fma2(kk, p2, e2);
+        z[m] = {soa::mul2(z[m].re, kk), soa::mul2(z[m].im, kk)};
+      }
+      eacc += (e2.x + e2.y) * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
+
+      soa::dft2<T, 1, false>(z);
+      dit_all<T>(z, std::make_integer_sequence<int, T>{});
+#pragma unroll
+      for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], twid(b, j));
     }
-    eacc += (e2.x + e2.y) * ((kx == 0 || 2 * kx == a.L1) ? 1.f : 2.f);
-
-    soa::dft2<T, 1, false>(z);
-    dit_all<T>(z, std::make_integer_sequence<int, T>{});
-#pragma unroll
-    for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], twid(b, j));
     __syncthreads();  // the forward exchange and the K^F stage have been read
     if (next < ntiles) issue_k(nkt, nyi);
     cp_async_commit();
+    if (has_row) {
 #pragma unroll
-    for (int b = 0; b < T; ++b) sh4[xi(b, j) + t] = pack(z[b]);
+      for (int b = 0; b < T; ++b) sh4[xi(b, j) + t] = pack(z[b]);
+    }
     __syncthreads();
 
 #pragma unroll
@@ -264,33 +272,41 @@ __global__ void __launch_bounds__(TK * T, 512 / (TK * T))
   if (E != nullptr) energy_finish_f32(eacc, partials, counter, escale, E);
 }
 
-const void* zpipe_kernel(int L, bool half, int* tk_io, int* threads, size_t* smem) {
+const void* zpipe_kernel(int L, bool half, int* tk_io, int* threads, size_t* smem, int* P_out) {
   const void* fn = nullptr;
   int T = 0;
   int tk = *tk_io;
   if (tk != 8 && tk != 16) return nullptr;
+  int P = 0;
   switch (L) {
     case 128:  // 16 lines per tile (8 would leave a CTA at two warps)
-      fn = half ? (const void*)k_zconv_pipe<8, true, 16> : (const void*)k_zconv_pipe<8, false, 16>;
-      T = 8;
+      fn = half ? (const void*)k_zconv_pipe<8, 8, true, 16> : (const void*)k_zconv_pipe<8, 8, false, 16>;
+      T = P = 8;
       tk = 16;
+      break;
+    case 384:  // 12 x 32, 8 lines per tile
+      fn = half ? (const void*)k_zconv_pipe<16, 12, true, 8> : (const void*)k_zconv_pipe<16, 12, false, 8>;
+      T = 16;
+      P = 12;
+      tk = 8;
       break;
     case 512:
       if (tk == 16)
-        fn = half ? (const void*)k_zconv_pipe<16, true, 16> : (const void*)k_zconv_pipe<16, false, 16>;
+        fn = half ? (const void*)k_zconv_pipe<16, 16, true, 16> : (const void*)k_zconv_pipe<16, 16, false, 16>;
       else
-        fn = half ? (const void*)k_zconv_pipe<16, true, 8> : (const void*)k_zconv_pipe<16, false, 8>;
-      T = 16;
+        fn = half ? (const void*)k_zconv_pipe<16, 16, true, 8> : (const void*)k_zconv_pipe<16, 16, false, 8>;
+      T = P = 16;
       break;
     default: return nullptr;
   }
-  const int NA = half ? T / 2 : T;
+  const int NA = half ? P / 2 : P;
   *tk_io = tk;
   *threads = tk * T;
+  *P_out = P;
   // exchange, input stage (16 lines only; 8 lines reuse the exchange), K^F
   // slice, twiddle table (8 lines only)
-  *smem = (size_t)T * T * tk * sizeof(float4) + (tk == 16 ? (size_t)NA * 2 * T * tk * sizeof(float2) : 0) +
-          (size_t)(T * T + 1) * tk * sizeof(float) + (tk == 8 ? (size_t)T * (T + 1) * sizeof(float4) : 0);
+  *smem = (size_t)T * P * tk * sizeof(float4) + (tk == 16 ? (size_t)NA * 2 * T * tk * sizeof(float2) : 0) +
+          (size_t)(P * T + 1) * tk * sizeof(float) + (tk == 8 ? (size_t)T * (P + 1) * sizeof(float4) : 0);
   return fn;
 }
 

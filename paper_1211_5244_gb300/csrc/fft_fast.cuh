@@ -70,7 +70,8 @@ const void* zpipe_q_kernel(int L, bool half, int* threads, size_t* smem, int* tk
 
 // The persistent, prefetching packed z-pass kernel (L3 = 512), or nullptr.
 // tk lines per tile (8 or 16).
-const void* zpipe_kernel(int L, bool half, int* tk, int* threads, size_t* smem);  // *tk: requested in, used out
+// *tk: requested in, used out; *P: rows of the four-step factorisation L = P * 2T
+const void* zpipe_kernel(int L, bool half, int* tk, int* threads, size_t* smem, int* P);
 
 // The tensor-core z-pass kernel (L3 = 512; half: n3 = 256, else n3 = 512),
 // its table size in floats and the host fill of that table.

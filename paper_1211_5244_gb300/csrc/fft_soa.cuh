@@ -100,8 +100,59 @@ __device__ __forceinline__ c2 twc2(c2 v) {
   }
 }
 
+// v * W_N^K (DIR = -1) or v * conj(W_N^K) (DIR = +1), both lanes, for N
+// dividing 96 (the radix-3 combinations), constants folded
+template <int N, int K, int DIR>
+__device__ __forceinline__ c2 twk2(c2 v) {
+  static_assert(96 % N == 0 && K >= 0, "N must divide 96");
+  constexpr int m = (K * (96 / N)) % 96;
+  if constexpr (m == 0) {
+    return v;
+  } else if constexpr (m == 48) {
+    return {make_float2(-v.re.x, -v.re.y), make_float2(-v.im.x, -v.im.y)};
+  } else if constexpr (m == 24 || m == 72) {
+    constexpr bool minus_i = (m == 24) == (DIR < 0);
+    return minus_i ? c2{v.im, make_float2(-v.re.x, -v.re.y)} : c2{make_float2(-v.im.x, -v.im.y), v.re};
+  } else {
+    constexpr float c = (float)regs::cos96(m), sn = (float)regs::sin96(m);
+    const float2 C = make_float2(c, c), SN = make_float2(sn, sn), NSN = make_float2(-sn, -sn);
+    if constexpr (DIR < 0) return {fma2(v.im, SN, mul2(v.re, C)), fma2(v.re, NSN, mul2(v.im, C))};
+    else return {fma2(v.im, NSN, mul2(v.re, C)), fma2(v.re, SN, mul2(v.im, C))};
+  }
+}
+
+// 3-point DFT of both lanes in place: y0 = a + s, y1,2 = (a - s/2) +- DIR i
+// (sqrt(3)/2)(b - c), s = b + c
+template <int DIR>
+__device__ __forceinline__ void bfly3(c2& a, c2& b, c2& c) {
+  const float2 H = make_float2(0.86602540378443864676f, 0.86602540378443864676f);
+  const float2 NHALF = make_float2(-0.5f, -0.5f);
+  const c2 s = b + c, d = b - c;
+  const c2 m = {fma2(s.re, NHALF, a.re), fma2(s.im, NHALF, a.im)};
+  const c2 hd = {mul2(d.re, H), mul2(d.im, H)};
+  a = a + s;
+  b = add_i<DIR>(m, hd);
+  c = sub_i<DIR>(m, hd);
+}
+
 template <int N, int DIR, bool HZ, bool HO = false>
 __device__ __forceinline__ void dft2(c2 (&x)[N]);
+
+// radix-3 combination for output index K of an N-point DIT step (N = 3 M)
+template <int N, int K, int DIR>
+__device__ __forceinline__ void bfly3k(c2 (&x)[N], const c2 (&s0)[N / 3], const c2 (&s1)[N / 3],
+                                       const c2 (&s2)[N / 3]) {
+  c2 t0 = s0[K], t1 = twk2<N, K, DIR>(s1[K]), t2 = twk2<N, 2 * K, DIR>(s2[K]);
+  bfly3<DIR>(t0, t1, t2);
+  x[K] = t0;
+  x[K + N / 3] = t1;
+  x[K + 2 * N / 3] = t2;
+}
+template <int N, int DIR, int... K>
+__device__ __forceinline__ void combine3(c2 (&x)[N], const c2 (&s0)[N / 3], const c2 (&s1)[N / 3],
+                                         const c2 (&s2)[N / 3], std::integer_sequence<int, K...>) {
+  (bfly3k<N, K, DIR>(x, s0, s1, s2), ...);
+}
 
 // HO: only the outputs below N/2 are formed
 template <int N, int K, int DIR, bool HO>
@@ -137,13 +188,29 @@ __device__ __forceinline__ void combine4(c2 (&x)[N], const c2 (&s0)[N / 4], cons
   (bfly4<N, K, DIR, HO>(x, s0, s1, s2, s3), ...);
 }
 
-// In-place N-point DFTs of both lanes (N a power of two <= 64), natural order.
-// HZ: the upper half of the input is zero. HO: only the lower half of the
-// output is needed (N >= 8; the upper half is left undefined).
+// In-place N-point DFTs of both lanes (N a power of two <= 64, or three
+// times one), natural order. HZ: the upper half of the input is zero. HO:
+// only the lower half of the output is needed (N >= 8; the upper half is left
+// undefined; with the factor 3 the caller's unread outputs are simply not
+// formed by the compiler).
 template <int N, int DIR, bool HZ, bool HO>
 __device__ __forceinline__ void dft2(c2 (&x)[N]) {
   static_assert(!HO || N >= 8, "output pruning needs the radix-4 combine");
-  if constexpr (N == 1) {
+  if constexpr (N % 3 == 0) {
+    constexpr int M = N / 3;
+    static_assert(!HZ || M % 2 == 0, "HZ needs an even sub-length");
+    c2 s0[M], s1[M], s2[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      s0[i] = x[3 * i];
+      s1[i] = x[3 * i + 1];
+      s2[i] = x[3 * i + 2];
+    }
+    dft2<M, DIR, HZ>(s0);
+    dft2<M, DIR, HZ>(s1);
+    dft2<M, DIR, HZ>(s2);
+    combine3<N, DIR>(x, s0, s1, s2, std::make_integer_sequence<int, M>{});
+  } else if constexpr (N == 1) {
   } else if constexpr (N == 2) {
     if constexpr (HZ) {
       x[1] = x[0];

@@ -231,9 +231,9 @@ __global__ void twiddle_matrix_kernel(float2* twx, int L1, int P) {
 
 // paired twiddles of the packed z kernel: tw4[r T + c] = (Re W^{rc}, Re W^{(r+T)c},
 // Im W^{rc}, Im W^{(r+T)c}), W = exp(-2 pi i / L), r, c < T
-__global__ void twiddle_pairs_kernel(float4* tw4, int L, int T) {
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < T * T; idx += gridDim.x * blockDim.x) {
-    const int r = idx / T, c = idx % T;
+__global__ void twiddle_pairs_kernel(float4* tw4, int L, int T, int P) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < T * P; idx += gridDim.x * blockDim.x) {
+    const int r = idx / P, c = idx % P;
     double s0, c0, s1, c1;
     sincospi(2.0 * ((r * c) % L) / L, &s0, &c0);
     sincospi(2.0 * (((r + T) * c) % L) / L, &s1, &c1);
@@ -310,10 +310,10 @@ cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s) {
     twiddle_matrix_kernel<<<grid_for(p->xP * p->xP), 256, 0, s>>>(static_cast<float2*>(p->twx), p->L[0], p->xP);
   // the packed y and z kernels run along the second and third axes of the order
   if (p->ysoa)
-    twiddle_pairs_kernel<<<grid_for(256), 256, 0, s>>>(static_cast<float4*>(p->tw4y), p->L[p->ord[1]], 16);
+    twiddle_pairs_kernel<<<grid_for(256), 256, 0, s>>>(static_cast<float4*>(p->tw4y), p->L[p->ord[1]], 16, 16);
   if (p->zsoa_T)
-    twiddle_pairs_kernel<<<grid_for(p->zsoa_T * p->zsoa_T), 256, 0, s>>>(static_cast<float4*>(p->tw4z),
-                                                                       p->L[p->ord[2]], p->zsoa_T);
+    twiddle_pairs_kernel<<<grid_for(p->zsoa_T * p->zsoa_P), 256, 0, s>>>(
+        static_cast<float4*>(p->tw4z), p->L[p->ord[2]], p->zsoa_T, p->zsoa_P);
   return cudaGetLastError();
 }
 

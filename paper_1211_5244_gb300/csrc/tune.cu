@@ -204,7 +204,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
           ap->generic |= !tp->cfg[k].fast;
           ap->generic_ax[pass_axis(tp, k)] |= !tp->cfg[k].fast;
         }
-        ap->zpipe = tp->zsoa_T == 16 && tp->cfg[P3].fast && !tp->tctab;
+        ap->zpipe = tp->zsoa_T == 16 && tp->zsoa_P == 16 && tp->cfg[P3].fast && !tp->tctab;
         ap->ypacked = tp->ysoa == 3;
         ap->xy = tp->xyfuse != 0;
         ap->chunkable = !tp->xyfuse && tp->cfg[P1].fast && tp->cfg[P2].fast && tp->cfg[P4].fast &&

@@ -374,6 +374,27 @@ def test_parity_padded_below_half(torch_cuda, n, bc, L):
     _check(V, E, rho, bc, 0.25, "f32", L=L)
 
 
+# Lengths 384 = 12 x 32 (the factor 3 of 2n at n = 192): the packed z kernel
+# with 12-point steps 1 and 4, half and full inputs, a ragged last kx tile, an
+# odd L2, and the z-pass kernel along y (order x, z, y).
+LEN384_CASES = [
+    ((40, 36, 192), "fff", (80, 72, 384), XFIRST),
+    ((24, 20, 150), "fff", (48, 40, 384), XFIRST),   # n3 = 150 < L3/2: masked rows
+    ((30, 17, 384), "ffp", (60, 34, 384), XFIRST),   # periodic z, all 384 rows
+    ((12, 7, 192), "fpf", (24, 7, 384), XFIRST),     # odd L2 = 7
+    ((20, 192, 64), "pfp", (20, 384, 64), (0, 2, 1)),  # z-pass kernel along the free y axis
+]
+
+
+@pytest.mark.parametrize("n,bc,L,order", LEN384_CASES)
+def test_parity_length_384_kernels(torch_cuda, n, bc, L, order):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=41 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L, order=order)
+    assert list(plan.info().L) == list(L)
+    assert plan.info().blocks[2] > 0  # the specialised z-pass kernel ran
+    _check(V, E, rho, bc, 0.25, "f32", L=L)
+
+
 # Odd L2 (a periodic y axis of odd length) with the specialised z kernels:
 # their tile order pairs ky with L2 - ky and must still visit every ky once.
 ODD_L2_CASES = [
