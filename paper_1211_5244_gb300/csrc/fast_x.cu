@@ -1,5 +1,6 @@
 // Specialised FP32 kernels for the x passes (real-to-complex forward,
-// complex-to-real inverse, §3), real length L1 = 2M with M a power of two.
+// complex-to-real inverse, §3), real length L1 = 2M with M a power of two or
+// M = 192 (= 24 x 8, radix-3 register DFTs).
 //
 // A real row x of length L1 is transformed as the complex sequence
 // z[m] = x[2m] + i x[2m+1] of length M (four-step, as in fast_strided.cu),
@@ -264,6 +265,7 @@ const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, si
     case 32: fn = pick_x<8, 4, 32>(kind, half); T = 4; TR = 32; ROW = XShape<8, 4>::ROW; break;
     case 64: fn = pick_x<8, 8, 32>(kind, half); T = 8; TR = 32; ROW = XShape<8, 8>::ROW; break;
     case 128: fn = pick_x<16, 8, 32>(kind, half); T = 8; TR = 32; ROW = XShape<16, 8>::ROW; break;
+    case 192: fn = pick_x<24, 8, 16>(kind, half); T = 8; TR = 16; ROW = XShape<24, 8>::ROW; break;
     case 256: fn = pick_x<16, 16, 16>(kind, half); T = 16; TR = 16; ROW = XShape<16, 16>::ROW; break;
     case 512: fn = pick_x<32, 16, 8>(kind, half); T = 16; TR = 8; ROW = XShape<32, 16>::ROW; break;
     default: return nullptr;
@@ -330,7 +332,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   // outputs beyond n1 are not stored) or n1 = L1 (periodic). Even n1 moves
   // rho and V as 8-byte pairs of reals; odd n1 (rows off the 8-byte grid)
   // one real at a time
-  if (L1 % 2 == 0 && pow2(L1 / 2) && (n1 <= L1 / 2 || n1 == L1)) {
+  if (L1 % 2 == 0 && (pow2(L1 / 2) || L1 == 384) && (n1 <= L1 / 2 || n1 == L1)) {
     const int M = L1 / 2;
     const bool half = n1 <= M;
     int threads, rows;
@@ -338,7 +340,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const void* f0 = xline_kernel(M, 0, half, &threads, &rows, &smem);
     const void* f1 = xline_kernel(M, 1, half, &threads, &rows, &smem);
     if (f0 && f1) {
-      p->xP = M == 32 ? 8 : (M == 64 ? 8 : (M == 128 ? 16 : (M == 256 ? 16 : 32)));
+      p->xP = M == 32 ? 8 : (M == 64 ? 8 : (M == 128 ? 16 : (M == 192 ? 24 : (M == 256 ? 16 : 32))));
       dim3 grid((n2 * n3 + rows - 1) / rows);
       FastArgs xinv = base;
       xinv.rev = l2order;  // the inverse y pass wrote the last z planes last (x, y, z order)
@@ -348,7 +350,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     }
   }
   // y passes (along b): nb <= Lb/2 (zero padding) or nb = Lb (periodic)
-  if (pow2(Lb) && (nb <= Lb / 2 || nb == Lb)) {
+  if ((pow2(Lb) || Lb == 384) && (nb <= Lb / 2 || nb == Lb)) {
     const bool half = nb <= Lb / 2;
     int threads0 = 0, threads1 = 0;
     size_t smem0 = 0, smem1 = 0;  // the forward and inverse kernels may differ
@@ -360,7 +362,8 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     // y_kind = 2 the non-persistent ones.
     const bool plain = p->y_kind == 2;
     const bool exact = 2 * nb == Lb || nb == Lb;
-    const bool soa0 = !plain && exact && p->y_kind != 1;
+    // (at L = 384 the packed kernels are the only ones and take any count)
+    const bool soa0 = !plain && (exact || Lb == 384) && p->y_kind != 1;
     const bool soa1 = soa0;
     int tk0 = 16, tk1 = 16;  // lines per tile (kx columns) of the chosen kernels
     const void* f0 = soa0 ? ysoa_kernel(Lb, 0, half, &threads0, &smem0) : nullptr;

@@ -512,15 +512,18 @@ const void* zpipe_q_kernel(int L, bool half, int* threads, size_t* smem, int* tk
 }
 // ---------------------------------------------------------------- packed y passes
 
-// Persistent packed y pass for L2 = 512 (T = 16): KIND 0 forward (n2 inputs,
-// L2 outputs), KIND 1 inverse (L2 inputs, n2 outputs). Same pairs as the z
-// kernel; the next tile's rows land (cp.async) in the exchange buffer once
-// the current tile's exchange has been read.
-template <int KIND, bool HALF>
+// Persistent packed y pass for L2 = P * 32 (T = 16; P = 16: 512, P = 12:
+// 384): KIND 0 forward (n2 inputs, L2 outputs), KIND 1 inverse (L2 inputs, n2
+// outputs). Same pairs as the z kernel (with P < T the threads j >= P hold no
+// row of the 2T-point step); the next tile's rows land (cp.async) in the
+// exchange buffer once the current tile's exchange has been read. Rows beyond
+// a.nl (a count below L2/2) are zero on input and not stored on output.
+template <int KIND, int P, bool HALF>
 __global__ void __launch_bounds__(256, 2)
     k_ysoa_pipe(const void* src_v, void* dst_v, const float*, const float4* __restrict__ tw4, FastArgs a,
                 double*, unsigned*, double, double*) {
-  constexpr int T = 16, TK = 16, P = T, Q = 2 * T, L = P * Q;
+  constexpr int T = 16, TK = 16, Q = 2 * T, L = P * Q;
+  static_assert(P <= T, "a thread holds at most one row of the 2T-point step");
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = KIND == 0 ? NA * Q : L;
   extern __shared__ float4 smem4[];
@@ -549,11 +552,16 @@ __global__ void __launch_bounds__(256, 2)
   const long long igstep = (long long)ISTEP * a.src_elem;
   float2* const is0 = stage + irow0 * TK + 2 * (threadIdx.x % IPR);
   auto plane = [&](int zi) { return a.rev ? (int)a.nrows - 1 - zi : zi; };
+  const int ivalid = KIND == 0 ? a.nl - irow0 : ROWS;  // sweep i copies a physical row iff ISTEP * i < ivalid
   auto prefetch = [&](int kt, int zi) {
-    const float2* sp = src + (long long)plane(zi) * a.src_plane + (a.kt0 + kt) * TK + igoff;
+    const float2* sp0 = src + (long long)plane(zi) * a.src_plane + (a.kt0 + kt) * TK;
+    const float2* sp = sp0 + igoff;
 #pragma unroll
     for (int i = 0; i < ROWS / ISTEP; ++i) {
-      cp_async16(is0 + i * ISTEP * TK, sp);
+      if (ISTEP * i < ivalid)
+        cp_async16(is0 + i * ISTEP * TK, sp);
+      else  // beyond the physical rows: zeros (nothing is read)
+        cp_async16_zero(is0 + i * ISTEP * TK, sp0);
       sp += igstep;
     }
   };
@@ -600,19 +608,23 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int k1 = 0; k1 < P; ++k1) sh4[(j * P + k1) * TK + t] = pack(y[k1]);
       __syncthreads();
+      const bool has_row = P == T || j < P;
       c2 z[T];
+      if (has_row) {
 #pragma unroll
-      for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * TK + t]);
+        for (int b = 0; b < T; ++b) z[b] = unpack(sh4[(b * P + j) * TK + t]);
+      }
       __syncthreads();  // exchange read: the next tile's rows may land
       if (next < ntiles) prefetch(nkt, nzi);
       cp_async_commit();
+      if (has_row) {
       dif_all<T>(z, std::make_integer_sequence<int, T>{});
       soa::dft2<T, -1, false>(z);
       if (valid) {
-        // z[m] = (X[j + 2T m], X[j + T + 2T m])
+        // z[m] = (X[j + 2P m], X[j + P + 2P m])
         float2* p0 = d + (long long)j * de;
-        float2* p1 = p0 + (long long)T * de;
-        const long long step = (long long)(2 * T) * de;
+        float2* p1 = p0 + (long long)P * de;
+        const long long step = (long long)(2 * P) * de;
 #pragma unroll
         for (int m = 0; m < T; ++m) {
           *p0 = make_float2(z[m].re.x, z[m].im.x);
@@ -621,21 +633,27 @@ __global__ void __launch_bounds__(256, 2)
           p1 += step;
         }
       }
+      }
     } else {
+      const bool has_row = P == T || j < P;
       c2 z[T];
+      if (has_row) {
 #pragma unroll
-      for (int m = 0; m < T; ++m) {
-        const float2 u0 = valid ? stage[(j + 2 * T * m) * TK + t] : make_float2(0.f, 0.f);
-        const float2 u1 = valid ? stage[(j + T + 2 * T * m) * TK + t] : make_float2(0.f, 0.f);
-        z[m] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+        for (int m = 0; m < T; ++m) {
+          const float2 u0 = valid ? stage[(j + 2 * P * m) * TK + t] : make_float2(0.f, 0.f);
+          const float2 u1 = valid ? stage[(j + P + 2 * P * m) * TK + t] : make_float2(0.f, 0.f);
+          z[m] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+        }
       }
       __syncthreads();  // inputs read: the space becomes the exchange
-      soa::dft2<T, 1, false>(z);
-      dit_all<T>(z, std::make_integer_sequence<int, T>{});
+      if (has_row) {
+        soa::dft2<T, 1, false>(z);
+        dit_all<T>(z, std::make_integer_sequence<int, T>{});
 #pragma unroll
-      for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], tws[b * (P + 1) + j]);
+        for (int b = 0; b < T; ++b) z[b] = cmul_pair<1>(z[b], tws[b * (P + 1) + j]);
 #pragma unroll
-      for (int b = 0; b < T; ++b) sh4[(b * P + j) * TK + t] = pack(z[b]);
+        for (int b = 0; b < T; ++b) sh4[(b * P + j) * TK + t] = pack(z[b]);
+      }
       __syncthreads();
       c2 y[P];
 #pragma unroll
@@ -648,12 +666,22 @@ __global__ void __launch_bounds__(256, 2)
         float2* p0 = d + (long long)j * de;
         float2* p1 = p0 + (long long)T * de;
         const long long step = (long long)Q * de;
+        if (a.nl >= NA * Q) {  // every output row is physical
 #pragma unroll
-        for (int aa = 0; aa < NA; ++aa) {
-          *p0 = make_float2(y[aa].re.x, y[aa].im.x);
-          *p1 = make_float2(y[aa].re.y, y[aa].im.y);
-          p0 += step;
-          p1 += step;
+          for (int aa = 0; aa < NA; ++aa) {
+            *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+            *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+            p0 += step;
+            p1 += step;
+          }
+        } else {
+#pragma unroll
+          for (int aa = 0; aa < NA; ++aa) {
+            if (j + Q * aa < a.nl) *p0 = make_float2(y[aa].re.x, y[aa].im.x);
+            if (j + T + Q * aa < a.nl) *p1 = make_float2(y[aa].re.y, y[aa].im.y);
+            p0 += step;
+            p1 += step;
+          }
         }
       }
     }
@@ -665,12 +693,22 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem) {
-  if (L != 512) return nullptr;
-  const void* fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, true> : (const void*)k_ysoa_pipe<0, false>)
-                             : (half ? (const void*)k_ysoa_pipe<1, true> : (const void*)k_ysoa_pipe<1, false>);
+  const void* fn = nullptr;
+  int P = 0;
+  if (L == 512) {
+    P = 16;
+    fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, 16, true> : (const void*)k_ysoa_pipe<0, 16, false>)
+                   : (half ? (const void*)k_ysoa_pipe<1, 16, true> : (const void*)k_ysoa_pipe<1, 16, false>);
+  } else if (L == 384) {
+    P = 12;
+    fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, 12, true> : (const void*)k_ysoa_pipe<0, 12, false>)
+                   : (half ? (const void*)k_ysoa_pipe<1, 12, true> : (const void*)k_ysoa_pipe<1, 12, false>);
+  } else {
+    return nullptr;
+  }
   *threads = 256;
-  *smem = (size_t)16 * 16 * 16 * sizeof(float4) + (size_t)16 * 17 * sizeof(float4);  // exchange (the input
-                                                                                      // rows share it), twiddles
+  // exchange (the input rows share it), twiddles
+  *smem = (size_t)16 * P * 16 * sizeof(float4) + (size_t)16 * (P + 1) * sizeof(float4);
   return fn;
 }
 

@@ -310,7 +310,8 @@ cudaError_t build_twiddles(ps_plan_s* p, cudaStream_t s) {
     twiddle_matrix_kernel<<<grid_for(p->xP * p->xP), 256, 0, s>>>(static_cast<float2*>(p->twx), p->L[0], p->xP);
   // the packed y and z kernels run along the second and third axes of the order
   if (p->ysoa)
-    twiddle_pairs_kernel<<<grid_for(256), 256, 0, s>>>(static_cast<float4*>(p->tw4y), p->L[p->ord[1]], 16, 16);
+    twiddle_pairs_kernel<<<grid_for(256), 256, 0, s>>>(static_cast<float4*>(p->tw4y), p->L[p->ord[1]], 16,
+                                                       p->L[p->ord[1]] / 32);  // L2 = P * 32
   if (p->zsoa_T)
     twiddle_pairs_kernel<<<grid_for(p->zsoa_T * p->zsoa_P), 256, 0, s>>>(
         static_cast<float4*>(p->tw4z), p->L[p->ord[2]], p->zsoa_T, p->zsoa_P);

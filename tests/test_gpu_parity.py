@@ -383,6 +383,15 @@ LEN384_CASES = [
     ((30, 17, 384), "ffp", (60, 34, 384), XFIRST),   # periodic z, all 384 rows
     ((12, 7, 192), "fpf", (24, 7, 384), XFIRST),     # odd L2 = 7
     ((20, 192, 64), "pfp", (20, 384, 64), (0, 2, 1)),  # z-pass kernel along the free y axis
+    ((192, 10, 12), "fff", (384, 20, 24), XFIRST),     # x R2C / C2R at M = 192 = 24 x 8
+    ((384, 6, 8), "pff", (384, 12, 16), XFIRST),       # periodic x, all 384 reals
+    ((150, 6, 8), "fff", (384, 12, 16), XFIRST),       # n1 = 150 < L1/2
+    ((191, 5, 6), "fff", (384, 10, 12), XFIRST),       # odd n1
+    ((20, 192, 12), "fff", (40, 384, 24), XFIRST),     # packed y passes at L2 = 384
+    ((20, 384, 10), "fpf", (40, 384, 20), XFIRST),     # periodic y, all 384 rows
+    ((24, 150, 10), "fff", (48, 384, 20), XFIRST),     # n2 = 150 < L2/2: masked rows
+    ((20, 32, 384), "pfp", (20, 64, 384), (0, 2, 1)),  # y-pass kernels along z
+    ((192, 192, 48), "fff", (384, 384, 96), XFIRST),   # x and y at 384 together
 ]
 
 
@@ -390,9 +399,26 @@ LEN384_CASES = [
 def test_parity_length_384_kernels(torch_cuda, n, bc, L, order):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=41 + sum(n), noise=1e-3, subtract_mean="p" in bc)
     V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L, order=order)
-    assert list(plan.info().L) == list(L)
-    assert plan.info().blocks[2] > 0  # the specialised z-pass kernel ran
+    info = plan.info()
+    assert list(info.L) == list(L)
+    # the specialised kernel of every pass along an axis of length 384 ran
+    along = [info.order[0], info.order[1], info.order[2]]  # axes of the x, y and z passes
+    for passes, axis in (((0, 4), along[0]), ((1, 3), along[1]), ((2,), along[2])):
+        if L[axis] == 384:
+            assert all(info.blocks[k] > 0 for k in passes), (passes, list(info.blocks))
     _check(V, E, rho, bc, 0.25, "f32", L=L)
+
+
+def test_hartree_shape_on_length_384(torch_cuda):
+    """The 192^3 free grid of the Hartree workload at the paper's 2n = 384 on
+    every axis (the specialised kernels of all five passes), full grid against
+    the oracle."""
+    n = (192, 192, 192)
+    rho = synth.gaussian_mixture(n, 0.3, 8, seed=501, noise=1e-3)
+    V, E, plan = _gpu_solve(torch_cuda, rho, "fff", 0.3, "f32")
+    assert list(plan.info().L) == [384, 384, 384]
+    assert all(b > 0 for b in plan.info().blocks), list(plan.info().blocks)
+    _check(V, E, rho, "fff", 0.3, "f32")
 
 
 # Odd L2 (a periodic y axis of odd length) with the specialised z kernels:
