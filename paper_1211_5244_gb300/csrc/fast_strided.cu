@@ -1,4 +1,5 @@
-// Specialised FP32 kernels for the y and z passes, power-of-two lengths.
+// Specialised FP32 kernels for the y and z passes, power-of-two lengths and
+// 96 = 24 x 4, 192 = 24 x 8 (radix-3 register DFTs).
 //
 // A CTA owns 16 lines adjacent in kx (the contiguous axis of A and B), so a
 // warp reads or writes two runs of 16 consecutive complex numbers (2 x 128 B)
@@ -382,6 +383,16 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
   const void* fn = nullptr;
   int T = 0, TK = 8;
   switch (L) {
+    case 96:  // 24 x 4 and 24 x 8 (radix-3 register DFTs), 16 lines per tile
+      fn = half ? (const void*)k_zpipe_u<24, 4, true, 16> : (const void*)k_zpipe_u<24, 4, false, 16>;
+      T = 4;
+      TK = 16;
+      break;
+    case 192:
+      fn = half ? (const void*)k_zpipe_u<24, 8, true, 16> : (const void*)k_zpipe_u<24, 8, false, 16>;
+      T = 8;
+      TK = 16;
+      break;
     case 1024: fn = half ? (const void*)k_zpipe_u<32, 32, true, 8> : (const void*)k_zpipe_u<32, 32, false, 8>; T = 32;
       break;
     default: return nullptr;
@@ -574,6 +585,8 @@ const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem,
   const void* fn = nullptr;
   int T = 0, TK = kTK;
   switch (L) {
+    case 96: fn = pick_ypipe<24, 4>(kind, half); T = 4; break;    // 24 x 4 (radix-3 register DFTs)
+    case 192: fn = pick_ypipe<24, 8>(kind, half); T = 8; break;   // 24 x 8
     case 256: fn = pick_ypipe<16, 16>(kind, half); T = 16; break;
     case 512: fn = pick_ypipe<16, 32>(kind, half); T = 16; break;
     case 1024: fn = pick_ypipe<32, 32, 8>(kind, half); T = 32; TK = 8; break;

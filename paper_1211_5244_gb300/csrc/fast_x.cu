@@ -1,6 +1,6 @@
 // Specialised FP32 kernels for the x passes (real-to-complex forward,
 // complex-to-real inverse, §3), real length L1 = 2M with M a power of two or
-// M = 192 (= 24 x 8, radix-3 register DFTs).
+// M = 48, 96, 192 (12 x 4, 24 x 4, 24 x 8: radix-3 register DFTs).
 //
 // A real row x of length L1 is transformed as the complex sequence
 // z[m] = x[2m] + i x[2m+1] of length M (four-step, as in fast_strided.cu),
@@ -263,6 +263,8 @@ const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, si
   int T = 0, TR = 0, ROW = 0;
   switch (M) {
     case 32: fn = pick_x<8, 4, 32>(kind, half); T = 4; TR = 32; ROW = XShape<8, 4>::ROW; break;
+    case 48: fn = pick_x<12, 4, 32>(kind, half); T = 4; TR = 32; ROW = XShape<12, 4>::ROW; break;
+    case 96: fn = pick_x<24, 4, 32>(kind, half); T = 4; TR = 32; ROW = XShape<24, 4>::ROW; break;
     case 64: fn = pick_x<8, 8, 32>(kind, half); T = 8; TR = 32; ROW = XShape<8, 8>::ROW; break;
     case 128: fn = pick_x<16, 8, 32>(kind, half); T = 8; TR = 32; ROW = XShape<16, 8>::ROW; break;
     case 192: fn = pick_x<24, 8, 16>(kind, half); T = 8; TR = 16; ROW = XShape<24, 8>::ROW; break;
@@ -279,6 +281,8 @@ const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, si
 // ---------------------------------------------------------------- selection
 
 static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+// lengths with register kernels besides the powers of two: 3 * 2^k
+static bool len3(int v) { return v == 96 || v == 192 || v == 384; }
 
 cudaError_t configure_fast_f32(ps_plan_s* p) {
   const int n1 = p->n[0], n2 = p->n[1], n3 = p->n[2];
@@ -332,7 +336,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   // outputs beyond n1 are not stored) or n1 = L1 (periodic). Even n1 moves
   // rho and V as 8-byte pairs of reals; odd n1 (rows off the 8-byte grid)
   // one real at a time
-  if (L1 % 2 == 0 && (pow2(L1 / 2) || L1 == 384) && (n1 <= L1 / 2 || n1 == L1)) {
+  if (L1 % 2 == 0 && (pow2(L1 / 2) || len3(L1)) && (n1 <= L1 / 2 || n1 == L1)) {
     const int M = L1 / 2;
     const bool half = n1 <= M;
     int threads, rows;
@@ -340,7 +344,8 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const void* f0 = xline_kernel(M, 0, half, &threads, &rows, &smem);
     const void* f1 = xline_kernel(M, 1, half, &threads, &rows, &smem);
     if (f0 && f1) {
-      p->xP = M == 32 ? 8 : (M == 64 ? 8 : (M == 128 ? 16 : (M == 192 ? 24 : (M == 256 ? 16 : 32))));
+      p->xP = M == 32 ? 8 : M == 48 ? 12 : M == 64 ? 8 : M == 96 ? 24 : M == 128 ? 16 : M == 192 ? 24
+            : M == 256 ? 16 : 32;
       dim3 grid((n2 * n3 + rows - 1) / rows);
       FastArgs xinv = base;
       xinv.rev = l2order;  // the inverse y pass wrote the last z planes last (x, y, z order)
@@ -350,7 +355,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     }
   }
   // y passes (along b): nb <= Lb/2 (zero padding) or nb = Lb (periodic)
-  if ((pow2(Lb) || Lb == 384) && (nb <= Lb / 2 || nb == Lb)) {
+  if ((pow2(Lb) || len3(Lb)) && (nb <= Lb / 2 || nb == Lb)) {
     const bool half = nb <= Lb / 2;
     int threads0 = 0, threads1 = 0;
     size_t smem0 = 0, smem1 = 0;  // the forward and inverse kernels may differ
@@ -528,7 +533,7 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
   // z pass (along c): the persistent prefetching packed kernels where they
   // exist (L = 128, 256, 384 and 512), the persistent unpacked one at
   // L = 1024, else the non-persistent unpacked one
-  if ((pow2(Lc) || Lc == 384) && (nc <= Lc / 2 || nc == Lc)) {
+  if ((pow2(Lc) || len3(Lc)) && (nc <= Lc / 2 || nc == Lc)) {
     const bool half = nc <= Lc / 2;
     int threads;
     size_t smem;

@@ -2,8 +2,8 @@
 // of a plan.
 //
 // Any padded length L >= 2n - 1 of a free axis gives the same physical result
-// (§2), but the cost of the transforms depends on L: a power of two or 384
-// selects the register-resident kernels, other smooth lengths use fewer or
+// (§2), but the cost of the transforms depends on L: a power of two or
+// 96, 192, 384 select the register-resident kernels, other smooth lengths use fewer or
 // cheaper radix stages than 2n when 2n has a large prime factor. The tuner times one
 // trial plan per candidate on the device and keeps the fastest, then tunes
 // the schedule at those lengths one choice at a time (each kept only if it
@@ -218,7 +218,7 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
 
   // 1. padded lengths: one rule applied to every free axis (2n; the next
   // power of two; the next 2,3- and 2,3,5,7-smooth lengths; the next length
-  // with register kernels, a power of two or 384)
+  // with register kernels, a power of two or 96, 192, 384)
   static const int p2[] = {2}, p23[] = {2, 3}, p2357[] = {2, 3, 5, 7};
   std::vector<std::vector<int>> cands;
   for (int rule = 0; rule < 5; ++rule) {
@@ -236,8 +236,10 @@ extern "C" int ps_plan_autotune(ps_plan p, int reps, void* stream) {
         case 2: v[j] = next_smooth(lo, p23, 2); break;
         case 3: v[j] = next_smooth(lo, p2357, 4); break;
         default: {
-          const int q = next_smooth(lo, p2, 1);
-          v[j] = (lo <= 384 && 384 < q) ? 384 : q;
+          int q = next_smooth(lo, p2, 1);
+          for (const int r : {96, 192, 384})
+            if (lo <= r && r < q) q = r;
+          v[j] = q;
           break;
         }
       }

@@ -374,9 +374,11 @@ def test_parity_padded_below_half(torch_cuda, n, bc, L):
     _check(V, E, rho, bc, 0.25, "f32", L=L)
 
 
-# Lengths 384 = 12 x 32 (the factor 3 of 2n at n = 192): the packed z kernel
-# with 12-point steps 1 and 4, half and full inputs, a ragged last kx tile, an
-# odd L2, and the z-pass kernel along y (order x, z, y).
+# Lengths 3 * 2^k with register kernels: 384 = 12 x 32 (the factor 3 of 2n at
+# n = 192; the packed z kernel with 12-point steps 1 and 4, half and full
+# inputs, a ragged last kx tile, an odd L2, the z-pass kernel along y), the
+# packed y and the x kernels at 384, and the unpacked y / z kernels at 96 and
+# 192 and x kernels at 96 and 192 (M = 48, 96), with masked counts.
 LEN384_CASES = [
     ((40, 36, 192), "fff", (80, 72, 384), XFIRST),
     ((24, 20, 150), "fff", (48, 40, 384), XFIRST),   # n3 = 150 < L3/2: masked rows
@@ -391,20 +393,32 @@ LEN384_CASES = [
     ((20, 384, 10), "fpf", (40, 384, 20), XFIRST),     # periodic y, all 384 rows
     ((24, 150, 10), "fff", (48, 384, 20), XFIRST),     # n2 = 150 < L2/2: masked rows
     ((20, 32, 384), "pfp", (20, 64, 384), (0, 2, 1)),  # y-pass kernels along z
-    ((192, 192, 48), "fff", (384, 384, 96), XFIRST),   # x and y at 384 together
+    ((192, 192, 48), "fff", (384, 384, 96), XFIRST),   # x and y at 384 together, z at 96
+    ((20, 96, 96), "fff", (40, 192, 192), XFIRST),     # y and z at 192
+    ((16, 12, 192), "ffp", (32, 24, 192), XFIRST),     # periodic z of 192
+    ((20, 70, 80), "fff", (40, 192, 192), XFIRST),     # counts below L/2 at 192
+    ((24, 48, 48), "fff", (48, 96, 96), XFIRST),       # y and z at 96
+    ((10, 96, 30), "fpf", (20, 96, 60), XFIRST),       # periodic y of 96
+    ((96, 10, 12), "fff", (192, 20, 24), XFIRST),      # x at M = 96
+    ((192, 6, 8), "pff", (192, 12, 16), XFIRST),       # periodic x of 192
+    ((70, 6, 8), "fff", (192, 12, 16), XFIRST),        # n1 = 70 < 96
+    ((48, 10, 12), "fff", (96, 20, 24), XFIRST),       # x at M = 48
+    ((41, 6, 8), "fff", (96, 12, 16), XFIRST),         # odd n1 at M = 48
+    ((96, 96, 96), "fff", (192, 192, 192), XFIRST),    # every pass at 192
+    ((20, 32, 96), "pfp", (20, 64, 96), (0, 2, 1)),    # y-pass kernels along the periodic z axis of 96
 ]
 
 
 @pytest.mark.parametrize("n,bc,L,order", LEN384_CASES)
-def test_parity_length_384_kernels(torch_cuda, n, bc, L, order):
+def test_parity_length_3x2k_kernels(torch_cuda, n, bc, L, order):
     rho = synth.gaussian_mixture(n, 0.25, 4, seed=41 + sum(n), noise=1e-3, subtract_mean="p" in bc)
     V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L, order=order)
     info = plan.info()
     assert list(info.L) == list(L)
-    # the specialised kernel of every pass along an axis of length 384 ran
+    # the specialised kernel of every pass along an axis of length 3 * 2^k ran
     along = [info.order[0], info.order[1], info.order[2]]  # axes of the x, y and z passes
     for passes, axis in (((0, 4), along[0]), ((1, 3), along[1]), ((2,), along[2])):
-        if L[axis] == 384:
+        if L[axis] in (96, 192, 384):
             assert all(info.blocks[k] > 0 for k in passes), (passes, list(info.blocks))
     _check(V, E, rho, bc, 0.25, "f32", L=L)
 
