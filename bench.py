@@ -543,8 +543,9 @@ def _timed_steps(step, K, flush, stream, sampler, dist):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     replicas.barrier(dist)
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.2)
+    if sampler is not None:
+        sampler.start()
+        time.sleep(0.2)
     for i in range(K):
         flush.zero_()
         starts[i].record(stream)
@@ -552,7 +553,7 @@ def _timed_steps(step, K, flush, stream, sampler, dist):
         ends[i].record(stream)
     torch.cuda.synchronize()
     replicas.barrier(dist)
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler is not None else None
     return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)], clocks
 
 
@@ -618,31 +619,16 @@ def run_hartree(args):
     _build.build()
     w, bc, _ = _spec(args)
     dt = args.dtype
-    rho_np = _density(w, rank, bc, dt)
-    vbar_np = _density(dict(w, seed=w["seed"] + 77), rank, bc, dt)
-    rho = torch.from_numpy(rho_np).cuda()
-    vbar = torch.from_numpy(vbar_np).cuda()
-    gE = torch.ones((), dtype=torch.float64, device="cuda")
-    # the free-axis lengths are the autotuner's choice among 2n and the smallest
-    # 2-, 2*3- and 2*3*5*7-smooth lengths >= 2n - 1 (all give the same result);
-    # --no-autotune keeps L = 2n (384 = 2^7 * 3 at n = 192)
-    plan = psolver.Plan(w["n"], bc, w["h"], dt, autotune=not args.no_autotune)
-    info = plan.info()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    out = {}
-
-    def step():
-        r = rho.detach().requires_grad_(True)
-        V, E = hartree(r, plan)
-        torch.autograd.backward([E, V], [gE, vbar])
-        out["V"], out["E"], out["g"] = V, E, r.grad
-
+    K = args.steps
+    h = _hartree_setup(w, bc, dt, not args.no_autotune, rank)
+    plan, info, step, out, rho_np, vbar_np = h["plan"], h["info"], h["step"], h["out"], h["rho_np"], h["vbar_np"]
+    gE = h["gE"]
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    K = args.steps
     step_ms, clocks = _timed_steps(step, K, flush, stream, ClockSampler(local), dist)
     npts = int(np.prod(w["n"]))
     value, total_s = replicas.aggregate(sum(step_ms) / 1e3, K * npts, dist, device="cuda")
@@ -711,28 +697,94 @@ def run_hartree(args):
         "kernel_src": _src_hash(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import numpy as _np
-        from oracle import poisson as op
-        r64 = rho_np.astype(_np.float64)
-        vb64 = vbar_np.astype(_np.float64)
-        KF = op.kernel_fourier(w["n"], bc, w["h"])
-        t0 = time.perf_counter()
-        Vo, Eo = op.solve(r64, bc, w["h"], KF=KF)
-        KVb, _ = op.solve(vb64, bc, w["h"], KF=KF)
-        go = KVb + w["h"] ** 3 * Vo
-        tcpu = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": npts / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"one full forward + backward step in the FP64 oracle (two numpy FFT "
-                                          f"solves of the padded grid and the energy term), single thread, "
-                                          f"{tcpu:.1f} s; K^F built untimed"}
-        err = _errors(out["V"].detach().double().cpu().numpy(), Vo, float(out["E"].item()), Eo)
-        gerr = _errors(out["g"].detach().double().cpu().numpy(), go)
-        err["grad_rel_l2"], err["grad_rel_max"] = gerr["rel_l2"], gerr["rel_max"]
-        line["error_vs_oracle"] = err
+        line["cpu_baseline"], line["error_vs_oracle"] = _hartree_oracle(w, bc, rho_np, vbar_np, out)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _hartree_setup(w, bc, dt, autotune, rank):
+    """The plan, densities and step function of the differentiable Hartree
+    workload: one step is the forward solve (V, E) through the autograd
+    function and the backward pass with incoming gradients (Vbar, 1)."""
+    import torch
+    from paper_1211_5244_gb300 import psolver
+    from paper_1211_5244_gb300.autograd import hartree
+    rho_np = _density(w, rank, bc, dt)
+    vbar_np = _density(dict(w, seed=w["seed"] + 77), rank, bc, dt)
+    rho = torch.from_numpy(rho_np).cuda()
+    vbar = torch.from_numpy(vbar_np).cuda()
+    gE = torch.ones((), dtype=torch.float64, device="cuda")
+    # the free-axis lengths are the autotuner's choice among 2n, the smallest
+    # 2-, 2*3- and 2*3*5*7-smooth lengths >= 2n - 1 and the smallest one with
+    # register kernels (all give the same result); without it L = 2n (384 =
+    # 2^7 * 3 at n = 192)
+    plan = psolver.Plan(w["n"], bc, w["h"], dt, autotune=autotune)
+    out = {}
+
+    def step():
+        r = rho.detach().requires_grad_(True)
+        V, E = hartree(r, plan)
+        torch.autograd.backward([E, V], [gE, vbar])
+        out["V"], out["E"], out["g"] = V, E, r.grad
+
+    return {"plan": plan, "info": plan.info(), "step": step, "out": out, "rho_np": rho_np, "vbar_np": vbar_np,
+            "gE": gE}
+
+
+def _hartree_oracle(w, bc, rho_np, vbar_np, out):
+    """The FP64 oracle's forward + backward step on the same densities, timed
+    on one host core, and the GPU step's errors against it (V, E, gradient)."""
+    import numpy as _np
+    from oracle import poisson as op
+    r64 = rho_np.astype(_np.float64)
+    vb64 = vbar_np.astype(_np.float64)
+    KF = op.kernel_fourier(w["n"], bc, w["h"])
+    t0 = time.perf_counter()
+    Vo, Eo = op.solve(r64, bc, w["h"], KF=KF)
+    KVb, _ = op.solve(vb64, bc, w["h"], KF=KF)
+    go = KVb + w["h"] ** 3 * Vo
+    tcpu = time.perf_counter() - t0
+    npts = int(_np.prod(w["n"]))
+    base = {"value": npts / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full forward + backward step in the FP64 oracle (two numpy FFT "
+                      f"solves of the padded grid and the energy term), single thread, "
+                      f"{tcpu:.1f} s; K^F built untimed"}
+    err = _errors(out["V"].detach().double().cpu().numpy(), Vo, float(out["E"].item()), Eo)
+    gerr = _errors(out["g"].detach().double().cpu().numpy(), go)
+    err["grad_rel_l2"], err["grad_rel_max"] = gerr["rel_l2"], gerr["rel_max"]
+    return base, err
+
+
+def _hartree_measure(K, W, flush, stream, rank, dist, with_oracle):
+    """The 192^3 differentiable Hartree workload (forward + adjoint backward,
+    autotuned lengths) for the headline line: ms per step with the same timing
+    rules, and the errors of V, E and the gradient against the FP64 oracle."""
+    import numpy as np
+    import torch
+    from paper_1211_5244_gb300 import replicas, synth
+    w, bc, dt = dict(synth.WORKLOADS["hartree192_f32"]), "fff", "f32"
+    h = _hartree_setup(w, bc, dt, True, rank)
+    for _ in range(W):
+        flush.zero_()
+        h["step"]()
+    torch.cuda.synchronize()
+    step_ms, _ = _timed_steps(h["step"], K, flush, stream, None, dist)
+    npts = int(np.prod(w["n"]))
+    value, total_s = replicas.aggregate(sum(step_ms) / 1e3, K * npts, dist, device="cuda")
+    ms = total_s * 1e3 / K
+    info = h["info"]
+    peak, _ = _peak_hbm()
+    step_bytes = 2 * info.alg_bytes + 3 * npts * 4
+    res = {"ms_per_step": ms, "value": value, "unit": UNIT, "L": list(info.L),
+           "workload": _workload_desc(w, bc, dt, list(info.L)) + "; step = forward (V, E) + backward with "
+                       "(Vbar, 1) through ps_solve_vjp, autotuned lengths",
+           "step_roofline": {"alg_bytes": step_bytes, "frac": step_bytes / (ms / 1e3) / 1e9 / peak,
+                             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    if with_oracle:
+        _, res["error_vs_oracle"] = _hartree_oracle(w, bc, h["rho_np"], h["vbar_np"], h["out"])
+    return res
 
 
 def _tf32x3_measure(w, bc, rho, K, W, flush, stream, dist, ref):
@@ -796,7 +848,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="headline line without its tf32x3 and batched64 objects")
+                    help="headline line without its tf32x3, batched64 and hartree192 objects")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "free512", "bc128", "hartree192", "localpot256", "batched64"],
                     help="localpot256: the 256^3 free solve with a caller's even kernel (ps_kernel_set_real)")
@@ -970,6 +1022,12 @@ def main():
                                                  with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         except Exception as exc:
             line["batched64"] = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            line["hartree192"] = _hartree_measure(min(K, 50), args.warmup, flush, stream, rank, dist,
+                                                  with_oracle=(rank == 0 and world == 1
+                                                               and not args.no_cpu_baseline))
+        except Exception as exc:
+            line["hartree192"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -513,7 +513,8 @@ CHUNK_CASES = [
     ((256, 256, 20), "fff", 3, 3),     # chunks of 7, 7, 6 planes (y packed persistent L = 512)
     ((64, 128, 40), "fff", 4, 4),      # y unpacked persistent L = 256, x M = 64
     ((128, 128, 17), "pff", 17, 17),   # one plane per chunk
-    ((96, 256, 24), "ppf", 5, 1),      # x M = 48 on the generic kernels: chunks do not apply
+    ((80, 256, 24), "ppf", 5, 1),      # x M = 40 on the generic kernels: chunks do not apply
+    ((96, 256, 24), "ppf", 5, 5),      # x M = 48 (12 x 4 register kernels) in chunks
     ((256, 512, 12), "fpf", 2, 2),     # y packed full L = 512
 ]
 
