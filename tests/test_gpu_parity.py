@@ -435,6 +435,23 @@ def test_hartree_shape_on_length_384(torch_cuda):
     _check(V, E, rho, "fff", 0.3, "f32")
 
 
+# The unpacked L3 = 1024 z kernel (32 x 32) with counts below and at L3/2, an
+# odd L2, a ragged kx tile, and all 1024 rows physical
+SPLIT1024_CASES = [
+    ((20, 12, 512), "fff", (40, 24, 1024)),    # n3 = L3/2
+    ((9, 7, 400), "fpf", (18, 7, 1024)),       # n3 = 400 < 512, odd L2, a ragged kx tile
+    ((6, 5, 1024), "ffp", (12, 10, 1024)),     # periodic z of 1024
+]
+
+
+@pytest.mark.parametrize("n,bc,L", SPLIT1024_CASES)
+def test_parity_z_length_1024(torch_cuda, n, bc, L):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=61 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, plan = _gpu_solve(torch_cuda, rho, bc, 0.25, "f32", L=L, order=XFIRST)
+    assert plan.info().blocks[2] > 0
+    _check(V, E, rho, bc, 0.25, "f32", L=L)
+
+
 # Odd L2 (a periodic y axis of odd length) with the specialised z kernels:
 # their tile order pairs ky with L2 - ky and must still visit every ky once.
 ODD_L2_CASES = [
