@@ -41,7 +41,10 @@ struct XShape {
   static constexpr int T = P < Q ? P : Q;
   static constexpr int QP = Q + 2;
   static constexpr int EX = P * QP;
-  static constexpr int ROW = EX > M + 1 ? EX : M + 1;
+  static constexpr int ROW0 = EX > M + 1 ? EX : M + 1;
+  // with T < 16 lanes per row a warp spans 32 / T rows: a row pitch of T
+  // (mod 16) float2 puts the rows of a half-warp on different banks
+  static constexpr int ROW = T >= 16 ? ROW0 : ROW0 + ((T - ROW0 % 16) % 16 + 16) % 16;
   static_assert(EX > M + 1 && EX % 2 == 0, "the exchange region must be even and hold the row spectrum");
 };
 
