@@ -24,8 +24,13 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+// lengths of the register four-step Bluestein convolution (FP32): powers of
+// two and 3 * 2^k from 32 to 384, at least 2N (the N inputs fill the lower
+// half of each column of its first step)
 int blue_regs_length(int M, int N) {
-  return (M >= 32 && M <= 256 && (M & (M - 1)) == 0 && M >= 2 * N) ? M : 0;
+  for (const int v : {32, 64, 96, 128, 192, 256, 384})
+    if (v == M) return M >= 2 * N ? M : 0;
+  return 0;
 }
 
 }  // namespace ps
@@ -263,16 +268,17 @@ int ps_plan_set_lengths(ps_plan p, int L1, int L2, int L3) {
       const size_t csz = 2 * (p->dtype == PS_F32 ? 4 : 8);
       const int max_M = (int)std::min<size_t>(kMaxLen, 200 * 1024 / (2 * 2 * csz));
       int M = bluestein_length(N, max_M);
-      // FP32: the power of two >= 2N - 1 where the register four-step form
-      // exists (about twice the points of the smooth length, at a fraction of
-      // the cost per point of the Stockham stages); PS_BLUE_REGS=0 (or
-      // PS_BLUE_M=min) keeps the smooth length
+      // FP32: the shortest length >= 2N where the register four-step form
+      // exists (a power of two or 3 * 2^k up to 384: up to twice the points of
+      // the smooth length, at a fraction of the cost per point of the
+      // Stockham stages); PS_BLUE_REGS=0 (or PS_BLUE_M=min) keeps the smooth length
       const char* rv = getenv("PS_BLUE_REGS");
       const char* mv = getenv("PS_BLUE_M");
       const bool regs = !(rv && atoi(rv) == 0) && !(mv && strcmp(mv, "min") == 0);
-      int m2 = 1;
-      while (m2 < 2 * N - 1) m2 *= 2;
-      if (p->dtype == PS_F32 && regs && blue_regs_length(m2, N)) M = m2;
+      int m2 = 0;
+      for (const int v : {32, 64, 96, 128, 192, 256, 384})
+        if (m2 == 0 && v >= 2 * N) m2 = v;
+      if (p->dtype == PS_F32 && regs && m2 && blue_regs_length(m2, N)) M = m2;
       if (M <= max_M) {
         p->blue[j].M = M;
         p->blue[j].st = factorize(M);

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) p5_generic(const cpx<T>* __restrict__ A, 
 
 // The five generic kernels of one Bluestein form: BM = 0 runs the Stockham
 // stages (any length), BM > 0 the register four-step convolution of length
-// BM (FP32, a power of two from 32 to 1024).
+// BM (FP32; 32, 64, 96, 128, 192, 256 or 384).
 template <typename T>
 struct GenKernels {
   void (*p1)(const T*, cpx<T>*, const cpx<T>*, GenArgs);
@@ -359,8 +359,11 @@ static GenKernels<T> gen_kernels(int bm) {
     switch (bm) {
       case 32: return gen_kernels_of<T, 32>();
       case 64: return gen_kernels_of<T, 64>();
+      case 96: return gen_kernels_of<T, 96>();
       case 128: return gen_kernels_of<T, 128>();
+      case 192: return gen_kernels_of<T, 192>();
       case 256: return gen_kernels_of<T, 256>();
+      case 384: return gen_kernels_of<T, 384>();
       default: break;
     }
   }

@@ -435,6 +435,24 @@ def test_hartree_shape_on_length_384(torch_cuda):
     _check(V, E, rho, "fff", 0.3, "f32")
 
 
+# Periodic prime lengths whose Bluestein convolution takes the register form at
+# 96, 192 and 384 (3 * 2^k, at least 2N) along each axis, FP32; FP64 plans keep
+# the Stockham stages
+BLUE3_CASES = [
+    ((37, 89, 131), "ppp", "f32"),   # x M = 96, y M = 192, z M = 384
+    ((157, 47, 179), "ppp", "f32"),  # 384, 96, 384
+    ((89, 11, 12), "pff", "f32"),    # wire x of 89 (M = 192)
+    ((37, 89, 131), "ppp", "f64"),
+]
+
+
+@pytest.mark.parametrize("n,bc,dtype", BLUE3_CASES)
+def test_parity_bluestein_register_lengths(torch_cuda, n, bc, dtype):
+    rho = synth.gaussian_mixture(n, 0.25, 4, seed=71 + sum(n), noise=1e-3, subtract_mean="p" in bc)
+    V, E, _ = _gpu_solve(torch_cuda, rho, bc, 0.25, dtype)
+    _check(V, E, rho, bc, 0.25, dtype)
+
+
 # The unpacked L3 = 1024 z kernel (32 x 32) with counts below and at L3/2, an
 # odd L2, a ragged kx tile, and all 1024 rows physical
 SPLIT1024_CASES = [
