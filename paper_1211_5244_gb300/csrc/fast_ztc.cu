@@ -16,15 +16,15 @@
 //
 // Precision: operands are split into a TF32 part and an FP32 remainder,
 // x = hi + lo (hi = x rounded to TF32, lo = x - hi exactly), for the data
-// and for the matrix. The three products X_hi F_hi, X_hi F_lo and X_lo F_hi
-// (each K = 64, N = 64) accumulate into one FP32 product in TMEM, as one
-// product along K = 192; the dropped X_lo F_lo is 2^-22 of the result. The
-// tensor cores read only the TF32 bits of an operand, so hi is passed as is
-// and lo loses at most 2^-11 of itself.
+// and for the matrix. The matrix is stored as [F_hi | F_lo] along N (N =
+// 128), so the two products X_hi [F_hi | F_lo] and X_lo [F_hi | F_lo],
+// accumulated in FP32, give all four partial products in two column halves,
+// summed on the CUDA cores. The tensor cores read only the TF32 bits of an
+// operand, so hi is passed as is and lo loses at most 2^-11 of itself.
 //
 // Layout per CTA (256 threads, 8 lines per tile, persistent):
-//   TMEM (256 columns): [0, 128) the A operand (hi, lo), [128, 192) the
-//   product. Rows are (k2, line), k2 < 16.
+//   TMEM (256 columns): [0, 128) the A operand (hi, lo), [128, 256) the
+//   product (F_hi half, F_lo half). Rows are (k2, line), k2 < 16.
 //   Shared memory: the matrix in the canonical K-major no-swizzle layout,
 //   the tile's n3 input rows and K^F slice (prefetched with cp.async during
 //   the previous tile), a padded transpose buffer, and the output rows.
@@ -167,17 +167,12 @@ struct TcLayout {
   static constexpr int SMEM = BAR_OFF + 16;
 };
 
-// one 32-point stage: D = A_hi F_hi + A_hi F_lo + A_lo F_hi, the three
-// split products accumulated along K into one N = 64 product (A in TMEM
-// columns [0, 64) and [64, 128), D in [128, 192); F_hi and F_lo are the two
-// N = 64 halves of the table, 16 KB apart)
+// one 32-point stage: D = A_hi [F_hi | F_lo] + A_lo [F_hi | F_lo]
+// (A in TMEM columns [0, 64) and [64, 128), D in [128, 256))
 __device__ __forceinline__ void stage32_mma(uint32_t tb, uint32_t mats) {
-  constexpr uint32_t id = tc::idesc<64>();
-  constexpr uint32_t lo = 64 * 64 * 4;
+  constexpr uint32_t id = tc::idesc<128>();
 #pragma unroll
   for (int ks = 0; ks < 8; ++ks) tc::mma(tb + 128, tb + 8 * ks, tc::sdesc(mats + 256 * ks, 128, 2048), id, ks > 0);
-#pragma unroll
-  for (int ks = 0; ks < 8; ++ks) tc::mma(tb + 128, tb + 8 * ks, tc::sdesc(mats + lo + 256 * ks, 128, 2048), id, 1);
 #pragma unroll
   for (int ks = 0; ks < 8; ++ks) tc::mma(tb + 128, tb + 64 + 8 * ks, tc::sdesc(mats + 256 * ks, 128, 2048), id, 1);
 }
@@ -277,12 +272,15 @@ __global__ void __launch_bounds__(256, NZ == 8 ? 2 : 1)
     __syncthreads();
     tc::fence_after();
   };
-  // this warpgroup's half of the product row: 16 complex values
+  // the two column halves of the product, summed: 16 complex values
   auto load_product = [&](float2 (&v)[16]) {
-    uint32_t d[32];
-    tc::ld32(tb + lane_base + 128 + 32 * g, d);
+    uint32_t dh[32], dl[32];
+    tc::ld32(tb + lane_base + 128 + 32 * g, dh);
+    tc::ld32(tb + lane_base + 192 + 32 * g, dl);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
+    for (int i = 0; i < 16; ++i)
+      v[i] = make_float2(__uint_as_float(dh[2 * i]) + __uint_as_float(dl[2 * i]),
+                         __uint_as_float(dh[2 * i + 1]) + __uint_as_float(dl[2 * i + 1]));
   };
   // 16 complex values as this warpgroup's half of an A operand row (hi, lo)
   auto store_operand = [&](const float2 (&v)[16]) {
@@ -440,8 +438,7 @@ const void* ztc_kernel(int L, bool half, int* threads, size_t* smem) {
 }
 
 // The 32-point DFT matrix as [F_hi | F_lo] (K = 64, N = 128) in the
-// canonical K-major layout (each N = 64 half is itself a canonical K = 64,
-// N = 64 operand, the second 16 KB after the first), then the twiddles W_512^{n1 k2} (n1 < 32,
+// canonical K-major layout, then the twiddles W_512^{n1 k2} (n1 < 32,
 // k2 < 16), computed in double precision.
 size_t ztc_table_floats(bool) { return (size_t)64 * 128 + 32 * 16 * 2; }
 
