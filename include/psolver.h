@@ -54,10 +54,12 @@ enum ps_dtype { PS_F32 = 0, PS_F64 = 1 };
  * PS_MATH_TF32X3:   FP32 plans only. Where a tensor-core kernel exists (today
  *   the z pass of L3 = 512 with n3 = 256 or 512) its DFT stages run as
  *   dense products with small DFT matrices on the tensor cores (tcgen05),
- *   each operand split into a TF32 part and a remainder and the product
- *   taken as hi*hi + hi*lo + lo*hi with FP32 accumulation (about FP32
- *   accuracy); the other passes stay on the CUDA cores. ps_plan_query's
- *   tensor_passes tells which passes use the tensor cores.
+ *   each operand split into a TF32 part and a remainder, the partial
+ *   products accumulated in FP32 in two halves (those with the matrix's TF32
+ *   part, those with its remainder) that the CUDA cores add (about FP32
+ *   accuracy); the other passes stay on the CUDA cores, and the energy is
+ *   the real-space sum 1/2 h^3 sum rho V accumulated in FP64 after the last
+ *   pass. ps_plan_query's tensor_passes tells which passes use the tensor cores.
  * PS_MATH_BF16X3:   split-BF16 tensor-core stages. Not built: this build's
  *   ps_plan_set_math returns PS_ERR_UNSUPPORTED for it. FP32-level accuracy
  *   from BF16 needs every operand split into three BF16 terms and six of the

@@ -370,6 +370,34 @@ static GenKernels<T> gen_kernels(int bm) {
   return gen_kernels_of<T, 0>();
 }
 
+// ---------------------------------------------------------------- energy
+
+// E = 1/2 h^3 sum_r rho(r) V(r) in real space with FP64 accumulation: the
+// energy of the tensor-core mode, whose Parseval sum over the spectrum of the
+// TF32 split products would carry that spectrum's error twice
+template <typename T>
+__global__ void __launch_bounds__(256)
+    energy_real_kernel(const T* __restrict__ rho, const T* __restrict__ V, long long n, double* partials,
+                       unsigned* counter, double scale, double* E) {
+  double acc = 0.0;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 products summed in groups of eight, each group added in FP64 (a
+    // conversion per element would run at the FP64 rate)
+    while (i < n) {
+      float f = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k, i += step)
+        if (i < n) f = fmaf(rho[i], V[i], f);
+      acc += (double)f;
+    }
+  } else {
+    for (; i < n; i += step) acc += rho[i] * V[i];
+  }
+  energy_finish(acc, partials, counter, scale, E);
+}
+
 // ---------------------------------------------------------------- VJP term
 
 // out = (accumulate ? out : 0) + h^3 * gE * V   (the dE/drho = h^3 V term of the VJP)
@@ -588,8 +616,18 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
   // the forward one copies rows of rho in 16-byte pieces
   const bool xyf = p->xyfuse && ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(V)) & 15) == 0;
   cudaError_t e;
+  // the tensor-core z pass leaves the energy to a real-space sum after P5
+  double* const Ez = p->tctab ? nullptr : E;
+  auto energy_after = [&]() -> cudaError_t {
+    if (!p->tctab || E == nullptr) return cudaSuccess;
+    const long long npts = (long long)p->n[0] * p->n[1] * p->n[2];
+    const long long want = (npts + 255) / 256;
+    const int grid = (int)std::min<long long>(std::min<long long>(want, 1216), p->npart);
+    energy_real_kernel<T><<<grid, 256, 0, s>>>(rho, V, npts, p->partials, p->counter, escale, E);
+    return cudaGetLastError();
+  };
   auto pass3 = [&]() -> cudaError_t {
-    if (p->cfg[P3].fast) return launch_fast(p, P3, B, B, E, escale, s);
+    if (p->cfg[P3].fast) return launch_fast(p, P3, B, B, Ez, escale, s);
     GenArgs a = gen_args<T>(p, P3);
     dim3 g((p->c + a.tk - 1) / a.tk, p->L[1]);
     gen_kernels<T>(p->cfg[P3].bm).pz<<<g, p->cfg[P3].threads, p->cfg[P3].gsmem, s>>>(
@@ -615,6 +653,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
       if ((e = launch_fast_chunk(p, P4, V, B, A, z0, cz, s)) != cudaSuccess) return e;
       if ((e = launch_fast_chunk(p, P5, V, B, A, z0, cz, s)) != cudaSuccess) return e;
     }
+    if ((e = energy_after()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], s);
     if (ev) cudaEventRecord(ev[5], s);
     return cudaGetLastError();
@@ -668,6 +707,7 @@ cudaError_t launch_solve(ps_plan_s* p, const T* rho, T* V, double* E, cudaStream
     gen_kernels<T>(p->cfg[P5].bm).p5<<<(nrows + rpc - 1) / rpc, p->cfg[P5].threads, p->cfg[P5].gsmem, s>>>(
         A, V, tw0, a);
   }
+  if ((e = energy_after()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], s);
   return cudaGetLastError();
 }
