@@ -374,8 +374,8 @@ cudaError_t configure_fast_f32(ps_plan_s* p) {
     const bool soa0 = !plain && (exact || Lb == 384) && p->y_kind != 1;
     const bool soa1 = soa0;
     int tk0 = 16, tk1 = 16;  // lines per tile (kx columns) of the chosen kernels
-    const void* f0 = soa0 ? ysoa_kernel(Lb, 0, half, &threads0, &smem0) : nullptr;
-    const void* f1 = soa1 ? ysoa_kernel(Lb, 1, half, &threads1, &smem1) : nullptr;
+    const void* f0 = soa0 ? ysoa_kernel(Lb, 0, half, &threads0, &smem0, &tk0) : nullptr;
+    const void* f1 = soa1 ? ysoa_kernel(Lb, 1, half, &threads1, &smem1, &tk1) : nullptr;
     p->ysoa = (f0 ? 1 : 0) | (f1 ? 2 : 0);
     if (!f0 && !plain) f0 = ypipe_kernel(Lb, 0, half, &threads0, &smem0, &tk0);
     if (!f1 && !plain) f1 = ypipe_kernel(Lb, 1, half, &threads1, &smem1, &tk1);

@@ -518,11 +518,11 @@ const void* zpipe_q_kernel(int L, bool half, int* threads, size_t* smem, int* tk
 // row of the 2T-point step); the next tile's rows land (cp.async) in the
 // exchange buffer once the current tile's exchange has been read. Rows beyond
 // a.nl (a count below L2/2) are zero on input and not stored on output.
-template <int KIND, int P, bool HALF>
-__global__ void __launch_bounds__(256, 2)
+template <int KIND, int P, bool HALF, int TK = 16>
+__global__ void __launch_bounds__(TK * 16, 512 / (TK * 16))
     k_ysoa_pipe(const void* src_v, void* dst_v, const float*, const float4* __restrict__ tw4, FastArgs a,
                 double*, unsigned*, double, double*) {
-  constexpr int T = 16, TK = 16, Q = 2 * T, L = P * Q;
+  constexpr int T = 16, Q = 2 * T, L = P * Q;
   static_assert(P <= T, "a thread holds at most one row of the 2T-point step");
   constexpr int NA = HALF ? P / 2 : P;
   constexpr int ROWS = KIND == 0 ? NA * Q : L;
@@ -692,23 +692,25 @@ __global__ void __launch_bounds__(256, 2)
   cp_async_wait_all();
 }
 
-const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem) {
+const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk) {
   const void* fn = nullptr;
-  int P = 0;
+  int P = 0, TK = 16;
   if (L == 512) {
     P = 16;
     fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, 16, true> : (const void*)k_ysoa_pipe<0, 16, false>)
                    : (half ? (const void*)k_ysoa_pipe<1, 16, true> : (const void*)k_ysoa_pipe<1, 16, false>);
   } else if (L == 384) {
     P = 12;
-    fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, 12, true> : (const void*)k_ysoa_pipe<0, 12, false>)
-                   : (half ? (const void*)k_ysoa_pipe<1, 12, true> : (const void*)k_ysoa_pipe<1, 12, false>);
+    TK = 8;
+    fn = kind == 0 ? (half ? (const void*)k_ysoa_pipe<0, 12, true, 8> : (const void*)k_ysoa_pipe<0, 12, false, 8>)
+                   : (half ? (const void*)k_ysoa_pipe<1, 12, true, 8> : (const void*)k_ysoa_pipe<1, 12, false, 8>);
   } else {
     return nullptr;
   }
-  *threads = 256;
+  *threads = 16 * TK;
+  *tk = TK;
   // exchange (the input rows share it), twiddles
-  *smem = (size_t)16 * P * 16 * sizeof(float4) + (size_t)16 * (P + 1) * sizeof(float4);
+  *smem = (size_t)16 * P * TK * sizeof(float4) + (size_t)16 * (P + 1) * sizeof(float4);
   return fn;
 }
 

@@ -59,7 +59,7 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 const void* xline_kernel(int M, int kind, bool half, int* threads, int* rows, size_t* smem);
 
 // The persistent packed y-pass kernels (L2 = 512), or nullptr.
-const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem);
+const void* ysoa_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk);
 
 // The persistent, prefetching y-pass kernels (L2 = 256, 512), or nullptr.
 const void* ypipe_kernel(int L, int kind, bool half, int* threads, size_t* smem, int* tk);
