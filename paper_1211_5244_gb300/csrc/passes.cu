@@ -558,6 +558,12 @@ cudaError_t configure_passes(ps_plan_s* p) {
       set_error("transform length %d needs more shared memory than a CTA has", rows[k]);
       return cudaErrorInvalidConfiguration;
     }
+    // register-form Bluestein: as many threads as the widest step has tasks
+    // (max(P, Q) x tk lines), so that no thread idles through steps 1 and 3
+    if (bm > 0 && canonical_order(p)) {
+      const int bp = blue_p(bm), tasks = std::max(bp, bm / bp) * cf.tk;
+      if (tasks < 256) cf.threads = (tasks + 31) / 32 * 32;
+    }
   }
   cudaError_t e;
   for (int k = -1; k < 5; ++k) {  // the Stockham kernels and those of each pass's Bluestein form
