@@ -179,12 +179,13 @@ int ps_plan_set_order(ps_plan plan, int a0, int a1, int a2);
 /*
  * ps_plan_autotune -- choose the padded lengths of the free axes and the
  * kernel schedule by timing. Any L >= 2n - 1 gives the same physical result
- * (§2); the candidates are the paper's 2n and the smallest lengths >= 2n - 1
- * made of the factors {2}, {2, 3} and {2, 3, 5, 7} (a power of two selects
- * the register-resident kernels). Then, at the fastest lengths, each schedule
+ * (§2); the candidates are the paper's 2n, the smallest lengths >= 2n - 1
+ * made of the factors {2}, {2, 3} and {2, 3, 5, 7}, and the smallest length
+ * >= 2n - 1 with register-resident FP32 kernels (a power of two, 96, 192 or
+ * 384). Then, at the fastest lengths, each schedule
  * choice that applies to the plan is timed in turn and kept if faster: the
  * lines per tile of the generic passes, their radix split (radix 8 first or
- * radix 4 only), the lines per tile of the persistent packed z kernel, the y
+ * radix 4 only), both again per physical axis, the lines per tile of the persistent packed z kernel, the y
  * kernel form (packed persistent, unpacked persistent, non-persistent), the
  * fused x/y passes (see ps_plan_info.fused), the chunks of the x and y passes
  * and, for a plan whose order is not x first, the x-first order. One trial plan per candidate
