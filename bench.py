@@ -56,8 +56,8 @@ PASS_NAMES = ["p1_fwd_x_r2c", "p2_fwd_y", "p3_z_fwd_mul_inv", "p4_inv_y", "p5_in
 Z_KERNEL_FILES = ("fast_zsoa.cu", "fft_soa.cuh", "fft_regs.cuh", "fft_fast.cuh", "reduce.cuh", "common.cuh",
                   "../../include/psolver.h")
 TRAFFIC = {
-    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 367240448 + 221577216, "files": Z_KERNEL_FILES,
-                                          "src": "0e5a45581f19d3b5"},
+    ("p3_z_fwd_mul_inv", "free256_f32"): {"bytes": 367789568 + 221741824, "files": Z_KERNEL_FILES,
+                                          "src": "3a25e6ce393611ad"},
 }
 
 def _src_hash(files=None):
