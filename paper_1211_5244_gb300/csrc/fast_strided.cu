@@ -203,7 +203,7 @@ const void* strided_kernel(int L, int kind, bool half, int* threads, size_t* sme
 // apart, on alternate halves of the banks, instead of 32 apart on the same
 // 16 banks (a 4-way conflict in the forward write and the inverse read).
 template <int P, int Q, bool HALF, int TK>
-__global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 1024 ? 2 : 3)
+__global__ void __launch_bounds__(TK*(P < Q ? P : Q), P > Q ? 512 / (TK * Q) : (P * Q >= 1024 ? 2 : 3))
     k_zpipe_u(const void*, void* line_v, const float* __restrict__ K, const float2* __restrict__ tw, FastArgs a,
               double* partials, unsigned* counter, double escale, double* E) {
   constexpr int L = P * Q;
@@ -418,7 +418,7 @@ const void* zpipe_u_kernel(int L, bool half, int* threads, size_t* smem, int* tk
 // bank halves instead of 4-way on the same 16 banks. The input rows keep the
 // unpadded layout (they are read before the exchange is written).
 template <int P, int Q, int KIND, bool HALF, int TK>
-__global__ void __launch_bounds__(TK*(P < Q ? P : Q), P * Q >= 512 ? 2 : 3)
+__global__ void __launch_bounds__(TK*(P < Q ? P : Q), P > Q ? 512 / (TK * Q) : (P * Q >= 512 ? 2 : 3))
     k_ypipe(const void* src_v, void* dst_v, const float*, const float2* __restrict__ tw, FastArgs a, double*,
             unsigned*, double, double*) {
   pdl_wait();
